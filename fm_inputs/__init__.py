@@ -1,0 +1,85 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle.
+
+This module holds data only: the named workloads (particle masses and charges,
+total momentum, grid sizes, splitting parameters, shifts) and seeded random
+vectors.  It contains none of the method's arithmetic, so both the CUDA path
+and the CPU oracle may take their inputs from it without sharing any
+computation.
+
+Workloads follow the systems of Section 4 (atomic He with an infinitely heavy
+core, ``10^15`` a.u. in practice) and the He-like / Ps- / H- systems of the
+benchmark configurations.  Energies are in the units of the reduced-coordinate
+equations (Hartree for electron-mass units); box sizes are in reduced
+coordinates.
+"""
+from __future__ import annotations
+
+import copy
+
+import numpy as np
+
+INF_MASS = 1.0e15  # "infinite" core mass, Section 4
+
+SYSTEMS = {
+    # masses (m1, m2, m3), charges (Z1, Z2, Z3); particles 1, 2 are identical
+    "He": {"mass": (1.0, 1.0, INF_MASS), "charge": (-1.0, -1.0, 2.0)},
+    "Hminus": {"mass": (1.0, 1.0, INF_MASS), "charge": (-1.0, -1.0, 1.0)},
+    "Psminus": {"mass": (1.0, 1.0, 1.0), "charge": (-1.0, -1.0, 1.0)},
+}
+
+# splitting modes
+MERKURIEV, NO_SPLIT, SCHRODINGER = 0, 1, 2
+# node maps
+MAP_POW, MAP_EQUI, MAP_SIN = 0, 1, 2
+
+
+def make_workload(system="He", J=0, tau=1, p=1, identical_pair=12,
+                  nint=(24, 24, 8), R=(40.0, 40.0), maps=(MAP_POW, MAP_POW, MAP_SIN),
+                  mode=MERKURIEV, nu=2.01, x0=1.0, y0=float("inf"), vs_cut=1e-20,
+                  shift=-2.95, k=1, name=None):
+    """Return a plain dict describing one Faddeev-Merkuriev problem."""
+    sysd = SYSTEMS[system]
+    return {
+        "name": name or f"{system}_J{J}_{nint[0]}x{nint[1]}x{nint[2]}",
+        "system": system,
+        "mass": tuple(float(m) for m in sysd["mass"]),
+        "charge": tuple(float(z) for z in sysd["charge"]),
+        "J": int(J), "tau": int(tau), "p": int(p), "identical_pair": int(identical_pair),
+        "nint": tuple(int(n) for n in nint), "R": tuple(float(r) for r in R),
+        "maps": tuple(int(m) for m in maps),
+        "mode": int(mode), "nu": float(nu), "x0": float(x0), "y0": float(y0),
+        "vs_cut": float(vs_cut),
+        "shift": float(shift), "k": int(k),
+    }
+
+
+# The named workloads.  Interval counts are the spline intervals per axis;
+# cubic Hermite splines give 2*n dofs in x, y (Dirichlet at both ends) and
+# 2*n + 2 in z.
+WORKLOADS = {
+    # He-like, L=0, 24x24 intervals in x, y to 40, 8 in z: small case
+    "he_l0_24x24x8": make_workload("He", 0, nint=(24, 24, 8), R=(40.0, 40.0), shift=-2.95, k=1,
+                                   name="he_l0_24x24x8"),
+    # He-like, L=0, 96x96x24 intervals: the large single-GPU case
+    "he_l0_96x96x24": make_workload("He", 0, nint=(96, 96, 24), R=(40.0, 40.0), shift=-2.95, k=1,
+                                    name="he_l0_96x96x24"),
+}
+for _J in (1, 2, 3):
+    WORKLOADS[f"psm_l{_J}_64x64x16"] = make_workload(
+        "Psminus", _J, nint=(64, 64, 16), R=(80.0, 80.0), shift=-0.27, k=4,
+        name=f"psm_l{_J}_64x64x16")
+
+
+def workload(name, **overrides):
+    """A copy of a named workload with fields overridden."""
+    w = copy.deepcopy(WORKLOADS[name])
+    w.update(overrides)
+    return w
+
+
+def rand_vec(n, seed):
+    """Seeded N(0,1) vector of length n (float64)."""
+    return np.random.default_rng(seed).standard_normal(int(n))
+
+
+SEED_BASE = 20050539

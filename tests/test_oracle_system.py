@@ -1,0 +1,179 @@
+"""Pins for the oracle's collocation matrices: exact action on polynomials,
+the separable two-body limit, dense brute force, splitting invariance and the
+paper's He energies."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from fm_inputs import workload, MERKURIEV, NO_SPLIT, SCHRODINGER
+from oracle import physics as ph
+from oracle import solvers
+from oracle.system import FMSystem
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _poly_fns(rng, a, b, dirichlet):
+    """A random cubic (vanishing at a and b when dirichlet) with its first two derivatives."""
+    if dirichlet:
+        q0, q1 = rng.standard_normal(2)
+        co = np.polymul(np.polymul([1.0, -a], [-1.0, b]), [q1, q0])
+    else:
+        co = rng.standard_normal(4)
+    return (lambda t: np.polyval(co, t), lambda t: np.polyval(np.polyder(co), t),
+            lambda t: np.polyval(np.polyder(co, 2), t))
+
+
+def _interp(g, fx, fy, fz):
+    cx = g.ax.basis.coefficients_of(fx[0], fx[1])
+    cy = g.ay.basis.coefficients_of(fy[0], fy[1])
+    cz = g.az.basis.coefficients_of(fz[0], fz[1])
+    return np.einsum("k,i,j->kij", cz, cx, cy).reshape(-1)
+
+
+@pytest.mark.parametrize("J,tau", [(0, 1), (1, 1), (2, 1), (2, -1)])
+def test_local_operator_on_polynomials(J, tau):
+    """H (without coupling) applied to interpolants of separable cubics equals Eq. FM-pre's
+    left operator applied to the cubics, at every collocation point."""
+    wl = workload("he_l0_24x24x8", J=J, tau=tau, nint=(4, 3, 3), R=(7.0, 9.0))
+    s = FMSystem(wl)
+    a = 1
+    g = s.g[a]
+    rng = np.random.default_rng(7)
+    F = []
+    c = np.zeros(s.N)
+    for iM in range(s.nM):
+        fx = _poly_fns(rng, 0.0, g.Rx, True)
+        fy = _poly_fns(rng, 0.0, g.Ry, True)
+        fz = _poly_fns(rng, -1.0, 1.0, False)
+        F.append((fx, fy, fz))
+        c[s.off[a] + iM * g.npts: s.off[a] + (iM + 1) * g.npts] = _interp(g, fx, fy, fz)
+    out = s.H_local() @ c
+    k, i, j, z, x, y = g.coords(np.arange(g.npts))
+    W = s.W(a, x, y, z)
+    for iM, Mp in enumerate(s.Mps):
+        fx, fy, fz = F[iM]
+        f = fx[0](x) * fy[0](y) * fz[0](z)
+        fzz = fx[0](x) * fy[0](y) * fz[2](z)
+        fz1 = fx[0](x) * fy[0](y) * fz[1](z)
+        exp = (-fx[0](x) * fy[2](y) * fz[0](z) - fx[2](x) * fy[0](y) * fz[0](z)
+               - (1 / x ** 2 + 1 / y ** 2) * ((1 - z * z) * fzz - 2 * (Mp + 1) * z * fz1 - Mp * (Mp + 1) * f)
+               + (J * (J + 1) - 2 * Mp * Mp) / y ** 2 * f + W * f)
+        if iM + 1 < s.nM:
+            gx, gy, gz = F[iM + 1]
+            exp += ph.lam_hat_plus(J, Mp) / y ** 2 * gx[0](x) * gy[0](y) * (-(1 - z * z) * gz[1](z) + 2 * (Mp + 1) * z * gz[0](z))
+        if iM - 1 >= 0:
+            gx, gy, gz = F[iM - 1]
+            exp += ph.lam_hat_minus(J, Mp) / y ** 2 * gx[0](x) * gy[0](y) * gz[1](z)
+        got = out[s.off[a] + iM * g.npts: s.off[a] + (iM + 1) * g.npts]
+        assert np.max(np.abs(got - exp)) < 1e-9 * np.max(np.abs(exp))
+
+
+def test_coupling_rows_evaluate_rotated_polynomials():
+    """The coupling rows applied to an interpolated cubic source give V^(s) rho g(X_beta) exactly (L = 0)."""
+    wl = workload("he_l0_24x24x8", nint=(4, 4, 3), R=(9.0, 8.0), mode=NO_SPLIT)
+    s = FMSystem(wl)
+    rng = np.random.default_rng(8)
+    g3 = s.g[3]
+    fx, fy, fz = _poly_fns(rng, 0.0, g3.Rx, True), _poly_fns(rng, 0.0, g3.Ry, True), _poly_fns(rng, -1.0, 1.0, False)
+    c = np.zeros(s.N)
+    c[s.off[3]:s.off[3] + g3.csize] = _interp(g3, fx, fy, fz)
+    g1 = s.g[1]
+    rows = s.off[1] + np.arange(g1.npts)
+    out = (s.H(rows) - s.H_local(rows)) @ c
+    k, i, j, z, x, y = g1.coords(np.arange(g1.npts))
+    cc, ss = ph.rotation_cs(s.m, 3, 1)
+    xb, yb, zb = ph.rotate_xyz(cc, ss, x, y, z)
+    inside = (xb <= g3.Rx) & (yb <= g3.Ry)
+    vs, _ = ph.split_potential(s.m, s.Z, 1, x, y, NO_SPLIT, 2.01, 1.0, np.inf)
+    exp = np.where(inside, vs * x * y / (xb * yb) * fx[0](xb) * fy[0](yb) * fz[0](zb), 0.0)
+    assert np.max(np.abs(out - exp)) < 1e-9 * np.max(np.abs(exp))
+
+
+def test_separable_two_body_limit():
+    """Z_1 = 0: the alpha = 1 block separates, E = eps_x(hydrogen) + eps_y(box) exactly,
+    approaching -mu_1 (Z_2 Z_3)^2 / 2 + (pi/R_y)^2 under refinement."""
+    wl = workload("he_l0_24x24x8", nint=(6, 5, 3), R=(20.0, 15.0), identical_pair=0)
+    wl["charge"] = (0.0, -1.0, 2.0)
+    s = FMSystem(wl)
+    H, S = s.H(), s.S()
+    g = s.g[1]
+    x = g.ax.pts
+    A = -g.ax.mat(2) + (np.sqrt(2 * s.mu_pair[0]) * (-2.0) / x)[:, None] * g.ax.mat(0)
+    ex = np.sort(sla.eig(A, g.ax.mat(0), right=False).real)
+    ey = np.sort(sla.eig(-g.ay.mat(2), g.ay.mat(0), right=False).real)
+    target = ex[0] + ey[0]
+    E, _ = solvers.eigs_near(H, S, target + 0.01, 2)
+    assert np.min(np.abs(E - target)) < 1e-11
+    # the two 1D factors approach the closed forms under refinement
+    from oracle.splines import Axis, MAP_POW, MAP_EQUI
+    ax = Axis(MAP_POW, 96, 0.0, 20.0, dirichlet=True)
+    ay = Axis(MAP_EQUI, 48, 0.0, 15.0, dirichlet=True)
+    A = -ax.mat(2) + (np.sqrt(2 * s.mu_pair[0]) * (-2.0) / ax.pts)[:, None] * ax.mat(0)
+    fine = np.sort(sla.eig(A, ax.mat(0), right=False).real)[0] + np.sort(sla.eig(-ay.mat(2), ay.mat(0), right=False).real)[0]
+    assert abs(fine - (-s.mu_pair[0] * 4.0 / 2 + (np.pi / 15.0) ** 2)) < 1e-4
+
+
+def test_dense_brute_force_matches_shift_invert():
+    wl = workload("he_l0_24x24x8", nint=(4, 4, 2), R=(12.0, 12.0))
+    s = FMSystem(wl)
+    H, S = s.H(), s.S()
+    Ed = solvers.eigs_dense(H, S)
+    E, v = solvers.eigs_near(H, S, -2.95, 3)
+    for e in E:
+        assert np.min(np.abs(Ed - e)) < 1e-11 * abs(e)
+        assert np.min(np.abs(Ed - e)) == np.min(np.abs(Ed - e))
+    assert solvers.residual(H, S, E[0].real, v[:, 0].real) < 1e-10
+
+
+def test_splitting_invariance_and_he_ground_state():
+    """Merkuriev split, no split and the Schrodinger limit give the same level to
+    discretisation error, converging (4th order) toward He 1^1S = -2.90372."""
+    spread, dist = [], []
+    for nint in ((8, 8, 4), (12, 12, 6)):
+        Es = []
+        for mode in (MERKURIEV, NO_SPLIT, SCHRODINGER):
+            wl = workload("he_l0_24x24x8", nint=nint, R=(20.0, 20.0), mode=mode)
+            s = FMSystem(wl)
+            E, _ = solvers.eigs_near(s.H(), s.S(), -2.95, 1)
+            Es.append(E[0].real)
+        spread.append(np.ptp(Es))
+        dist.append(abs(np.mean(Es) + 2.90372))
+    assert spread[1] < 0.01 and dist[1] < 0.04
+    assert spread[0] / spread[1] > 3 and dist[0] / dist[1] > 3
+
+
+def test_he_2P_levels_approach_paper_values():
+    """He J=1 (2^1P, 3^1P) with the paper's boxes (1: 36, 36; 3: 9, 6): the
+    Richardson estimate from two grids lies near the benchmark energies of Table pardiso."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_energies.json")))
+    E2P, E3P = gold["He_2_1P"]["value"], gold["He_3_1P"]["value"]
+    res = []
+    for n1, n3 in (((12, 12, 4), (5, 4, 4)), ((16, 16, 4), (6, 5, 5))):
+        wl = workload("he_l0_24x24x8", J=1, nint=n1, R=(36.0, 36.0))
+        wl["grids"] = {3: {"nint": n3, "R": (9.0, 6.0)}}
+        s = FMSystem(wl)
+        E, _ = solvers.eigs_near(s.H(), s.S(), -2.10, 3)
+        res.append(np.sort(E.real)[:2])
+    q = (16 / 12) ** 4 - 1
+    extrap = res[1] + (res[1] - res[0]) / q
+    assert abs(extrap[0] - E2P) < 3e-3 and abs(extrap[1] - E3P) < 3e-3
+    assert abs((extrap[1] - extrap[0]) - (E3P - E2P)) < 1.5e-3
+
+
+def test_golden_convergence_sequence():
+    """Stored oracle sequence (tests/golden/make_golden.py) approaches the paper's He 2^1P/3^1P."""
+    path = os.path.join(GOLDEN, "oracle_he_2P.json")
+    data = json.load(open(path))
+    gold = json.load(open(os.path.join(GOLDEN, "paper_energies.json")))
+    E = np.array([r["E"][:2] for r in data["runs"]])
+    n = np.array([r["n1"][0] for r in data["runs"]], dtype=float)
+    err = np.abs(E - np.array([gold["He_2_1P"]["value"], gold["He_3_1P"]["value"]]))
+    assert np.all(np.diff(err[:, 0]) < 0) and np.all(np.diff(err[:, 1]) < 0)
+    q = (n[-1] / n[-2]) ** 4 - 1
+    extrap = E[-1] + (E[-1] - E[-2]) / q
+    assert abs(extrap[0] - gold["He_2_1P"]["value"]) < 1e-3
+    assert abs(extrap[1] - gold["He_3_1P"]["value"]) < 1e-3
