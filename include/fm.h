@@ -1,0 +1,180 @@
+/*
+ * libfm -- GB300 (sm_103a) solver for the spline-collocation discretisation of the
+ * three-body Faddeev-Merkuriev equations in total orbital momentum representation
+ * (Gradusov, Roudnev, Yarevsky, Yakovlev, arXiv:2005.05398).
+ *
+ * The problem (Section 3.1, Eq. FM-lin): find E and c with H c = E S c, or solve
+ * (H - E S) x = b, where H is the collocation matrix of Eq. FM-fin (equivalently
+ * Eq. FM-pre with its right-hand side moved to the left) and S has entries
+ * S^k(z) S^i(x) S^j(y) at the collocation points.  The iterative solves are
+ * preconditioned by the tensor-trick inverse of Eq. prec-2 (Section 3.2).
+ *
+ * Conventions
+ *  - Every function returns an fm_status (0 on success).  fm_strerror() names a code.
+ *  - Vectors are float64 and live in device memory of the context's GPU unless the
+ *    entry point says "host".  Their length is n_unknowns (fm_size()).  The caller
+ *    owns every buffer it passes; the library never frees caller memory and keeps
+ *    no pointer to it after the call returns.
+ *  - Vector layout (Section 3.2 ordering): [solved component a][M' = M0..J][k_z][i_x][j_y],
+ *    j_y fastest.  Solved components: particles {1, 3} when particles 1 and 2 are
+ *    identical (Eq. 2-sym-part), {1, 2, 3} otherwise, {1} in the Schrodinger limit.
+ *  - All work is ordered on the context's stream (fm_opts.stream, or the legacy
+ *    default stream when NULL).  fm_apply / fm_apply_S / fm_precond_apply return
+ *    without synchronising; fm_solve / fm_eigs synchronise before they return.
+ *  - A context is used by one host thread at a time.
+ *  - Energies are in the units of the reduced-coordinate equations (Hartree for
+ *    electron-mass units); box sizes R_x, R_y are in reduced Jacobi coordinates.
+ */
+#ifndef FM_H
+#define FM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FM_OK = 0,
+  FM_ERR_ARG = -1,              /* invalid argument (sizes, n_M = 0, null pointers, ...) */
+  FM_ERR_OOM = -2,              /* device or host allocation failed */
+  FM_ERR_CUDA = -3,             /* a CUDA runtime call failed */
+  FM_ERR_NOT_CONVERGED = -4,    /* iteration limit reached; outputs hold the best iterate */
+  FM_ERR_BREAKDOWN = -5,        /* Krylov breakdown (zero or non-finite norm) */
+  FM_ERR_COMPLEX_SPECTRUM = -6, /* a 1D generalized eigenproblem has complex eigenvalues */
+  FM_ERR_NO_SHIFT = -7,         /* preconditioner used before fm_set_shift */
+  FM_ERR_NUMERIC = -8           /* singular 1D or banded factor, non-finite setup value */
+} fm_status;
+
+/* Three particles (Section 2.1).  Masses in electron masses ("infinite" core: 1e15,
+ * Section 4), charges in units of e.  J = total orbital momentum, tau = +1/-1 the
+ * parity label of the F basis (Eq. F-def), exch_p = +1/-1 exchange symmetry of the
+ * identical pair (Eq. 2-sym), identical_pair = 12 when particles 1 and 2 are
+ * identical (solve components 1 and 3), 0 otherwise (solve 1, 2, 3). */
+typedef struct {
+  double mass[3];
+  double charge[3];
+  int J;
+  int tau;
+  int exch_p;
+  int identical_pair;
+} fm_system;
+
+enum { FM_MAP_POW = 0, FM_MAP_EQUI = 1, FM_MAP_SIN = 2 };
+
+/* Spline grid of one solved component, notation (n_x, n_y, n_z; R_x, R_y) of Section 4.
+ * Cubic Hermite splines, nint intervals per axis: 2*nint functions in x and y
+ * (Dirichlet at 0 and R), 2*nint + 2 in z on [-1, 1].  Node maps: Eq. map-pow
+ * (FM_MAP_POW, x and y), equidistant, and sin(pi u / 2) (FM_MAP_SIN, z only). */
+typedef struct {
+  int nint_x, nint_y, nint_z;
+  double Rx, Ry;
+  int xmap, ymap, zmap;
+  int basis; /* 0 = cubic Hermite (the only basis of this library) */
+} fm_grid;
+
+enum { FM_SPLIT_MERKURIEV = 0, FM_SPLIT_NONE = 1, FM_SPLIT_SCHRODINGER = 2 };
+
+/* Potential splitting (Eqs. PotSplit, split3b, Mcutoff0): mode 0 = Merkuriev cut-off
+ * chi = 2/(1+exp[(x/x0)^nu/(1+y/y0)]) (y0 = +inf allowed), mode 1 = no splitting
+ * (V^(s) = V: standard Faddeev equations), mode 2 = Schrodinger limit (one component,
+ * all pair potentials on the left, Section 2.1).  In mode 0 a collocation point
+ * carries the V^(s) coupling only where chi > vs_cut (0 keeps every nonzero chi). */
+typedef struct {
+  int mode;
+  double nu, x0, y0;
+  double vs_cut;
+} fm_splitting;
+
+enum { FM_PREC_FP64 = 0, FM_PREC_FP32 = 1 };
+
+typedef struct {
+  double tol;        /* relative residual of fm_solve (FGMRES true residual), e.g. 1e-12 */
+  int restart_m;     /* FGMRES restart length (1..128) */
+  int max_iters;     /* total FGMRES iteration limit per fm_solve */
+  int precision;     /* FM_PREC_FP64 or FM_PREC_FP32 (preconditioner arithmetic) */
+  int ncv;           /* Arnoldi basis size of fm_eigs (>= 2k + 1) */
+  int max_restarts;  /* Arnoldi restarts of fm_eigs */
+  double eig_tol;    /* relative Ritz residual of fm_eigs, e.g. 1e-12 */
+  int z_eigs;        /* 0 = replace z eigenvalues by -l(l+1) (Eq. prop-eq); 1 = keep them (n_M = 1 only) */
+  int device;        /* CUDA device ordinal */
+  void* stream;      /* cudaStream_t, NULL = legacy default stream */
+} fm_opts;
+
+typedef struct {
+  int iters;          /* FGMRES iterations (fm_solve) or total inner iterations (fm_eigs) */
+  int restarts;       /* FGMRES restarts or Arnoldi restarts */
+  int op_applies;     /* shift-invert operator applications (fm_eigs) */
+  int converged;      /* 1 when every requested quantity met its tolerance */
+  double resid;       /* final relative residual (fm_solve) or max eigen-residual (fm_eigs) */
+  double ms;          /* wall time of the call */
+} fm_info;
+
+typedef struct fm_ctx fm_ctx;
+
+/* Default options: tol 1e-12, restart 64, max_iters 2000, FP64, ncv 20, 50 restarts,
+ * eig_tol 1e-12, replaced z eigenvalues, device 0, default stream. */
+void fm_default_opts(fm_opts* opts);
+
+/* Build a context: 1D bases and collocation points (Section 3.1), pointwise potential
+ * tables, the V^(s) coupling geometry (Eqs. r-form, s-rot), the E-independent z and x
+ * decompositions of the preconditioner (Eq. z-dec and the x problems of Section 3.2)
+ * and the Krylov workspace.  grids: n_grids = 1 (same grid for every solved component)
+ * or one per solved component.  On error *out is NULL. */
+int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_splitting* split,
+              const fm_opts* opts, fm_ctx** out);
+
+/* Sizes: total unknowns, solved components, n_M = J - M0 + 1 (Section 2.2). */
+int fm_size(const fm_ctx* ctx, int64_t* n_unknowns, int* n_components, int* n_M);
+
+/* Per solved component: particle label (1..3), dims = {n_z, n_x, n_y}, offset of its block. */
+int fm_component(const fm_ctx* ctx, int comp, int* label, int dims[3], int64_t* offset);
+
+/* y = (H - E S) x (Eq. FM-lin).  x and y: device, length n_unknowns, must not overlap. */
+int fm_apply(fm_ctx* ctx, double E, const double* x, double* y);
+
+/* y = S x.  Device buffers, no overlap. */
+int fm_apply_S(fm_ctx* ctx, const double* x, double* y);
+
+/* Build the E*-dependent part of the preconditioner (the banded y systems of
+ * Eq. ops / the tridiagonal M' chains, Section 3.2) for shift Estar. */
+int fm_set_shift(fm_ctx* ctx, double Estar);
+
+/* y = L^{-1}(E*) x, the tensor-trick preconditioner of Eq. prec-2.  Device buffers,
+ * no overlap.  FM_ERR_NO_SHIFT before the first fm_set_shift. */
+int fm_precond_apply(fm_ctx* ctx, const double* x, double* y);
+
+/* Solve (H - E S) x = rhs by right-preconditioned FGMRES (restarted) with the
+ * preconditioner built for E (fm_set_shift is called when E differs from the current
+ * shift).  x (device) is the initial guess on entry (pass zeros for none) and the
+ * solution on return.  Converged when ||rhs - (H - E S) x|| <= tol ||rhs|| in float64.
+ * FM_ERR_NOT_CONVERGED leaves the best iterate in x.  info may be NULL. */
+int fm_solve(fm_ctx* ctx, double E, const double* rhs, double* x, fm_info* info);
+
+/* k eigenpairs of H c = E S c nearest 'shift' by restarted Arnoldi on the
+ * shift-invert operator (H - shift S)^{-1} S (Eq. FM-lin; E = shift + 1/theta), each
+ * operator application an fm_solve.  v0 (device, may be NULL = seeded normal start)
+ * starts the iteration.  evals (host, k doubles) receive E sorted by |E - shift|;
+ * evecs (device, k * n_unknowns, may be NULL) the eigenvectors normalised to unit
+ * 2-norm with their largest-magnitude entry positive.  info may be NULL. */
+int fm_eigs(fm_ctx* ctx, double shift, int k, const double* v0, double* evals, double* evecs, fm_info* info);
+
+/* fm_eigs with HOST buffers: v0_host (may be NULL) is copied to the device, evecs_host
+ * (may be NULL) receives the eigenvectors.  The copies run on the context's stream. */
+int fm_eigs_host(fm_ctx* ctx, double shift, int k, const double* v0_host, double* evals,
+                 double* evecs_host, fm_info* info);
+
+/* Release every resource of the context.  NULL is allowed. */
+void fm_destroy(fm_ctx* ctx);
+
+/* Static description of a status code. */
+const char* fm_strerror(int status);
+
+/* Diagnostics: counts of the library's own kernel launches since the context was
+ * created (launches) and bytes of device memory the context holds. */
+int fm_stats(const fm_ctx* ctx, int64_t* launches, int64_t* device_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FM_H */

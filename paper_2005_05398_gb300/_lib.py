@@ -1,0 +1,219 @@
+"""ctypes binding of libfm (include/fm.h): argument marshalling only.
+
+Every computation runs inside libfm's CUDA kernels; PyTorch provides device
+memory and streams.  The functions keep the C names (fm_create, fm_apply,
+fm_precond_apply, fm_solve, fm_eigs, ...).  Loading fails loudly when the
+library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfm.so")
+
+c_double, c_int, c_int64, c_void_p = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+
+
+class fm_system(ctypes.Structure):
+    _fields_ = [("mass", c_double * 3), ("charge", c_double * 3), ("J", c_int), ("tau", c_int),
+                ("exch_p", c_int), ("identical_pair", c_int)]
+
+
+class fm_grid(ctypes.Structure):
+    _fields_ = [("nint_x", c_int), ("nint_y", c_int), ("nint_z", c_int), ("Rx", c_double), ("Ry", c_double),
+                ("xmap", c_int), ("ymap", c_int), ("zmap", c_int), ("basis", c_int)]
+
+
+class fm_splitting(ctypes.Structure):
+    _fields_ = [("mode", c_int), ("nu", c_double), ("x0", c_double), ("y0", c_double), ("vs_cut", c_double)]
+
+
+class fm_opts(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("restart_m", c_int), ("max_iters", c_int), ("precision", c_int),
+                ("ncv", c_int), ("max_restarts", c_int), ("eig_tol", c_double), ("z_eigs", c_int),
+                ("device", c_int), ("stream", c_void_p)]
+
+
+class fm_info(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("restarts", c_int), ("op_applies", c_int), ("converged", c_int),
+                ("resid", c_double), ("ms", c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+FM_OK, FM_ERR_NOT_CONVERGED = 0, -4
+
+_LIB = None
+
+SIGNATURES = {
+    "fm_default_opts": (None, [ctypes.POINTER(fm_opts)]),
+    "fm_create": (c_int, [ctypes.POINTER(fm_system), ctypes.POINTER(fm_grid), c_int, ctypes.POINTER(fm_splitting),
+                          ctypes.POINTER(fm_opts), ctypes.POINTER(c_void_p)]),
+    "fm_size": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    "fm_component": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int64)]),
+    "fm_apply": (c_int, [c_void_p, c_double, c_void_p, c_void_p]),
+    "fm_apply_S": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "fm_set_shift": (c_int, [c_void_p, c_double]),
+    "fm_precond_apply": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "fm_solve": (c_int, [c_void_p, c_double, c_void_p, c_void_p, ctypes.POINTER(fm_info)]),
+    "fm_eigs": (c_int, [c_void_p, c_double, c_int, c_void_p, ctypes.POINTER(c_double), c_void_p,
+                        ctypes.POINTER(fm_info)]),
+    "fm_eigs_host": (c_int, [c_void_p, c_double, c_int, c_void_p, ctypes.POINTER(c_double), c_void_p,
+                             ctypes.POINTER(fm_info)]),
+    "fm_destroy": (None, [c_void_p]),
+    "fm_strerror": (ctypes.c_char_p, [c_int]),
+    "fm_stats": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)]),
+}
+
+
+class FMError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} failed: {lib().fm_strerror(code).decode()} ({code})")
+        self.code = code
+
+
+def lib():
+    """The loaded libfm (raises when it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfm.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(fn, rc, allow=()):
+    if rc != FM_OK and rc not in allow:
+        raise FMError(fn, rc)
+    return rc
+
+
+def _ptr(t):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return c_void_p(t.data_ptr())
+
+
+def make_structs(wl):
+    """C structs from a workload dict (fm_inputs)."""
+    s = fm_system()
+    s.mass[:] = list(wl["mass"])
+    s.charge[:] = list(wl["charge"])
+    s.J, s.tau, s.exch_p, s.identical_pair = wl["J"], wl["tau"], wl["p"], wl["identical_pair"]
+    labels = [1] if wl["mode"] == 2 else ([1, 3] if wl["identical_pair"] == 12 else [1, 2, 3])
+    per = wl.get("grids") or {}
+    gl = []
+    for a in (labels if per else labels[:1]):
+        nint = per.get(a, {}).get("nint", wl["nint"])
+        R = per.get(a, {}).get("R", wl["R"])
+        g = fm_grid()
+        g.nint_x, g.nint_y, g.nint_z = nint
+        g.Rx, g.Ry = R
+        g.xmap, g.ymap, g.zmap = wl["maps"]
+        g.basis = 0
+        gl.append(g)
+    grids = (fm_grid * len(gl))(*gl)
+    sp = fm_splitting()
+    sp.mode, sp.nu, sp.x0 = wl["mode"], wl["nu"], wl["x0"]
+    sp.y0 = wl["y0"] if math.isfinite(wl["y0"]) else float("inf")
+    sp.vs_cut = wl.get("vs_cut", 0.0)
+    return s, grids, len(gl), sp
+
+
+class Context:
+    """One libfm context (fm_create ... fm_destroy)."""
+
+    def __init__(self, wl, **opt):
+        L = lib()
+        self.wl = dict(wl)
+        o = fm_opts()
+        L.fm_default_opts(ctypes.byref(o))
+        for k, v in opt.items():
+            if k == "stream":
+                o.stream = c_void_p(v.cuda_stream if hasattr(v, "cuda_stream") else v)
+            else:
+                setattr(o, k, v)
+        self.opts = o
+        s, grids, ng, sp = make_structs(wl)
+        h = c_void_p()
+        _check("fm_create", L.fm_create(ctypes.byref(s), grids, ng, ctypes.byref(sp), ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        n, nc, nM = c_int64(), c_int(), c_int()
+        _check("fm_size", L.fm_size(h, ctypes.byref(n), ctypes.byref(nc), ctypes.byref(nM)))
+        self.n, self.ncomp, self.nM = n.value, nc.value, nM.value
+        self.components = []
+        for i in range(self.ncomp):
+            lab, dims, off = c_int(), (c_int * 3)(), c_int64()
+            _check("fm_component", L.fm_component(h, i, ctypes.byref(lab), dims, ctypes.byref(off)))
+            self.components.append({"label": lab.value, "nz": dims[0], "nx": dims[1], "ny": dims[2], "off": off.value})
+
+    def fm_apply(self, E, x, y):
+        _check("fm_apply", lib().fm_apply(self.h, float(E), _ptr(x), _ptr(y)))
+
+    def fm_apply_S(self, x, y):
+        _check("fm_apply_S", lib().fm_apply_S(self.h, _ptr(x), _ptr(y)))
+
+    def fm_set_shift(self, E):
+        _check("fm_set_shift", lib().fm_set_shift(self.h, float(E)))
+
+    def fm_precond_apply(self, x, y):
+        _check("fm_precond_apply", lib().fm_precond_apply(self.h, _ptr(x), _ptr(y)))
+
+    def fm_solve(self, E, rhs, x, allow_not_converged=False):
+        info = fm_info()
+        rc = lib().fm_solve(self.h, float(E), _ptr(rhs), _ptr(x), ctypes.byref(info))
+        _check("fm_solve", rc, (FM_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return info.as_dict()
+
+    def fm_eigs(self, shift, k, v0=None, evecs=None, allow_not_converged=False):
+        ev = (c_double * k)()
+        info = fm_info()
+        rc = lib().fm_eigs(self.h, float(shift), int(k), _ptr(v0), ev, _ptr(evecs), ctypes.byref(info))
+        _check("fm_eigs", rc, (FM_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return list(ev), info.as_dict()
+
+    def fm_eigs_host(self, shift, k, v0_host=None, evecs_host=None):
+        """Host buffers: numpy float64 arrays (v0_host length n, evecs_host k*n) or pinned torch tensors."""
+        ev = (c_double * k)()
+        info = fm_info()
+
+        def hp(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                return c_void_p(a.data_ptr())
+            return a.ctypes.data_as(c_void_p)
+        _check("fm_eigs_host", lib().fm_eigs_host(self.h, float(shift), int(k), hp(v0_host), ev, hp(evecs_host),
+                                                  ctypes.byref(info)))
+        return list(ev), info.as_dict()
+
+    def fm_stats(self):
+        a, b = c_int64(), c_int64()
+        _check("fm_stats", lib().fm_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return {"launches": a.value, "device_bytes": b.value}
+
+    def fm_destroy(self):
+        if getattr(self, "h", None):
+            lib().fm_destroy(self.h)
+            self.h = None
+
+    close = fm_destroy
+
+    def __del__(self):
+        try:
+            self.fm_destroy()
+        except Exception:
+            pass

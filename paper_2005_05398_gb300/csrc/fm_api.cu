@@ -1,0 +1,527 @@
+// The C ABI of libfm (include/fm.h): context life cycle, operator and preconditioner
+// applications, the FGMRES linear solver and the shift-invert Arnoldi eigensolver
+// (Eq. FM-lin; the paper runs IRAM (ARPACK) around a preconditioned GMRES, Section 4).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fm_dense.h"
+#include "fm_internal.h"
+
+namespace fmi {
+
+int dev_alloc(fm_ctx* c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return FM_ERR_OOM;
+  }
+  c->allocs.push_back(*p);
+  c->device_bytes += (int64_t)bytes;
+  return FM_OK;
+}
+
+int upload(fm_ctx* c, void** p, const void* host, size_t bytes) {
+  int rc = dev_alloc(c, p, bytes);
+  if (rc) return rc;
+  if (bytes) {
+    FM_CUDA(cudaMemcpyAsync(*p, host, bytes, cudaMemcpyHostToDevice, c->stream));
+    FM_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return FM_OK;
+}
+
+static double wall_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static int nrm2(fm_ctx* c, const double* v, double* out) {
+  double h = 0.0;
+  int rc = dot_many(c, v, c->N, 1, v, &h);
+  *out = std::sqrt(std::max(h, 0.0));
+  return rc;
+}
+
+// classical Gram-Schmidt with one re-orthogonalisation against V[0..nv): h += V^T w, w -= V h
+static int cgs2(fm_ctx* c, const double* V, int nv, double* w, double* h) {
+  std::vector<double> h1(nv), h2(nv);
+  int rc;
+  if ((rc = dot_many(c, V, c->N, nv, w, h1.data()))) return rc;
+  if ((rc = axpy_many(c, V, c->N, nv, h1.data(), w, -1.0))) return rc;
+  if ((rc = dot_many(c, V, c->N, nv, w, h2.data()))) return rc;
+  if ((rc = axpy_many(c, V, c->N, nv, h2.data(), w, -1.0))) return rc;
+  for (int i = 0; i < nv; ++i) h[i] = h1[i] + h2[i];
+  return FM_OK;
+}
+
+// Right-preconditioned restarted FGMRES for (H - E S) x = b (x: initial guess in, solution out).
+static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, int max_iters, int* iters_out,
+                  int* restarts_out, double* resid_out) {
+  int rc;
+  const int m = c->opts.restart_m;
+  const int64_t N = c->N;
+  double bnorm;
+  if ((rc = nrm2(c, b, &bnorm))) return rc;
+  *iters_out = 0;
+  *restarts_out = 0;
+  if (!(bnorm > 0.0)) {
+    FM_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), c->stream));
+    *resid_out = 0.0;
+    return std::isfinite(bnorm) ? FM_OK : FM_ERR_BREAKDOWN;
+  }
+  double* r = c->r;
+  if ((rc = launch_apply(c, E, x, r, false))) return rc;
+  if ((rc = axpby(c, 1.0, b, -1.0, r))) return rc;
+  double beta;
+  if ((rc = nrm2(c, r, &beta))) return rc;
+  std::vector<double> R((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 1), y(m);
+  int total = 0;
+  bool converged = false;
+  while (true) {
+    if (!std::isfinite(beta)) return FM_ERR_BREAKDOWN;
+    if (beta <= tol * bnorm) {
+      converged = true;
+      break;
+    }
+    if (total >= max_iters) break;
+    if ((rc = scale_copy(c, r, 1.0 / beta, c->V))) return rc;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m && total < max_iters; ++j) {
+      double* Vj = c->V + (int64_t)j * N;
+      double* Zj = c->Z + (int64_t)j * N;
+      if ((rc = launch_precond(c, Vj, Zj))) return rc;
+      if ((rc = launch_apply(c, E, Zj, c->w, false))) return rc;
+      if ((rc = cgs2(c, c->V, j + 1, c->w, h.data()))) return rc;
+      double hn;
+      if ((rc = nrm2(c, c->w, &hn))) return rc;
+      if (!std::isfinite(hn)) return FM_ERR_BREAKDOWN;
+      for (int i = 0; i < j; ++i) {  // previous Givens rotations
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+      }
+      const double rr = std::hypot(h[j], hn);
+      cs[j] = (rr == 0.0) ? 1.0 : h[j] / rr;
+      sn[j] = (rr == 0.0) ? 0.0 : hn / rr;
+      h[j] = rr;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) R[(size_t)i * m + j] = h[i];
+      ++total;
+      jdone = j + 1;
+      if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0) break;
+      if ((rc = scale_copy(c, c->w, 1.0 / hn, c->V + (int64_t)(j + 1) * N))) return rc;
+    }
+    for (int i = jdone - 1; i >= 0; --i) {  // R y = g
+      double s = g[i];
+      for (int k = i + 1; k < jdone; ++k) s -= R[(size_t)i * m + k] * y[k];
+      if (R[(size_t)i * m + i] == 0.0) return FM_ERR_BREAKDOWN;
+      y[i] = s / R[(size_t)i * m + i];
+    }
+    if ((rc = axpy_many(c, c->Z, N, jdone, y.data(), x, 1.0))) return rc;
+    ++*restarts_out;
+    if ((rc = launch_apply(c, E, x, r, false))) return rc;
+    if ((rc = axpby(c, 1.0, b, -1.0, r))) return rc;
+    if ((rc = nrm2(c, r, &beta))) return rc;
+  }
+  *iters_out = total;
+  *resid_out = beta / bnorm;
+  return converged ? FM_OK : FM_ERR_NOT_CONVERGED;
+}
+
+// Householder-free modified Gram-Schmidt QR of an m x k matrix (row-major), twice.
+static bool small_qr(int m, int k, std::vector<double>& Y) {
+  for (int pass = 0; pass < 2; ++pass)
+    for (int j = 0; j < k; ++j) {
+      for (int i = 0; i < j; ++i) {
+        double d = 0.0;
+        for (int r = 0; r < m; ++r) d += Y[(size_t)r * k + i] * Y[(size_t)r * k + j];
+        for (int r = 0; r < m; ++r) Y[(size_t)r * k + j] -= d * Y[(size_t)r * k + i];
+      }
+      double nr = 0.0;
+      for (int r = 0; r < m; ++r) nr += Y[(size_t)r * k + j] * Y[(size_t)r * k + j];
+      nr = std::sqrt(nr);
+      if (!(nr > 1e-14)) return false;
+      for (int r = 0; r < m; ++r) Y[(size_t)r * k + j] /= nr;
+    }
+  return true;
+}
+
+struct Ritz {
+  double theta;
+  int col;
+  bool real;
+};
+
+}  // namespace fmi
+
+using namespace fmi;
+
+extern "C" {
+
+void fm_default_opts(fm_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-12;
+  o->restart_m = 64;
+  o->max_iters = 2000;
+  o->precision = FM_PREC_FP64;
+  o->ncv = 20;
+  o->max_restarts = 50;
+  o->eig_tol = 1e-12;
+  o->z_eigs = 0;
+  o->device = 0;
+  o->stream = nullptr;
+}
+
+const char* fm_strerror(int s) {
+  switch (s) {
+    case FM_OK: return "ok";
+    case FM_ERR_ARG: return "invalid argument";
+    case FM_ERR_OOM: return "out of memory";
+    case FM_ERR_CUDA: return "CUDA runtime error";
+    case FM_ERR_NOT_CONVERGED: return "iteration limit reached without convergence";
+    case FM_ERR_BREAKDOWN: return "Krylov breakdown (zero or non-finite norm)";
+    case FM_ERR_COMPLEX_SPECTRUM: return "a 1D generalized eigenproblem has complex eigenvalues";
+    case FM_ERR_NO_SHIFT: return "preconditioner used before fm_set_shift";
+    case FM_ERR_NUMERIC: return "singular or non-finite set-up quantity";
+    default: return "unknown status";
+  }
+}
+
+void fm_destroy(fm_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->red_host) cudaFreeHost(c->red_host);
+  delete c;
+}
+
+int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_splitting* split, const fm_opts* opts,
+              fm_ctx** out) {
+  if (!out) return FM_ERR_ARG;
+  *out = nullptr;
+  if (!sys || !grids || !split || n_grids < 1) return FM_ERR_ARG;
+  fm_opts o;
+  if (opts) o = *opts;
+  else fm_default_opts(&o);
+  if (sys->J < 0 || (sys->tau != 1 && sys->tau != -1) || (sys->exch_p != 1 && sys->exch_p != -1)) return FM_ERR_ARG;
+  if (sys->identical_pair != 0 && sys->identical_pair != 12) return FM_ERR_ARG;
+  for (int i = 0; i < 3; ++i)
+    if (!(sys->mass[i] > 0.0) || !std::isfinite(sys->charge[i])) return FM_ERR_ARG;
+  if (sys->identical_pair == 12 && (sys->mass[0] != sys->mass[1] || sys->charge[0] != sys->charge[1])) return FM_ERR_ARG;
+  if (split->mode < 0 || split->mode > 2 || !(split->nu > 0) || !(split->x0 > 0) || !(split->y0 > 0) || split->vs_cut < 0)
+    return FM_ERR_ARG;
+  const int M0 = (1 - sys->tau) / 2, nM = sys->J - M0 + 1;
+  if (nM <= 0 || nM > 8) return FM_ERR_ARG;
+  if (o.z_eigs == 1 && nM != 1) return FM_ERR_ARG;
+  if (o.restart_m < 1 || o.restart_m > 256 || o.max_iters < 1 || !(o.tol > 0) || o.ncv < 3 || o.ncv > 64 ||
+      o.max_restarts < 0 || !(o.eig_tol > 0) || (o.precision != 0 && o.precision != 1))
+    return FM_ERR_ARG;
+  fm_ctx* c = new fm_ctx();
+  c->sys = *sys;
+  c->split = *split;
+  c->opts = o;
+  c->device = o.device;
+  c->stream = (cudaStream_t)o.stream;
+  c->M0 = M0;
+  c->nM = nM;
+  for (int i = 0; i < nM; ++i) c->Mps.push_back(M0 + i);
+  int rc = FM_OK;
+  auto fail = [&](int e) {
+    fm_destroy(c);
+    return e;
+  };
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(FM_ERR_CUDA);
+  if ((rc = kernels_init(c))) return fail(rc);
+  if ((rc = setup_host(c, grids, n_grids))) return fail(rc);
+  const int64_t N = c->N;
+  const int m = o.restart_m;
+  c->red_blocks = 2 * 152;
+  if ((rc = dev_alloc(c, (void**)&c->P, N * 8)) || (rc = dev_alloc(c, (void**)&c->Q, N * 8)) ||
+      (rc = dev_alloc(c, (void**)&c->R, N * 8)) || (rc = dev_alloc(c, (void**)&c->t64, N * 8)) ||
+      (rc = dev_alloc(c, (void**)&c->u64, N * 8)) || (rc = dev_alloc(c, (void**)&c->t32, N * 4)) ||
+      (rc = dev_alloc(c, (void**)&c->u32, N * 4)) || (rc = dev_alloc(c, (void**)&c->V, (size_t)(m + 1) * N * 8)) ||
+      (rc = dev_alloc(c, (void**)&c->Z, (size_t)std::max(m, o.ncv) * N * 8)) || (rc = dev_alloc(c, (void**)&c->w, N * 8)) ||
+      (rc = dev_alloc(c, (void**)&c->r, N * 8)) ||
+      (rc = dev_alloc(c, (void**)&c->red, ((size_t)c->red_blocks * 256 + 8192) * 8)) ||
+      (rc = dev_alloc(c, (void**)&c->AV, (size_t)(o.ncv + 1) * N * 8)) ||
+      (rc = dev_alloc(c, (void**)&c->tmpN, N * 8)) || (rc = dev_alloc(c, (void**)&c->tmpN2, N * 8)) ||
+      (rc = dev_alloc(c, (void**)&c->tmpN3, N * 8)))
+    return fail(rc);
+  if (cudaMallocHost((void**)&c->red_host, 8192 * 8) != cudaSuccess) return fail(FM_ERR_OOM);
+  c->m_alloc = m;
+  c->ncv_alloc = o.ncv;
+  *out = c;
+  return FM_OK;
+}
+
+int fm_size(const fm_ctx* c, int64_t* n, int* ncomp, int* nM) {
+  if (!c) return FM_ERR_ARG;
+  if (n) *n = c->N;
+  if (ncomp) *ncomp = (int)c->comps.size();
+  if (nM) *nM = c->nM;
+  return FM_OK;
+}
+
+int fm_component(const fm_ctx* c, int comp, int* label, int dims[3], int64_t* offset) {
+  if (!c || comp < 0 || comp >= (int)c->comps.size()) return FM_ERR_ARG;
+  const auto& cp = c->comps[comp];
+  if (label) *label = cp.label;
+  if (dims) {
+    dims[0] = cp.nz;
+    dims[1] = cp.nx;
+    dims[2] = cp.ny;
+  }
+  if (offset) *offset = cp.off;
+  return FM_OK;
+}
+
+int fm_stats(const fm_ctx* c, int64_t* launches, int64_t* bytes) {
+  if (!c) return FM_ERR_ARG;
+  if (launches) *launches = c->launches;
+  if (bytes) *bytes = c->device_bytes;
+  return FM_OK;
+}
+
+int fm_apply(fm_ctx* c, double E, const double* x, double* y) {
+  if (!c || !x || !y || x == y || !std::isfinite(E)) return FM_ERR_ARG;
+  FM_CUDA(cudaSetDevice(c->device));
+  return launch_apply(c, E, x, y, false);
+}
+
+int fm_apply_S(fm_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y || x == y) return FM_ERR_ARG;
+  FM_CUDA(cudaSetDevice(c->device));
+  return launch_apply(c, 0.0, x, y, true);
+}
+
+int fm_set_shift(fm_ctx* c, double Estar) {
+  if (!c || !std::isfinite(Estar)) return FM_ERR_ARG;
+  FM_CUDA(cudaSetDevice(c->device));
+  return setup_shift(c, Estar);
+}
+
+int fm_precond_apply(fm_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y || x == y) return FM_ERR_ARG;
+  if (!c->have_shift) return FM_ERR_NO_SHIFT;
+  FM_CUDA(cudaSetDevice(c->device));
+  return launch_precond(c, x, y);
+}
+
+int fm_solve(fm_ctx* c, double E, const double* rhs, double* x, fm_info* info) {
+  if (!c || !rhs || !x || rhs == x || !std::isfinite(E)) return FM_ERR_ARG;
+  FM_CUDA(cudaSetDevice(c->device));
+  const double t0 = wall_ms();
+  int rc;
+  if (!c->have_shift || c->Estar != E)
+    if ((rc = setup_shift(c, E))) return rc;
+  int it = 0, rs = 0;
+  double res = 0.0;
+  rc = fgmres(c, E, rhs, x, c->opts.tol, c->opts.max_iters, &it, &rs, &res);
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = it;
+    info->restarts = rs;
+    info->resid = res;
+    info->converged = (rc == FM_OK);
+    info->ms = wall_ms() - t0;
+  }
+  return rc;
+}
+
+int fm_eigs(fm_ctx* c, double shift, int k, const double* v0, double* evals, double* evecs, fm_info* info) {
+  if (!c || !evals || k < 1 || !std::isfinite(shift)) return FM_ERR_ARG;
+  const int m = c->ncv_alloc;
+  if (m < k + 2) return FM_ERR_ARG;
+  FM_CUDA(cudaSetDevice(c->device));
+  const double t0 = wall_ms();
+  const int64_t N = c->N;
+  int rc;
+  if (!c->have_shift || c->Estar != shift)
+    if ((rc = setup_shift(c, shift))) return rc;
+  double* V = c->AV;
+  if (v0) FM_CUDA(cudaMemcpyAsync(V, v0, N * 8, cudaMemcpyDeviceToDevice, c->stream));
+  else if ((rc = fill_normal(c, V, 20050539ull))) return rc;
+  double nv;
+  if ((rc = nrm2(c, V, &nv))) return rc;
+  if (!(nv > 0.0) || !std::isfinite(nv)) return FM_ERR_ARG;
+  if ((rc = scale_copy(c, V, 1.0 / nv, V))) return rc;
+  std::vector<double> G((size_t)(m + 1) * m, 0.0);  // projected matrix, row-major (m+1) x m
+  int kcur = 0, restarts = 0, inner = 0, ops = 0, nsz = 0;
+  bool converged = false;
+  std::vector<Ritz> best;
+  std::vector<double> Y;  // eigenvectors of the projected matrix (nsz x nsz)
+  double max_res = 0.0;
+  while (true) {
+    bool done = false;
+    for (int j = kcur; j < m; ++j) {
+      double* Vj = V + (int64_t)j * N;
+      double* w = V + (int64_t)(j + 1) * N;
+      if ((rc = launch_apply(c, 0.0, Vj, c->tmpN, true))) return rc;  // S v_j
+      FM_CUDA(cudaMemsetAsync(w, 0, N * 8, c->stream));
+      int it = 0, rs = 0;
+      double res = 0.0;
+      rc = fgmres(c, shift, c->tmpN, w, c->opts.tol, c->opts.max_iters, &it, &rs, &res);
+      inner += it;
+      ++ops;
+      if (rc != FM_OK && rc != FM_ERR_NOT_CONVERGED) return rc;
+      std::vector<double> h(j + 1);
+      if ((rc = cgs2(c, V, j + 1, w, h.data()))) return rc;
+      double hn;
+      if ((rc = nrm2(c, w, &hn))) return rc;
+      if (!std::isfinite(hn)) return FM_ERR_BREAKDOWN;
+      for (int i = 0; i <= j; ++i) G[(size_t)i * m + j] = h[i];
+      G[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0)
+        if ((rc = scale_copy(c, w, 1.0 / hn, w))) return rc;
+      nsz = j + 1;
+      if (nsz < k) continue;
+      // Ritz pairs of the nsz x nsz projected matrix
+      std::vector<double> A((size_t)nsz * nsz), re(nsz), im(nsz);
+      Y.assign((size_t)nsz * nsz, 0.0);
+      for (int r = 0; r < nsz; ++r)
+        for (int q = 0; q < nsz; ++q) A[(size_t)r * nsz + q] = G[(size_t)r * m + q];
+      if (fmh::eig_general(nsz, A.data(), re.data(), im.data(), Y.data()) < 0) return FM_ERR_NUMERIC;
+      std::vector<int> order(nsz);
+      for (int i = 0; i < nsz; ++i) order[i] = i;
+      std::sort(order.begin(), order.end(),
+                [&](int a, int b) { return std::hypot(re[a], im[a]) > std::hypot(re[b], im[b]); });
+      best.clear();
+      bool ok = true;
+      max_res = 0.0;
+      for (int t = 0; t < nsz && (int)best.size() < nsz; ++t) {
+        const int e = order[t];
+        Ritz rz{re[e], e, im[e] == 0.0};
+        best.push_back(rz);
+        if ((int)best.size() <= k) {
+          if (!rz.real) {
+            ok = false;
+            continue;
+          }
+          const double resid = std::fabs(hn * Y[(size_t)(nsz - 1) * nsz + e]) / std::max(std::fabs(rz.theta), 1e-300);
+          max_res = std::max(max_res, resid);
+          if (resid > c->opts.eig_tol) ok = false;
+        }
+      }
+      if (ok || hn == 0.0) {
+        converged = ok;
+        done = true;
+        break;
+      }
+    }
+    if (done || restarts >= c->opts.max_restarts) break;
+    // thick restart: keep the real Ritz vectors of the kk largest |theta|
+    const int kk = std::min(m - 1, std::max(k, (m + k) / 2));
+    std::vector<int> keep;
+    for (const auto& rz : best)
+      if (rz.real && (int)keep.size() < kk) keep.push_back(rz.col);
+    const int nk = (int)keep.size();
+    if (nk < 1) break;
+    std::vector<double> Qy((size_t)m * nk);
+    for (int r = 0; r < m; ++r)
+      for (int q = 0; q < nk; ++q) Qy[(size_t)r * nk + q] = Y[(size_t)r * m + keep[q]];
+    if (!small_qr(m, nk, Qy)) break;
+    // T = Qy^T G Qy, b = g_{m+1,m} Qy[m-1, :]
+    std::vector<double> GQ((size_t)m * nk, 0.0), T((size_t)nk * nk, 0.0);
+    for (int r = 0; r < m; ++r)
+      for (int q = 0; q < nk; ++q) {
+        double s = 0.0;
+        for (int t = 0; t < m; ++t) s += G[(size_t)r * m + t] * Qy[(size_t)t * nk + q];
+        GQ[(size_t)r * nk + q] = s;
+      }
+    for (int a = 0; a < nk; ++a)
+      for (int q = 0; q < nk; ++q) {
+        double s = 0.0;
+        for (int r = 0; r < m; ++r) s += Qy[(size_t)r * nk + a] * GQ[(size_t)r * nk + q];
+        T[(size_t)a * nk + q] = s;
+      }
+    const double gl = G[(size_t)m * m + (m - 1)];
+    if ((rc = combine(c, V, N, m, Qy.data(), nk, c->Z, N))) return rc;  // new basis into Z (scratch)
+    FM_CUDA(cudaMemcpyAsync(V, c->Z, (size_t)nk * N * 8, cudaMemcpyDeviceToDevice, c->stream));
+    FM_CUDA(cudaMemcpyAsync(V + (int64_t)nk * N, V + (int64_t)m * N, N * 8, cudaMemcpyDeviceToDevice, c->stream));
+    std::fill(G.begin(), G.end(), 0.0);
+    for (int a = 0; a < nk; ++a)
+      for (int q = 0; q < nk; ++q) G[(size_t)a * m + q] = T[(size_t)a * nk + q];
+    for (int q = 0; q < nk; ++q) G[(size_t)nk * m + q] = gl * Qy[(size_t)(m - 1) * nk + q];
+    kcur = nk;
+    ++restarts;
+  }
+  if (nsz < k || (int)best.size() < k) return FM_ERR_NOT_CONVERGED;
+  // eigenvectors c = V y, energies E = shift + 1/theta
+  std::vector<double> Ek(k);
+  std::vector<double> res_k(k, 0.0);
+  for (int i = 0; i < k; ++i) {
+    if (!best[i].real) return FM_ERR_NOT_CONVERGED;
+    Ek[i] = shift + 1.0 / best[i].theta;
+  }
+  std::vector<int> ord(k);
+  for (int i = 0; i < k; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return std::fabs(Ek[a] - shift) < std::fabs(Ek[b] - shift); });
+  for (int ii = 0; ii < k; ++ii) {
+    const int i = ord[ii];
+    std::vector<double> yv(nsz);
+    for (int r = 0; r < nsz; ++r) yv[r] = Y[(size_t)r * nsz + best[i].col];
+    double* cvec = c->tmpN3;
+    if ((rc = combine(c, V, N, nsz, yv.data(), 1, cvec, N))) return rc;
+    double nr, mx;
+    if ((rc = nrm2(c, cvec, &nr))) return rc;
+    if ((rc = absmax(c, cvec, &mx))) return rc;
+    const double sc = (mx < 0 ? -1.0 : 1.0) / nr;
+    if ((rc = scale_copy(c, cvec, sc, cvec))) return rc;
+    // eigen-residual ||H c - E S c|| / ||S c|| in float64
+    if ((rc = launch_apply(c, Ek[i], cvec, c->tmpN, false))) return rc;
+    if ((rc = launch_apply(c, 0.0, cvec, c->tmpN2, true))) return rc;
+    double rn, sn;
+    if ((rc = nrm2(c, c->tmpN, &rn)) || (rc = nrm2(c, c->tmpN2, &sn))) return rc;
+    res_k[ii] = rn / sn;
+    evals[ii] = Ek[i];
+    if (evecs) FM_CUDA(cudaMemcpyAsync(evecs + (int64_t)ii * N, cvec, N * 8, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = inner;
+    info->restarts = restarts;
+    info->op_applies = ops;
+    info->converged = converged;
+    double mr = 0.0;
+    for (double r : res_k) mr = std::max(mr, r);
+    info->resid = mr;
+    info->ms = wall_ms() - t0;
+  }
+  return converged ? FM_OK : FM_ERR_NOT_CONVERGED;
+}
+
+int fm_eigs_host(fm_ctx* c, double shift, int k, const double* v0_host, double* evals, double* evecs_host, fm_info* info) {
+  if (!c || !evals || k < 1) return FM_ERR_ARG;
+  FM_CUDA(cudaSetDevice(c->device));
+  const int64_t N = c->N;
+  int rc;
+  if (evecs_host && c->evec_stage_k < k) {
+    if ((rc = dev_alloc(c, (void**)&c->evec_stage, (size_t)k * N * 8))) return rc;
+    c->evec_stage_k = k;
+  }
+  const double* v0d = nullptr;
+  if (v0_host) {
+    FM_CUDA(cudaMemcpyAsync(c->tmpN3, v0_host, N * 8, cudaMemcpyHostToDevice, c->stream));
+    v0d = c->tmpN3;
+  }
+  rc = fm_eigs(c, shift, k, v0d, evals, evecs_host ? c->evec_stage : nullptr, info);
+  if (rc != FM_OK && rc != FM_ERR_NOT_CONVERGED) return rc;
+  if (evecs_host)
+    FM_CUDA(cudaMemcpyAsync(evecs_host, c->evec_stage, (size_t)k * N * 8, cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  return rc;
+}
+
+}  // extern "C"

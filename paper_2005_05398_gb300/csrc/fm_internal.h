@@ -1,0 +1,152 @@
+// Internal structures of libfm (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fm.h"
+
+namespace fmi {
+
+// One spline axis (Section 3.1): nodes, collocation points and, per collocation
+// point, the four nonzero basis functions as taps base+t, t = 0..3 (a tap outside
+// [0, n) carries the value 0).
+struct Axis {
+  int kind = 0, nint = 0, n = 0;
+  double a = 0, b = 0;
+  bool dirichlet = false;
+  std::vector<double> nodes, pts;
+  std::vector<int> base;               // per point
+  std::vector<double> S, D1, D2;       // per point, 4 values each
+  void build(int kind, int nint, double a, double b, bool dirichlet);
+  int locate(double p) const;          // interval m with nodes[m] <= p <= nodes[m+1]
+  // taps of an arbitrary point (values, first derivatives or second derivatives)
+  void eval(double p, int deriv, int* base_out, double v[4]) const;
+};
+
+// Device-side 1D tap tables of one axis.
+struct AxisDev {
+  int* base = nullptr;
+  double* S = nullptr;   // [n][4]
+  double* D1 = nullptr;
+  double* D2 = nullptr;
+  double* pts = nullptr;
+};
+
+struct Source {          // one V^(s) coupling source of a component (Eq. FM-pre right side)
+  int beta = 0;          // particle label of the source pair
+  int src = 0;           // index of the solved component whose expansion is evaluated
+  double zsign = 1.0;    // -1: psi_2(x, y, z) = p (-1)^{M'} psi_1(x, y, -z) (Eq. 2-sym-part)
+  bool sym = false;
+};
+
+struct Comp {
+  int label = 0;                 // particle label alpha
+  Axis ax, ay, az;
+  int nx = 0, ny = 0, nz = 0;
+  int64_t npts = 0, off = 0;     // points per M' block, offset in the vector
+  double Rx = 0, Ry = 0;
+  std::vector<Source> sources;
+  // device tables
+  AxisDev dx, dy, dz;
+  double* W = nullptr;           // [nz][nx][ny] left-hand potential V_a + sum V^(l)_b (Eq. FM-pre)
+  // coupling tables: n_act active points, per (source s): taps and weights
+  int n_act = 0;
+  int* act_pt = nullptr;         // [n_act] point index (k*nx + i)*ny + j
+  int* cpl_base = nullptr;       // [ns][3][n_act]  (z, x, y tap bases)
+  double* cpl_val = nullptr;     // [ns][12][n_act] (Sz[4], Sx[4], Sy[4])
+  double* cpl_w = nullptr;       // [ns][nM*nM][n_act] weight of (M', M'')
+  // preconditioner, E-independent
+  double* Wz = nullptr;          // [nM][nz][nz]
+  double* Wzb = nullptr;         // [nM][nz][nz]
+  double* Wx = nullptr;          // [nl][nx][nx], l = M0 .. J + nz - 1
+  double* Wxb = nullptr;
+  float* Wz32 = nullptr; float* Wzb32 = nullptr; float* Wx32 = nullptr; float* Wxb32 = nullptr;
+  std::vector<double> Lz;        // [nM][nz] computed z eigenvalues
+  std::vector<double> Lx;        // [nl][nx]
+  int nl = 0;
+  // preconditioner, E-dependent banded y systems: per l a group of nx lines
+  std::vector<int> chain_lo, chain_n;   // per l: first iM and length of the M' chain
+  int* d_chain_lo = nullptr; int* d_chain_n = nullptr;
+  int64_t* d_band_off = nullptr; int64_t* d_lmul_off = nullptr; int64_t* d_piv_off = nullptr;
+  std::vector<int64_t> band_off;        // per l: offset (in elements) of its group in yU / yL
+  std::vector<int64_t> piv_off;
+  int64_t band_total = 0, lmul_total = 0, piv_total = 0;
+  double* yU = nullptr;          // per l: [n][kl+ku+1][nx]
+  double* yL = nullptr;          // per l: [n][kl][nx]
+  unsigned char* yP = nullptr;   // per l: [n][nx] pivot offsets
+  float* yU32 = nullptr; float* yL32 = nullptr;
+  std::vector<int64_t> lmul_off;
+};
+
+}  // namespace fmi
+
+struct fm_ctx {
+  fm_system sys{};
+  fm_splitting split{};
+  fm_opts opts{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int M0 = 0, nM = 0;
+  std::vector<int> Mps;
+  std::vector<fmi::Comp> comps;
+  int64_t N = 0;
+  double mu_pair[3]{}, mu_rel[3]{};
+  // preconditioner state
+  bool have_shift = false;
+  double Estar = 0.0;
+  // workspace
+  double* P = nullptr;           // [N] y/x-pass planes for the apply (S_x S_y c)
+  double* Q = nullptr;           // [N] (D_x S_y c)
+  double* R = nullptr;           // [N] (S_x D_y c)
+  double* t64 = nullptr;         // [N] preconditioner stage buffer
+  double* u64 = nullptr;
+  float* t32 = nullptr;
+  float* u32 = nullptr;
+  int m_alloc = 0;
+  double* V = nullptr;           // FGMRES basis [(m+1)][N]
+  double* Z = nullptr;           // FGMRES preconditioned directions [m][N]
+  double* w = nullptr;           // [N]
+  double* r = nullptr;           // [N]
+  double* red = nullptr;         // reduction scratch
+  double* red_host = nullptr;    // pinned
+  int red_blocks = 0;
+  // eigen workspace
+  int ncv_alloc = 0;
+  double* AV = nullptr;          // Arnoldi basis [(ncv+1)][N]
+  double* tmpN = nullptr;        // [N]
+  double* tmpN2 = nullptr;
+  double* tmpN3 = nullptr;
+  double* evec_stage = nullptr;  // fm_eigs_host staging (k vectors)
+  int evec_stage_k = 0;
+  int64_t launches = 0;
+  int64_t device_bytes = 0;
+  std::vector<void*> allocs;
+};
+
+// helpers shared by the translation units
+namespace fmi {
+int dev_alloc(fm_ctx* c, void** p, size_t bytes);
+int upload(fm_ctx* c, void** p, const void* host, size_t bytes);
+int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids);       // grids, tables, coupling, z/x decompositions
+int setup_shift(fm_ctx* c, double Estar);                            // banded y systems
+// kernels (fm_kernels.cu)
+int launch_apply(fm_ctx* c, double E, const double* x, double* y, bool only_S);
+int launch_precond(fm_ctx* c, const double* x, double* y);
+int dot_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, double* h_host);
+int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double sign);
+int scale_copy(fm_ctx* c, const double* x, double a, double* y);   // y = a x
+int axpby(fm_ctx* c, double a, const double* x, double b, double* y);  // y = a x + b y
+int fill_normal(fm_ctx* c, double* x, uint64_t seed);
+int combine(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* Q_host, int nc, double* out, int64_t ldo);
+int absmax(fm_ctx* c, const double* x, double* val);
+int kernels_init(fm_ctx* c);
+}  // namespace fmi
+
+#define FM_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return FM_ERR_CUDA;          \
+  } while (0)

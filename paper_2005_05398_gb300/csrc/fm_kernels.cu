@@ -1,0 +1,671 @@
+// CUDA kernels of libfm (sm_103a).
+//
+//  * operator apply y = (H - E S) x (Eq. FM-lin; H from Eq. FM-pre, storage idea of
+//    Eq. l-form): sum-factorised banded contractions, y/x pass then z pass with the
+//    pointwise coefficients and the M' +- 1 couplings fused;
+//  * the V^(s) coupling term (Eqs. r-form, s-rot): a gather of the source
+//    component's spline coefficients at the rotated collocation points;
+//  * the tensor-trick preconditioner (Eq. prec-2): z and x mode products and the
+//    banded y solves that replace the y eigen-transforms and the tridiagonal M'
+//    chains (the same operator, factorised by banded LU);
+//  * deterministic Krylov reductions (fixed grid, fixed reduction order).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <vector>
+
+#include "fm_internal.h"
+
+namespace {
+
+constexpr int kMaxM = 8;  // largest n_M handled by the register arrays (J <= 7)
+
+// ---------------------------------------------------------------------------
+// apply, pass 1: for one (component, M', z-dof k) plane c[i][j] (n_x x n_y) and a tile
+// of TX x-collocation points: P = (S_x (x) S_y) c, Q = (D2_x (x) S_y) c, R = (S_x (x) D2_y) c.
+// ---------------------------------------------------------------------------
+template <int TX>
+__global__ void __launch_bounds__(256) k_apply_xy(const double* __restrict__ c, double* __restrict__ P,
+                                                  double* __restrict__ Q, double* __restrict__ R, int nx, int ny,
+                                                  const int* __restrict__ bx, const double* __restrict__ Sx,
+                                                  const double* __restrict__ D2x, const int* __restrict__ by,
+                                                  const double* __restrict__ Sy, const double* __restrict__ D2y,
+                                                  bool only_S) {
+  extern __shared__ double sm[];
+  const int rows = TX + 2;
+  double* cs = sm;                 // [rows][ny]
+  double* As = sm + rows * ny;     // [rows][ny]  S_y pass
+  double* Bs = As + rows * ny;     // [rows][ny]  D2_y pass
+  const int64_t plane = (int64_t)blockIdx.y * nx * ny;
+  const int xi0 = blockIdx.x * TX;
+  const int r0 = xi0 - 1;
+  for (int idx = threadIdx.x; idx < rows * ny; idx += blockDim.x) {
+    const int r = r0 + idx / ny;
+    cs[idx] = (r >= 0 && r < nx) ? c[plane + (int64_t)r * ny + (idx % ny)] : 0.0;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < rows * ny; idx += blockDim.x) {
+    const int r = idx / ny, eta = idx % ny;
+    const int b = by[eta];
+    double a = 0.0, d = 0.0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int j = b + t;
+      if (j >= 0 && j < ny) {
+        const double v = cs[r * ny + j];
+        a = fma(Sy[eta * 4 + t], v, a);
+        d = fma(D2y[eta * 4 + t], v, d);
+      }
+    }
+    As[idx] = a;
+    Bs[idx] = d;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < TX * ny; idx += blockDim.x) {
+    const int xi = xi0 + idx / ny, eta = idx % ny;
+    if (xi >= nx) continue;
+    const int b = bx[xi] - r0;
+    double p = 0.0, q = 0.0, rr = 0.0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int lr = b + t;
+      if (lr >= 0 && lr < rows) {
+        const double a = As[lr * ny + eta];
+        p = fma(Sx[xi * 4 + t], a, p);
+        q = fma(D2x[xi * 4 + t], a, q);
+        rr = fma(Sx[xi * 4 + t], Bs[lr * ny + eta], rr);
+      }
+    }
+    const int64_t o = plane + (int64_t)xi * ny + eta;
+    P[o] = p;
+    if (!only_S) {
+      Q[o] = q;
+      R[o] = rr;
+    }
+  }
+}
+
+struct ZPassArgs {
+  const double* P;
+  const double* Q;
+  const double* R;
+  double* y;
+  const double* W;       // [nz][nx][ny]
+  const int* bz;
+  const double* Sz;
+  const double* D1z;
+  const double* D2z;
+  const double* zp;
+  const double* xp;
+  const double* yp;
+  int nx, ny, nz, nM, M0, J;
+  double E;
+  double lamp[kMaxM];    // lambda-hat^{J, M'} for M'+1 coupling
+  double lamm[kMaxM];    // lambda-hat^{J, -M'} for M'-1 coupling
+};
+
+// apply, pass 2: one thread per output point (M', zeta, xi, eta) of a component.
+__global__ void __launch_bounds__(256) k_apply_z(ZPassArgs a, bool only_S) {
+  const int64_t npts = (int64_t)a.nz * a.nx * a.ny;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= npts * a.nM) return;
+  const int iM = (int)(gid / npts);
+  const int64_t pt = gid - (int64_t)iM * npts;
+  const int zeta = (int)(pt / ((int64_t)a.nx * a.ny));
+  const int64_t xy = pt - (int64_t)zeta * a.nx * a.ny;
+  const int b = a.bz[zeta];
+  const int64_t blk = (int64_t)iM * npts;
+  double U = 0, Uz = 0, Uzz = 0, Uxx = 0, Uyy = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int k = b + t;
+    if (k >= 0 && k < a.nz) {
+      const int64_t o = blk + (int64_t)k * a.nx * a.ny + xy;
+      const double p = a.P[o];
+      U = fma(a.Sz[zeta * 4 + t], p, U);
+      if (!only_S) {
+        Uz = fma(a.D1z[zeta * 4 + t], p, Uz);
+        Uzz = fma(a.D2z[zeta * 4 + t], p, Uzz);
+        Uxx = fma(a.Sz[zeta * 4 + t], a.Q[o], Uxx);
+        Uyy = fma(a.Sz[zeta * 4 + t], a.R[o], Uyy);
+      }
+    }
+  }
+  if (only_S) {
+    a.y[gid] = U;
+    return;
+  }
+  const int xi = (int)(xy / a.ny), eta = (int)(xy - (int64_t)xi * a.ny);
+  const double x = a.xp[xi], y = a.yp[eta], z = a.zp[zeta];
+  const double ix2 = 1.0 / (x * x), iy2 = 1.0 / (y * y);
+  const double q = ix2 + iy2;
+  const int Mp = a.M0 + iM;
+  const double jm = (double)(a.J * (a.J + 1) - 2 * Mp * Mp);
+  const double C = q * (double)(Mp * (Mp + 1)) + jm * iy2 + a.W[pt] - a.E;
+  double out = -Uyy - Uxx - q * (1.0 - z * z) * Uzz + 2.0 * (Mp + 1) * z * q * Uz + C * U;
+  if (iM + 1 < a.nM) {  // lambda-hat^{J,M'}/y^2 [-(1-z^2) d/dz + 2(M'+1) z] psi_{M'+1}
+    double Up = 0, Uzp = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int k = b + t;
+      if (k >= 0 && k < a.nz) {
+        const double p = a.P[blk + npts + (int64_t)k * a.nx * a.ny + xy];
+        Up = fma(a.Sz[zeta * 4 + t], p, Up);
+        Uzp = fma(a.D1z[zeta * 4 + t], p, Uzp);
+      }
+    }
+    out += a.lamp[iM] * iy2 * (-(1.0 - z * z) * Uzp + 2.0 * (Mp + 1) * z * Up);
+  }
+  if (iM >= 1) {  // lambda-hat^{J,-M'}/y^2 d/dz psi_{M'-1}
+    double Uzm = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int k = b + t;
+      if (k >= 0 && k < a.nz) Uzm = fma(a.D1z[zeta * 4 + t], a.P[blk - npts + (int64_t)k * a.nx * a.ny + xy], Uzm);
+    }
+    out += a.lamm[iM] * iy2 * Uzm;
+  }
+  a.y[gid] = out;
+}
+
+struct CouplingArgs {
+  const double* x;      // full input vector
+  double* y;            // full output vector (accumulated)
+  int64_t row_off;      // offset of the target component
+  int64_t npts;         // points per M' block of the target component
+  int n_act;
+  const int* act_pt;
+  int ns;
+  const int* base[3];   // per source: [3][n_act]
+  const double* val[3]; // per source: [12][n_act]
+  const double* w[3];   // per source: [nM*nM][n_act]
+  int64_t src_off[3];
+  int64_t src_npts[3];
+  int snx[3], sny[3], snz[3];
+  int nM;
+};
+
+// V^(s) coupling: one thread per active collocation point of a component.
+__global__ void __launch_bounds__(128) k_apply_coupling(CouplingArgs a) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.n_act) return;
+  double acc[kMaxM];
+#pragma unroll
+  for (int m = 0; m < kMaxM; ++m) acc[m] = 0.0;
+  for (int s = 0; s < a.ns; ++s) {
+    const int bz = a.base[s][p], bx = a.base[s][a.n_act + p], by = a.base[s][2 * a.n_act + p];
+    double vz[4], vx[4], vy[4];
+    int iz[4], ix[4], iy[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      vz[t] = a.val[s][(0 + t) * (int64_t)a.n_act + p];
+      vx[t] = a.val[s][(4 + t) * (int64_t)a.n_act + p];
+      vy[t] = a.val[s][(8 + t) * (int64_t)a.n_act + p];
+      iz[t] = min(max(bz + t, 0), a.snz[s] - 1);
+      ix[t] = min(max(bx + t, 0), a.snx[s] - 1);
+      iy[t] = min(max(by + t, 0), a.sny[s] - 1);
+    }
+    for (int jM = 0; jM < a.nM; ++jM) {
+      const double* cb = a.x + a.src_off[s] + (int64_t)jM * a.src_npts[s];
+      double sz = 0.0;
+#pragma unroll
+      for (int tz = 0; tz < 4; ++tz) {
+        double sx = 0.0;
+#pragma unroll
+        for (int tx = 0; tx < 4; ++tx) {
+          const double* row = cb + ((int64_t)iz[tz] * a.snx[s] + ix[tx]) * a.sny[s];
+          double sy = vy[0] * row[iy[0]];
+          sy = fma(vy[1], row[iy[1]], sy);
+          sy = fma(vy[2], row[iy[2]], sy);
+          sy = fma(vy[3], row[iy[3]], sy);
+          sx = fma(vx[tx], sy, sx);
+        }
+        sz = fma(vz[tz], sx, sz);
+      }
+      for (int iM = 0; iM < a.nM; ++iM)
+        acc[iM] = fma(a.w[s][(int64_t)(iM * a.nM + jM) * a.n_act + p], sz, acc[iM]);
+    }
+  }
+  const int pt = a.act_pt[p];
+  for (int iM = 0; iM < a.nM; ++iM) a.y[a.row_off + (int64_t)iM * a.npts + pt] += acc[iM];
+}
+
+// ---------------------------------------------------------------------------
+// preconditioner: z mode product  out[l][p] = sum_k W[l][k] in[k][p] for one (component, M')
+// ---------------------------------------------------------------------------
+template <typename TI, typename TO, typename TW>
+__global__ void __launch_bounds__(128) k_zmix(const TW* __restrict__ Wall, const TI* __restrict__ in,
+                                              TO* __restrict__ out, int nz, int64_t nxy, int64_t comp_off) {
+  extern __shared__ unsigned char smraw[];
+  TW* Ws = reinterpret_cast<TW*>(smraw);  // [nz][nz]
+  const int iM = blockIdx.y;
+  const TW* W = Wall + (int64_t)iM * nz * nz;
+  for (int i = threadIdx.x; i < nz * nz; i += blockDim.x) Ws[i] = W[i];
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nxy) return;
+  const int64_t base = comp_off + (int64_t)iM * nz * nxy + p;
+  constexpr int CH = 8;
+  for (int l0 = 0; l0 < nz; l0 += CH) {
+    TW acc[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) acc[u] = 0;
+    for (int k = 0; k < nz; ++k) {
+      const TW v = (TW)in[base + (int64_t)k * nxy];
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (l0 + u < nz) acc[u] = fma(Ws[(l0 + u) * nz + k], v, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (l0 + u < nz) out[base + (int64_t)(l0 + u) * nxy] = (TO)acc[u];
+  }
+}
+
+// x mode product on every (M', z-mode) slab: out[i][j] = sum_i' W_x^{l}[i][i'] in[i'][j], l = M' + k.
+// Classic 64x64 smem tiling, 256 threads, 4x4 outputs per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_xmix(const T* __restrict__ Wall, const T* __restrict__ in, T* __restrict__ out,
+                                              int nx, int ny, int nz, int64_t comp_off, int M0) {
+  constexpr int BT = 64, BK = 16;
+  __shared__ T As[BK][BT + 1];
+  __shared__ T Bs[BK][BT + 1];
+  const int slab = blockIdx.z;  // iM * nz + k
+  const int iM = slab / nz, k = slab % nz;
+  const int l = M0 + iM + k;     // l index from M0
+  const T* W = Wall + (int64_t)(l - M0) * nx * nx;
+  const int64_t so = comp_off + (int64_t)slab * nx * ny;
+  const int row0 = blockIdx.y * BT, col0 = blockIdx.x * BT;
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  for (int k0 = 0; k0 < nx; k0 += BK) {
+    for (int e = threadIdx.x; e < BK * BT; e += 256) {
+      const int kk = e % BK, rr = e / BK;  // A tile: W[row0+rr][k0+kk]
+      const int gr = row0 + rr, gk = k0 + kk;
+      As[kk][rr] = (gr < nx && gk < nx) ? W[(int64_t)gr * nx + gk] : (T)0;
+      const int cc = e % BT, kb = e / BT;  // B tile: in[k0+kb][col0+cc]
+      const int gk2 = k0 + kb, gc = col0 + cc;
+      Bs[kb][cc] = (gk2 < nx && gc < ny) ? in[so + (int64_t)gk2 * ny + gc] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tr + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tc + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gr = row0 + tr + 16 * i, gc = col0 + tc + 16 * j;
+      if (gr < nx && gc < ny) out[so + (int64_t)gr * ny + gc] = acc[i][j];
+    }
+}
+
+// banded y solves: one thread per (l, i_x) line of a component; the right-hand side is
+// the M'-chain of y-vectors t[iM][l - M'][i_x][:] interleaved as r = j * nc + c.
+struct YArgs {
+  int nx, ny, nz, M0, nl;
+  int64_t comp_off;
+  const int* chain_lo;   // [nl]
+  const int* chain_n;    // [nl]
+  const int64_t* band_off;  // [nl] offset into U
+  const int64_t* lmul_off;  // [nl] offset into L
+  const int64_t* piv_off;   // [nl] offset into P
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_ysolve(YArgs a, const T* __restrict__ U, const T* __restrict__ L,
+                                                const unsigned char* __restrict__ Pv, T* __restrict__ t) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int il = blockIdx.y;
+  if (ix >= a.nx) return;
+  const int nc = a.chain_n[il], lo = a.chain_lo[il];
+  const int n = nc * a.ny;
+  const int kl = (nc == 1) ? 2 : 2 * nc + 1;
+  const int w = 2 * kl + 1;  // kl + ku + 1 with ku = kl
+  const T* Ub = U + a.band_off[il];
+  const T* Lb = L + a.lmul_off[il];
+  const unsigned char* Pb = Pv + a.piv_off[il];
+  const int l = a.M0 + il;
+  auto addr = [&](int r) -> int64_t {
+    const int j = r / nc, c = r - j * nc;
+    const int iM = lo + c;
+    const int k = l - a.M0 - iM;
+    return a.comp_off + (((int64_t)iM * a.nz + k) * a.nx + ix) * a.ny + j;
+  };
+  for (int r = 0; r < n; ++r) {
+    const int pr = r + Pb[(int64_t)r * a.nx + ix];
+    const int64_t ar = addr(r);
+    T xr = t[ar];
+    if (pr != r) {
+      const int64_t ap = addr(pr);
+      const T xp = t[ap];
+      t[ap] = xr;
+      xr = xp;
+      t[ar] = xr;
+    }
+    for (int d = 1; d <= kl && r + d < n; ++d) {
+      const int64_t ad = addr(r + d);
+      t[ad] = t[ad] - Lb[((int64_t)r * kl + (d - 1)) * a.nx + ix] * xr;
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    const int64_t ar = addr(r);
+    T s = t[ar];
+    for (int d = 1; d < w && r + d < n; ++d) s -= Ub[((int64_t)r * w + d) * a.nx + ix] * t[addr(r + d)];
+    t[ar] = s / Ub[((int64_t)r * w) * a.nx + ix];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Krylov helpers
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  __syncthreads();
+  return r;
+}
+
+// partial[j][block] = sum over this block's slice of V[j] . w
+__global__ void __launch_bounds__(kRedThreads) k_dot_many(const double* __restrict__ V, int64_t ldv, int nv,
+                                                         const double* __restrict__ w, int64_t n,
+                                                         double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  for (int j = 0; j < nv; ++j) {
+    const double* v = V + (int64_t)j * ldv;
+    double s = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s = fma(v[i], w[i], s);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_dot_finish(const double* __restrict__ partial, int nb, int nv, double* __restrict__ h) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nv) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partial[(int64_t)j * nb + b];
+  h[j] = s;
+}
+
+// w += sign * sum_j h[j] V[j]
+__global__ void __launch_bounds__(256) k_axpy_many(const double* __restrict__ V, int64_t ldv, int nv,
+                                                   const double* __restrict__ h, double sign, double* __restrict__ w,
+                                                   int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < nv; ++j) s = fma(h[j], V[(int64_t)j * ldv + i], s);
+    w[i] = fma(sign, s, w[i]);
+  }
+}
+
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
+}
+
+// counter-based normal deviates: splitmix64 -> two uniforms -> Box-Muller
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void k_fill_normal(double* x, int64_t n, uint64_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = splitmix64(seed ^ (2 * (uint64_t)i)), b = splitmix64(seed ^ (2 * (uint64_t)i + 1));
+    const double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+    const double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+    x[i] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+
+// out[c][i] = sum_j V[j][i] Q[j][c]  (Q row-major nv x nc on the device)
+__global__ void __launch_bounds__(256) k_combine(const double* __restrict__ V, int64_t ldv, int nv,
+                                                 const double* __restrict__ Qm, int nc, double* __restrict__ out,
+                                                 int64_t ldo, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int cc = 0; cc < nc; ++cc) {
+      double s = 0.0;
+      for (int j = 0; j < nv; ++j) s = fma(V[(int64_t)j * ldv + i], Qm[j * nc + cc], s);
+      out[(int64_t)cc * ldo + i] = s;
+    }
+  }
+}
+
+// per block: the entry of largest magnitude (value), first index on ties
+__global__ void __launch_bounds__(256) k_absmax(const double* __restrict__ x, int64_t n, double* __restrict__ pval,
+                                                long long* __restrict__ pidx) {
+  __shared__ double sv[256];
+  __shared__ long long si[256];
+  double best = 0.0;
+  long long bi = -1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    if (bi < 0 || fabs(v) > fabs(best)) { best = v; bi = i; }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      const double a = sv[threadIdx.x], b = sv[threadIdx.x + o];
+      const long long ia = si[threadIdx.x], ib = si[threadIdx.x + o];
+      if (ia < 0 || (ib >= 0 && (fabs(b) > fabs(a) || (fabs(b) == fabs(a) && ib < ia)))) {
+        sv[threadIdx.x] = b;
+        si[threadIdx.x] = ib;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pval[blockIdx.x] = sv[0];
+    pidx[blockIdx.x] = si[0];
+  }
+}
+
+inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+namespace fmi {
+
+int launch_apply(fm_ctx* c, double E, const double* x, double* y, bool only_S) {
+  for (auto& cp : c->comps) {
+    const int64_t off = cp.off;
+    constexpr int TX = 8;
+    const size_t smem = (size_t)3 * (TX + 2) * cp.ny * sizeof(double);
+    dim3 g1((cp.nx + TX - 1) / TX, cp.nz * c->nM);
+    k_apply_xy<TX><<<g1, 256, smem, c->stream>>>(x + off, c->P + off, c->Q + off, c->R + off, cp.nx, cp.ny, cp.dx.base,
+                                                 cp.dx.S, cp.dx.D2, cp.dy.base, cp.dy.S, cp.dy.D2, only_S);
+    c->launches++;
+    ZPassArgs a;
+    a.P = c->P + off; a.Q = c->Q + off; a.R = c->R + off; a.y = y + off; a.W = cp.W;
+    a.bz = cp.dz.base; a.Sz = cp.dz.S; a.D1z = cp.dz.D1; a.D2z = cp.dz.D2;
+    a.zp = cp.dz.pts; a.xp = cp.dx.pts; a.yp = cp.dy.pts;
+    a.nx = cp.nx; a.ny = cp.ny; a.nz = cp.nz; a.nM = c->nM; a.M0 = c->M0; a.J = c->sys.J; a.E = E;
+    for (int i = 0; i < kMaxM; ++i) {
+      a.lamp[i] = 0.0;
+      a.lamm[i] = 0.0;
+    }
+    for (int iM = 0; iM < c->nM; ++iM) {
+      const int Mp = c->Mps[iM], J = c->sys.J;
+      const double lp = sqrt((double)(J * (J + 1) - Mp * (Mp + 1)) > 0 ? (double)(J * (J + 1) - Mp * (Mp + 1)) : 0.0);
+      const double lm = sqrt((double)(J * (J + 1) - Mp * (Mp - 1)) > 0 ? (double)(J * (J + 1) - Mp * (Mp - 1)) : 0.0);
+      a.lamp[iM] = lp * sqrt(1.0 + (Mp == 0 ? 1.0 : 0.0));
+      a.lamm[iM] = lm * sqrt(1.0 + (Mp == 1 ? 1.0 : 0.0));
+    }
+    const int64_t tot = cp.npts * c->nM;
+    k_apply_z<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(a, only_S);
+    c->launches++;
+  }
+  if (!only_S) {
+    for (auto& cp : c->comps) {
+      if (cp.n_act == 0 || cp.sources.empty()) continue;
+      CouplingArgs a{};
+      a.x = x; a.y = y; a.row_off = cp.off; a.npts = cp.npts; a.n_act = cp.n_act; a.act_pt = cp.act_pt;
+      a.ns = (int)cp.sources.size(); a.nM = c->nM;
+      for (int s = 0; s < a.ns; ++s) {
+        const auto& src = c->comps[cp.sources[s].src];
+        a.base[s] = cp.cpl_base + (int64_t)s * 3 * cp.n_act;
+        a.val[s] = cp.cpl_val + (int64_t)s * 12 * cp.n_act;
+        a.w[s] = cp.cpl_w + (int64_t)s * c->nM * c->nM * cp.n_act;
+        a.src_off[s] = src.off; a.src_npts[s] = src.npts;
+        a.snx[s] = src.nx; a.sny[s] = src.ny; a.snz[s] = src.nz;
+      }
+      k_apply_coupling<<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
+      c->launches++;
+    }
+  }
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+template <typename T>
+static int precond_impl(fm_ctx* c, const double* x, double* y, T* t) {
+  for (auto& cp : c->comps) {
+    const int64_t nxy = (int64_t)cp.nx * cp.ny;
+    const T* Wzb = std::is_same<T, double>::value ? (const T*)cp.Wzb : (const T*)cp.Wzb32;
+    const T* Wz = std::is_same<T, double>::value ? (const T*)cp.Wz : (const T*)cp.Wz32;
+    const T* Wxb = std::is_same<T, double>::value ? (const T*)cp.Wxb : (const T*)cp.Wxb32;
+    const T* Wx = std::is_same<T, double>::value ? (const T*)cp.Wx : (const T*)cp.Wx32;
+    const T* U = std::is_same<T, double>::value ? (const T*)cp.yU : (const T*)cp.yU32;
+    const T* L = std::is_same<T, double>::value ? (const T*)cp.yL : (const T*)cp.yL32;
+    T* u = std::is_same<T, double>::value ? (T*)c->u64 : (T*)c->u32;
+    dim3 gz((unsigned)((nxy + 127) / 128), c->nM);
+    const size_t smz = (size_t)cp.nz * cp.nz * sizeof(T);
+    k_zmix<double, T, T><<<gz, 128, smz, c->stream>>>(Wzb, x, t, cp.nz, nxy, cp.off);
+    dim3 gx((cp.ny + 63) / 64, (cp.nx + 63) / 64, c->nM * cp.nz);
+    k_xmix<T><<<gx, 256, 0, c->stream>>>(Wxb, t, u, cp.nx, cp.ny, cp.nz, cp.off, c->M0);
+    YArgs ya;
+    ya.nx = cp.nx; ya.ny = cp.ny; ya.nz = cp.nz; ya.M0 = c->M0; ya.nl = cp.nl; ya.comp_off = cp.off;
+    ya.chain_lo = (const int*)cp.d_chain_lo; ya.chain_n = (const int*)cp.d_chain_n;
+    ya.band_off = cp.d_band_off; ya.lmul_off = cp.d_lmul_off; ya.piv_off = cp.d_piv_off;
+    dim3 gy((cp.nx + 127) / 128, cp.nl);
+    k_ysolve<T><<<gy, 128, 0, c->stream>>>(ya, U, L, cp.yP, u);
+    k_xmix<T><<<gx, 256, 0, c->stream>>>(Wx, u, t, cp.nx, cp.ny, cp.nz, cp.off, c->M0);
+    k_zmix<T, double, T><<<gz, 128, smz, c->stream>>>(Wz, t, y, cp.nz, nxy, cp.off);
+    c->launches += 5;
+  }
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+int launch_precond(fm_ctx* c, const double* x, double* y) {
+  if (c->opts.precision == FM_PREC_FP32) return precond_impl<float>(c, x, y, c->t32);
+  return precond_impl<double>(c, x, y, c->t64);
+}
+
+int dot_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, double* h_host) {
+  const int nb = c->red_blocks;
+  k_dot_many<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red);
+  k_dot_finish<<<(nv + 63) / 64, 64, 0, c->stream>>>(c->red, nb, nv, c->red + (int64_t)nb * 256);
+  c->launches += 2;
+  FM_CUDA(cudaMemcpyAsync(h_host, c->red + (int64_t)nb * 256, nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  return FM_OK;
+}
+
+int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double sign) {
+  double* hd = c->red + (int64_t)c->red_blocks * 256 + 512;
+  FM_CUDA(cudaMemcpyAsync(hd, h_host, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  k_axpy_many<<<grid_for(c->N, 256), 256, 0, c->stream>>>(V, ldv, nv, hd, sign, w, c->N);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+int scale_copy(fm_ctx* c, const double* x, double a, double* y) {
+  k_axpby<<<grid_for(c->N, 256), 256, 0, c->stream>>>(a, x, 0.0, y, c->N);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+int axpby(fm_ctx* c, double a, const double* x, double b, double* y) {
+  k_axpby<<<grid_for(c->N, 256), 256, 0, c->stream>>>(a, x, b, y, c->N);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+int combine(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* Q_host, int nc, double* out, int64_t ldo) {
+  double* qd = c->red + (int64_t)c->red_blocks * 256 + 512;
+  if (nv * nc > 7680) return FM_ERR_ARG;
+  FM_CUDA(cudaMemcpyAsync(qd, Q_host, (size_t)nv * nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  k_combine<<<grid_for(c->N, 256), 256, 0, c->stream>>>(V, ldv, nv, qd, nc, out, ldo, c->N);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  return FM_OK;
+}
+
+int absmax(fm_ctx* c, const double* x, double* val) {
+  const int nb = c->red_blocks;
+  double* pv = c->red;
+  long long* pi = (long long*)(c->red + nb);
+  k_absmax<<<nb, 256, 0, c->stream>>>(x, c->N, pv, pi);
+  c->launches++;
+  std::vector<double> hv(nb);
+  std::vector<long long> hi(nb);
+  FM_CUDA(cudaMemcpyAsync(hv.data(), pv, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaMemcpyAsync(hi.data(), pi, nb * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  double best = 0.0;
+  long long bi = -1;
+  for (int b = 0; b < nb; ++b) {
+    if (hi[b] < 0) continue;
+    if (bi < 0 || fabs(hv[b]) > fabs(best) || (fabs(hv[b]) == fabs(best) && hi[b] < bi)) { best = hv[b]; bi = hi[b]; }
+  }
+  *val = best;
+  return FM_OK;
+}
+
+int kernels_init(fm_ctx* c) {
+  (void)c;
+  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_zmix<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_zmix<double, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_zmix<float, double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  return FM_OK;
+}
+
+int fill_normal(fm_ctx* c, double* x, uint64_t seed) {
+  k_fill_normal<<<grid_for(c->N, 256), 256, 0, c->stream>>>(x, c->N, seed);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+}  // namespace fmi

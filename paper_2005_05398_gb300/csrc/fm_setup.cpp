@@ -1,0 +1,614 @@
+// Host set-up of libfm: spline axes and collocation (Section 3.1, Section 4), the
+// kinematics and potentials of Section 2, the V^(s) coupling geometry (Eqs. r-form,
+// s-rot), the z and x decompositions of the preconditioner (Eq. z-dec and the x
+// problems of Section 3.2) and the E*-dependent banded y systems.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "fm_dense.h"
+#include "fm_internal.h"
+
+namespace fmi {
+
+// ---------------------------------------------------------------------------
+// cubic Hermite shape functions on [t_m, t_m + h], local coordinate s in [0, 1]:
+// order (value left, slope left, value right, slope right)
+// ---------------------------------------------------------------------------
+static void shapes(double s, double h, int deriv, double v[4]) {
+  const double u = 1.0 - s;
+  if (deriv == 0) {
+    v[0] = (1.0 + 2.0 * s) * u * u;
+    v[1] = s * u * u * h;
+    v[2] = s * s * (3.0 - 2.0 * s);
+    v[3] = s * s * (s - 1.0) * h;
+  } else if (deriv == 1) {
+    v[0] = 6.0 * s * (s - 1.0) / h;
+    v[1] = u * (1.0 - 3.0 * s);
+    v[2] = 6.0 * s * u / h;
+    v[3] = s * (3.0 * s - 2.0);
+  } else {
+    v[0] = (12.0 * s - 6.0) / (h * h);
+    v[1] = (6.0 * s - 4.0) / h;
+    v[2] = (6.0 - 12.0 * s) / (h * h);
+    v[3] = (6.0 * s - 2.0) / h;
+  }
+}
+
+static void gauss(int q, double* g) {
+  if (q == 2) {
+    const double a = 1.0 / std::sqrt(3.0);
+    g[0] = -a; g[1] = a;
+  } else if (q == 3) {
+    const double a = std::sqrt(0.6);
+    g[0] = -a; g[1] = 0.0; g[2] = a;
+  } else {  // 4
+    const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(1.2));
+    const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(1.2));
+    g[0] = -b; g[1] = -a; g[2] = a; g[3] = b;
+  }
+}
+
+// taps for interval m: the Dirichlet basis drops the value functions of the end nodes;
+// the slope function of the last node then sits at tap 2.
+static void place(const Axis& A, int m, const double sh[4], int* base, double v[4]) {
+  if (!A.dirichlet) {
+    *base = 2 * m;
+    for (int t = 0; t < 4; ++t) v[t] = sh[t];
+    return;
+  }
+  *base = 2 * m - 1;
+  v[0] = (m == 0) ? 0.0 : sh[0];
+  v[1] = sh[1];
+  if (m == A.nint - 1) {
+    v[2] = sh[3];
+    v[3] = 0.0;
+  } else {
+    v[2] = sh[2];
+    v[3] = sh[3];
+  }
+}
+
+void Axis::build(int kind_, int nint_, double a_, double b_, bool dirichlet_) {
+  kind = kind_; nint = nint_; a = a_; b = b_; dirichlet = dirichlet_;
+  nodes.resize(nint + 1);
+  for (int i = 0; i <= nint; ++i) {
+    const double u = (double)i / nint;
+    if (kind == FM_MAP_POW) nodes[i] = 4.0 * (std::pow(1.0 + b / 4.0, u) - 1.0);
+    else if (kind == FM_MAP_SIN) nodes[i] = std::sin(M_PI * (-1.0 + 2.0 * u) / 2.0);
+    else nodes[i] = a + (b - a) * u;
+  }
+  nodes[0] = a;
+  nodes[nint] = b;
+  n = 2 * (nint + 1) - (dirichlet ? 2 : 0);
+  pts.clear(); base.clear(); S.clear(); D1.clear(); D2.clear();
+  for (int m = 0; m < nint; ++m) {
+    int q = 2;
+    if (!dirichlet) q = (nint == 1) ? 4 : ((m == 0 || m == nint - 1) ? 3 : 2);
+    double g[4];
+    gauss(q, g);
+    const double h = nodes[m + 1] - nodes[m];
+    for (int e = 0; e < q; ++e) {
+      const double s = 0.5 * (1.0 + g[e]);
+      const double p = nodes[m] + h * s;
+      pts.push_back(p);
+      double sh[4], v[4];
+      int bb;
+      for (int d = 0; d < 3; ++d) {
+        shapes(s, h, d, sh);
+        place(*this, m, sh, &bb, v);
+        std::vector<double>& dst = d == 0 ? S : (d == 1 ? D1 : D2);
+        for (int t = 0; t < 4; ++t) dst.push_back(v[t]);
+      }
+      base.push_back(bb);
+    }
+  }
+}
+
+int Axis::locate(double p) const {
+  int m = (int)(std::upper_bound(nodes.begin(), nodes.end(), p) - nodes.begin()) - 1;
+  return std::min(std::max(m, 0), nint - 1);
+}
+
+void Axis::eval(double p, int deriv, int* base_out, double v[4]) const {
+  if (!(p >= a && p <= b)) {
+    *base_out = 0;
+    v[0] = v[1] = v[2] = v[3] = 0.0;
+    return;
+  }
+  const int m = locate(p);
+  const double h = nodes[m + 1] - nodes[m];
+  double sh[4];
+  shapes((p - nodes[m]) / h, h, deriv, sh);
+  place(*this, m, sh, base_out, v);
+}
+
+// ---------------------------------------------------------------------------
+// kinematics and potentials (Section 2)
+// ---------------------------------------------------------------------------
+static void rotation(const double* m, int beta, int alpha, double* c, double* s) {
+  const double M = m[0] + m[1] + m[2];
+  const double mb = m[beta - 1], ma = m[alpha - 1];
+  *c = -std::sqrt(mb * ma / ((M - mb) * (M - ma)));
+  const double sg = ((beta - alpha) % 2 == 0 ? 1.0 : -1.0) * (alpha > beta ? 1.0 : -1.0);
+  *s = sg * std::sqrt(1.0 - (*c) * (*c));
+}
+
+static void rotate(double c, double s, double x, double y, double z, double* xb, double* yb, double* zb) {
+  *xb = std::sqrt(std::max(c * c * x * x + 2.0 * s * c * x * y * z + s * s * y * y, 0.0));
+  *yb = std::sqrt(std::max(s * s * x * x - 2.0 * s * c * x * y * z + c * c * y * y, 0.0));
+  double t = (s * c * (y * y - x * x) + (c * c - s * s) * x * y * z) / ((*xb) * (*yb));
+  *zb = std::min(1.0, std::max(-1.0, t));
+}
+
+static bool first_branch(int beta, int alpha) {
+  return (beta == 1 && alpha == 2) || (beta == 2 && alpha == 3) || (beta == 3 && alpha == 1);
+}
+
+static double w_angle(int beta, int alpha, double c, double s, double x, double y, double z, double yb) {
+  const double arg = std::min(1.0, std::max(-1.0, (-s * x * z + c * y) / yb));
+  const double w = std::acos(arg);
+  return first_branch(beta, alpha) ? w : 2.0 * M_PI - w;
+}
+
+static double coulomb(const fm_ctx* c, int a, double x) {
+  int b = -1, g = -1;
+  for (int i = 0; i < 3; ++i)
+    if (i != a - 1) (b < 0 ? b : g) = i;
+  return std::sqrt(2.0 * c->mu_pair[a - 1]) * c->sys.charge[b] * c->sys.charge[g] / x;
+}
+
+static double chi(const fm_splitting& sp, double x, double y) {
+  double arg = std::pow(x / sp.x0, sp.nu);
+  if (std::isfinite(sp.y0)) arg /= (1.0 + y / sp.y0);
+  return 2.0 / (1.0 + std::exp(arg));
+}
+
+static double vhat(const fm_ctx* c, int a, double y, double Ry) {
+  double zz = 0.0;
+  for (int i = 0; i < 3; ++i)
+    if (i != a - 1) zz += c->sys.charge[i];
+  const double qv = c->sys.charge[a - 1] * zz * std::sqrt(2.0 * c->mu_rel[a - 1]);
+  const double u = y / (0.05 * Ry);
+  return qv / y * (1.0 - std::exp(-u * u));
+}
+
+// ---------------------------------------------------------------------------
+// Wigner d (Eq. D-def) through the Jacobi-polynomial form, valid for M' >= |M|, and
+// the symmetries d_{M M'} = (-1)^{M-M'} d_{M' M} = d_{-M', -M} for the other indices.
+// d_over_sin returns d / sin(w)^k (k <= min(|M-M'|, |M+M'|)).
+// ---------------------------------------------------------------------------
+static double lfact(int n) { return std::lgamma(n + 1.0); }
+
+static double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  return std::exp(lfact(n) - lfact(k) - lfact(n - k));
+}
+
+static double jacobi_poly(int n, int al, int be, double x) {
+  double s = 0.0;
+  for (int k = 0; k <= n; ++k)
+    s += binom(n + al, n - k) * binom(n + be, k) * std::pow((x - 1.0) / 2.0, k) * std::pow((x + 1.0) / 2.0, n - k);
+  return s;
+}
+
+static double wigner_d_sin(int J, int M, int Mp, double w, int k) {
+  if (std::abs(M) > J || std::abs(Mp) > J) return 0.0;
+  double sign = 1.0;
+  int m = M, mp = Mp;
+  if (mp >= std::abs(m)) {
+  } else if (m >= std::abs(mp)) {  // d_{M M'} = (-1)^{M-M'} d_{M' M}
+    sign = ((m - mp) % 2 == 0) ? 1.0 : -1.0;
+    std::swap(m, mp);
+  } else if (-mp >= std::abs(m)) {  // d_{M M'} = (-1)^{M-M'} d_{-M, -M'}
+    sign = ((m - mp) % 2 == 0) ? 1.0 : -1.0;
+    m = -m;
+    mp = -mp;
+  } else {  // -M >= |M'|: d_{M M'} = d_{-M', -M}
+    const int t = m;
+    m = -mp;
+    mp = -t;
+  }
+  const double pref = std::exp(0.5 * (lfact(J + mp) + lfact(J - mp) - lfact(J + m) - lfact(J - m)));
+  const double sh = std::sin(0.5 * w), ch = std::cos(0.5 * w);
+  const double val = pref * std::pow(sh, mp - m - k) * std::pow(ch, mp + m - k) * jacobi_poly(J - mp, mp - m, mp + m, std::cos(w));
+  return sign * val / std::pow(2.0, k);
+}
+
+// (-1)^{M''-M'} 2/sqrt(2+2 d_{M''0}) F^{J tau}_{M'' M'}(0, w, 0), divided by sin(w)^k
+static double coupling_K(int J, int tau, int Mp, int Mpp, double w, int k) {
+  const double F = (wigner_d_sin(J, Mpp, Mp, w, k) + tau * ((Mp % 2 == 0) ? 1.0 : -1.0) * wigner_d_sin(J, Mpp, -Mp, w, k)) /
+                   std::sqrt(2.0 + (Mp == 0 ? 2.0 : 0.0));
+  return (((Mpp - Mp) % 2 == 0) ? 1.0 : -1.0) * 2.0 / std::sqrt(2.0 + (Mpp == 0 ? 2.0 : 0.0)) * F;
+}
+
+static double lam(int J, int Mp) {
+  const double v = (double)(J * (J + 1) - Mp * (Mp + 1));
+  return v > 0 ? std::sqrt(v) : 0.0;
+}
+static double lam_hat_plus(int J, int Mp) { return lam(J, Mp) * std::sqrt(Mp == 0 ? 2.0 : 1.0); }
+static double lam_hat_minus(int J, int Mp) { return lam(J, -Mp) * std::sqrt(Mp == 1 ? 2.0 : 1.0); }
+
+// g_l^{M'}(1) (Appendix, Eq. g-def, Condon-Shortley phase)
+static double g_at_one(int l, int Mp) {
+  const double nrm = std::sqrt((2 * l + 1) / 2.0 * std::exp(lfact(l - Mp) - lfact(l + Mp)));
+  return nrm * ((Mp % 2 == 0) ? 1.0 : -1.0) * std::exp(lfact(l + Mp) - lfact(Mp) - lfact(l - Mp)) / std::pow(2.0, Mp);
+}
+
+// ---------------------------------------------------------------------------
+template <typename F>
+static void parallel_for(int n, F f) {
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (n < 2 || nt == 1) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::atomic<int> next{0};
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&]() {
+      for (int i = next++; i < n; i = next++) f(i);
+    });
+  for (auto& t : th) t.join();
+}
+
+static int upload_axis(fm_ctx* c, const Axis& A, AxisDev& D) {
+  int rc;
+  if ((rc = upload(c, (void**)&D.base, A.base.data(), A.base.size() * sizeof(int)))) return rc;
+  if ((rc = upload(c, (void**)&D.S, A.S.data(), A.S.size() * sizeof(double)))) return rc;
+  if ((rc = upload(c, (void**)&D.D1, A.D1.data(), A.D1.size() * sizeof(double)))) return rc;
+  if ((rc = upload(c, (void**)&D.D2, A.D2.data(), A.D2.size() * sizeof(double)))) return rc;
+  if ((rc = upload(c, (void**)&D.pts, A.pts.data(), A.pts.size() * sizeof(double)))) return rc;
+  return FM_OK;
+}
+
+static std::vector<double> dense_of(const Axis& A, const std::vector<double>& vals) {
+  std::vector<double> M((size_t)A.n * A.n, 0.0);
+  for (int q = 0; q < A.n; ++q)
+    for (int t = 0; t < 4; ++t) {
+      const int j = A.base[q] + t;
+      if (j >= 0 && j < A.n) M[(size_t)q * A.n + j] += vals[q * 4 + t];
+    }
+  return M;
+}
+
+static std::vector<float> to_f32(const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); }
+
+int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
+  const fm_system& S = c->sys;
+  const double* m = S.mass;
+  const double M = m[0] + m[1] + m[2];
+  for (int a = 0; a < 3; ++a) {
+    int b = -1, g = -1;
+    for (int i = 0; i < 3; ++i)
+      if (i != a) (b < 0 ? b : g) = i;
+    c->mu_pair[a] = m[b] * m[g] / (m[b] + m[g]);
+    c->mu_rel[a] = m[a] * (m[b] + m[g]) / M;
+  }
+  std::vector<int> labels;
+  if (c->split.mode == FM_SPLIT_SCHRODINGER) labels = {1};
+  else if (S.identical_pair == 12) labels = {1, 3};
+  else labels = {1, 2, 3};
+  if (n_grids != 1 && n_grids != (int)labels.size()) return FM_ERR_ARG;
+  c->comps.resize(labels.size());
+  int64_t off = 0;
+  for (size_t ic = 0; ic < labels.size(); ++ic) {
+    Comp& cp = c->comps[ic];
+    const fm_grid& g = grids[n_grids == 1 ? 0 : ic];
+    if (g.nint_x < 1 || g.nint_y < 1 || g.nint_z < 1 || !(g.Rx > 0) || !(g.Ry > 0) || g.basis != 0) return FM_ERR_ARG;
+    if (g.zmap == FM_MAP_POW || g.xmap == FM_MAP_SIN || g.ymap == FM_MAP_SIN) return FM_ERR_ARG;
+    cp.label = labels[ic];
+    cp.ax.build(g.xmap, g.nint_x, 0.0, g.Rx, true);
+    cp.ay.build(g.ymap, g.nint_y, 0.0, g.Ry, true);
+    cp.az.build(g.zmap, g.nint_z, -1.0, 1.0, false);
+    cp.nx = cp.ax.n; cp.ny = cp.ay.n; cp.nz = cp.az.n;
+    cp.Rx = g.Rx; cp.Ry = g.Ry;
+    cp.npts = (int64_t)cp.nz * cp.nx * cp.ny;
+    cp.off = off;
+    off += cp.npts * c->nM;
+  }
+  c->N = off;
+  // sources (Eq. FM-pre right-hand side with Eq. 2-sym-part)
+  for (auto& cp : c->comps) {
+    cp.sources.clear();
+    if (c->split.mode == FM_SPLIT_SCHRODINGER) continue;
+    for (int beta = 1; beta <= 3; ++beta) {
+      if (beta == cp.label) continue;
+      Source s;
+      s.beta = beta;
+      int idx = -1;
+      for (size_t i = 0; i < labels.size(); ++i)
+        if (labels[i] == beta) idx = (int)i;
+      if (idx >= 0) {
+        s.src = idx;
+        s.zsign = 1.0;
+        s.sym = false;
+      } else {  // beta = 2 of the identical pair: component 1 at (x, y, -z) times p (-1)^{M''}
+        s.src = 0;
+        s.zsign = -1.0;
+        s.sym = true;
+      }
+      cp.sources.push_back(s);
+    }
+  }
+  const int J = S.J, nM = c->nM;
+  int rc;
+  for (auto& cp : c->comps) {
+    if ((rc = upload_axis(c, cp.ax, cp.dx))) return rc;
+    if ((rc = upload_axis(c, cp.ay, cp.dy))) return rc;
+    if ((rc = upload_axis(c, cp.az, cp.dz))) return rc;
+    // left-hand potential V_a(x) + sum_{b != a} V^(l)_b(x_b, y_b)   (Eq. FM-pre)
+    std::vector<double> W((size_t)cp.npts);
+    for (int k = 0; k < cp.nz; ++k)
+      for (int i = 0; i < cp.nx; ++i)
+        for (int j = 0; j < cp.ny; ++j) {
+          const double z = cp.az.pts[k], x = cp.ax.pts[i], y = cp.ay.pts[j];
+          double tot = coulomb(c, cp.label, x);
+          for (int beta = 1; beta <= 3; ++beta) {
+            if (beta == cp.label) continue;
+            double cc, ss, xb, yb, zb;
+            rotation(m, beta, cp.label, &cc, &ss);
+            rotate(cc, ss, x, y, z, &xb, &yb, &zb);
+            const double vc = coulomb(c, beta, xb);
+            if (c->split.mode == FM_SPLIT_SCHRODINGER) tot += vc;
+            else if (c->split.mode == FM_SPLIT_MERKURIEV) tot += (1.0 - chi(c->split, xb, yb)) * vc;
+          }
+          if (!std::isfinite(tot)) return FM_ERR_NUMERIC;
+          W[((size_t)k * cp.nx + i) * cp.ny + j] = tot;
+        }
+    if ((rc = upload(c, (void**)&cp.W, W.data(), W.size() * sizeof(double)))) return rc;
+
+    // coupling geometry (Eqs. r-form, s-rot): active points and, per source, taps and weights
+    if (!cp.sources.empty()) {
+      std::vector<int> act;
+      for (int k = 0; k < cp.nz; ++k)
+        for (int i = 0; i < cp.nx; ++i)
+          for (int j = 0; j < cp.ny; ++j) {
+            const double x = cp.ax.pts[i], y = cp.ay.pts[j];
+            bool on = true;
+            if (c->split.mode == FM_SPLIT_MERKURIEV) on = chi(c->split, x, y) > c->split.vs_cut;
+            if (on) act.push_back((int)(((int64_t)k * cp.nx + i) * cp.ny + j));
+          }
+      cp.n_act = (int)act.size();
+      const int ns = (int)cp.sources.size(), na = cp.n_act;
+      std::vector<int> base((size_t)ns * 3 * na);
+      std::vector<double> val((size_t)ns * 12 * na), wt((size_t)ns * nM * nM * na);
+      for (int s = 0; s < ns; ++s) {
+        const Source& src = cp.sources[s];
+        const Comp& sc = c->comps[src.src];
+        double cc, ss;
+        rotation(m, src.beta, cp.label, &cc, &ss);
+        for (int p = 0; p < na; ++p) {
+          const int pt = act[p];
+          const int k = pt / (cp.nx * cp.ny), rem = pt % (cp.nx * cp.ny), i = rem / cp.ny, j = rem % cp.ny;
+          const double z = cp.az.pts[k], x = cp.ax.pts[i], y = cp.ay.pts[j];
+          double xb, yb, zb;
+          rotate(cc, ss, x, y, z, &xb, &yb, &zb);
+          const double w = w_angle(src.beta, cp.label, cc, ss, x, y, z, yb);
+          int b3[3];
+          double v[12];
+          sc.az.eval(src.zsign * zb, 0, &b3[0], v);
+          sc.ax.eval(xb, 0, &b3[1], v + 4);
+          sc.ay.eval(yb, 0, &b3[2], v + 8);
+          for (int d = 0; d < 3; ++d) base[((size_t)s * 3 + d) * na + p] = b3[d];
+          for (int t = 0; t < 12; ++t) val[((size_t)s * 12 + t) * na + p] = v[t];
+          // weight V^(s)_a * rho * rho^{M''} * angular(M', M'') * [p (-1)^{M''}]
+          const double vc = coulomb(c, cp.label, x);
+          const double vs = (c->split.mode == FM_SPLIT_MERKURIEV) ? chi(c->split, x, y) * vc : vc;
+          const double rho = x * y / (xb * yb);
+          const double sin_t = std::sqrt(std::max(0.0, 1.0 - z * z));
+          const double sgnw = first_branch(src.beta, cp.label) ? 1.0 : -1.0;
+          for (int iM = 0; iM < nM; ++iM)
+            for (int jM = 0; jM < nM; ++jM) {
+              const int Mp = c->Mps[iM], Mpp = c->Mps[jM];
+              double ang;
+              if (Mpp >= Mp) {
+                ang = std::pow(sin_t, Mpp - Mp) * coupling_K(J, S.tau, Mp, Mpp, w, 0);
+              } else {
+                const int kk = Mp - Mpp;
+                ang = std::pow(std::fabs(ss) * x / yb, kk) * std::pow(sgnw, kk) * coupling_K(J, S.tau, Mp, Mpp, w, kk);
+              }
+              double wv = vs * rho * std::pow(rho, Mpp) * ang;
+              if (src.sym) wv *= S.exch_p * ((Mpp % 2 == 0) ? 1.0 : -1.0);
+              if (!std::isfinite(wv)) return FM_ERR_NUMERIC;
+              wt[(((size_t)s * nM * nM) + (size_t)iM * nM + jM) * na + p] = wv;
+            }
+        }
+      }
+      if ((rc = upload(c, (void**)&cp.act_pt, act.data(), act.size() * sizeof(int)))) return rc;
+      if ((rc = upload(c, (void**)&cp.cpl_base, base.data(), base.size() * sizeof(int)))) return rc;
+      if ((rc = upload(c, (void**)&cp.cpl_val, val.data(), val.size() * sizeof(double)))) return rc;
+      if ((rc = upload(c, (void**)&cp.cpl_w, wt.data(), wt.size() * sizeof(double)))) return rc;
+    }
+
+    // z decompositions per M' (Eq. z-dec), columns normalised to g_l^{M'}(1)
+    const int nz = cp.nz, nx = cp.nx;
+    std::vector<double> Wz((size_t)nM * nz * nz), Wzb((size_t)nM * nz * nz);
+    cp.Lz.assign((size_t)nM * nz, 0.0);
+    const std::vector<double> Szd = dense_of(cp.az, cp.az.S);
+    for (int iM = 0; iM < nM; ++iM) {
+      const int Mp = c->Mps[iM];
+      std::vector<double> A1((size_t)nz * nz, 0.0);
+      for (int q = 0; q < nz; ++q) {
+        const double z = cp.az.pts[q];
+        for (int t = 0; t < 4; ++t) {
+          const int j = cp.az.base[q] + t;
+          if (j < 0 || j >= nz) continue;
+          A1[(size_t)q * nz + j] += (1.0 - z * z) * cp.az.D2[q * 4 + t] - 2.0 * (Mp + 1) * z * cp.az.D1[q * 4 + t] -
+                                    Mp * (Mp + 1.0) * cp.az.S[q * 4 + t];
+        }
+      }
+      double* Wb = &Wzb[(size_t)iM * nz * nz];
+      double* Wr = &Wz[(size_t)iM * nz * nz];
+      const int e = fmh::decompose(nz, A1.data(), Szd.data(), true, Wb, Wr, &cp.Lz[(size_t)iM * nz]);
+      if (e == -1) return FM_ERR_COMPLEX_SPECTRUM;
+      if (e != 0) return FM_ERR_NUMERIC;
+      const int top = 2 * cp.az.nint;  // value function of the node z = 1
+      for (int l = 0; l < nz; ++l) {
+        const double f1 = Wr[(size_t)top * nz + l];
+        if (f1 == 0.0) return FM_ERR_NUMERIC;
+        const double sc = g_at_one(Mp + l, Mp) / f1;
+        for (int q = 0; q < nz; ++q) Wr[(size_t)q * nz + l] *= sc;
+        for (int q = 0; q < nz; ++q) Wb[(size_t)l * nz + q] /= sc;
+      }
+    }
+    if ((rc = upload(c, (void**)&cp.Wz, Wz.data(), Wz.size() * 8))) return rc;
+    if ((rc = upload(c, (void**)&cp.Wzb, Wzb.data(), Wzb.size() * 8))) return rc;
+    {
+      auto f = to_f32(Wz), fb = to_f32(Wzb);
+      if ((rc = upload(c, (void**)&cp.Wz32, f.data(), f.size() * 4))) return rc;
+      if ((rc = upload(c, (void**)&cp.Wzb32, fb.data(), fb.size() * 4))) return rc;
+    }
+    // x decompositions per l = M0 .. J + nz - 1
+    cp.nl = nM + nz - 1;
+    const int nl = cp.nl;
+    std::vector<double> Wx((size_t)nl * nx * nx), Wxb((size_t)nl * nx * nx);
+    cp.Lx.assign((size_t)nl * nx, 0.0);
+    const std::vector<double> Sxd = dense_of(cp.ax, cp.ax.S), D2xd = dense_of(cp.ax, cp.ax.D2);
+    std::vector<int> errs(nl, 0);
+    const Comp* cpp = &cp;
+    parallel_for(nl, [&](int il) {
+      const int l = c->M0 + il;
+      const double ll1 = (c->opts.z_eigs == 1) ? -cpp->Lz[il] : (double)l * (l + 1);
+      std::vector<double> A1((size_t)nx * nx);
+      for (int q = 0; q < nx; ++q) {
+        const double x = cpp->ax.pts[q];
+        const double f = ll1 / (x * x) + coulomb(c, cpp->label, x);
+        for (int j = 0; j < nx; ++j) A1[(size_t)q * nx + j] = -D2xd[(size_t)q * nx + j] + f * Sxd[(size_t)q * nx + j];
+      }
+      errs[il] = fmh::decompose(nx, A1.data(), Sxd.data(), false, &Wxb[(size_t)il * nx * nx], &Wx[(size_t)il * nx * nx],
+                                &cp.Lx[(size_t)il * nx]);
+    });
+    for (int e : errs) {
+      if (e == -1) return FM_ERR_COMPLEX_SPECTRUM;
+      if (e != 0) return FM_ERR_NUMERIC;
+    }
+    if ((rc = upload(c, (void**)&cp.Wx, Wx.data(), Wx.size() * 8))) return rc;
+    if ((rc = upload(c, (void**)&cp.Wxb, Wxb.data(), Wxb.size() * 8))) return rc;
+    {
+      auto f = to_f32(Wx), fb = to_f32(Wxb);
+      if ((rc = upload(c, (void**)&cp.Wx32, f.data(), f.size() * 4))) return rc;
+      if ((rc = upload(c, (void**)&cp.Wxb32, fb.data(), fb.size() * 4))) return rc;
+    }
+    // M' chains per l and the storage plan of the banded y factors
+    cp.chain_lo.assign(nl, 0);
+    cp.chain_n.assign(nl, 0);
+    cp.band_off.assign(nl, 0);
+    cp.lmul_off.assign(nl, 0);
+    cp.piv_off.assign(nl, 0);
+    int64_t bo = 0, lo = 0, po = 0;
+    for (int il = 0; il < nl; ++il) {
+      const int l = c->M0 + il;
+      int first = -1, cnt = 0;
+      for (int iM = 0; iM < nM; ++iM) {
+        const int Mp = c->Mps[iM];
+        if (Mp <= l && l <= Mp + nz - 1) {
+          if (first < 0) first = iM;
+          ++cnt;
+        }
+      }
+      cp.chain_lo[il] = first;
+      cp.chain_n[il] = cnt;
+      const int n = cnt * cp.ny, kl = (cnt == 1) ? 2 : 2 * cnt + 1;
+      cp.band_off[il] = bo;
+      cp.lmul_off[il] = lo;
+      cp.piv_off[il] = po;
+      bo += (int64_t)n * (2 * kl + 1) * nx;
+      lo += (int64_t)n * kl * nx;
+      po += (int64_t)n * nx;
+    }
+    cp.band_total = bo;
+    cp.lmul_total = lo;
+    cp.piv_total = po;
+    if ((rc = upload(c, (void**)&cp.d_chain_lo, cp.chain_lo.data(), nl * sizeof(int)))) return rc;
+    if ((rc = upload(c, (void**)&cp.d_chain_n, cp.chain_n.data(), nl * sizeof(int)))) return rc;
+    if ((rc = upload(c, (void**)&cp.d_band_off, cp.band_off.data(), nl * sizeof(int64_t)))) return rc;
+    if ((rc = upload(c, (void**)&cp.d_lmul_off, cp.lmul_off.data(), nl * sizeof(int64_t)))) return rc;
+    if ((rc = upload(c, (void**)&cp.d_piv_off, cp.piv_off.data(), nl * sizeof(int64_t)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&cp.yU, bo * 8))) return rc;
+    if ((rc = dev_alloc(c, (void**)&cp.yL, lo * 8))) return rc;
+    if ((rc = dev_alloc(c, (void**)&cp.yP, po))) return rc;
+    if ((rc = dev_alloc(c, (void**)&cp.yU32, bo * 4))) return rc;
+    if ((rc = dev_alloc(c, (void**)&cp.yL32, lo * 4))) return rc;
+  }
+  return FM_OK;
+}
+
+// The E*-dependent banded y systems: for each (l, i_x) the block-tridiagonal (in M')
+// system with banded blocks N^{M'}_{l i} = A1 + (J(J+1) - 2M'^2 + l(l+1)) A2 and
+// N^{M'+-} = (off-diagonal coefficient) A2, where A1 = -D_y + V^ S_y - E* S_y +
+// (Lambda_x^l)_{ii} S_y and A2 = Y_r2 S_y (Section 3.2, Eq. ops and the matrix L0).
+// Factorised by banded LU with the unknowns ordered r = j * n_c + c.
+int setup_shift(fm_ctx* c, double Estar) {
+  const int J = c->sys.J;
+  int rc;
+  for (auto& cp : c->comps) {
+    const int nx = cp.nx, ny = cp.ny;
+    std::vector<double> U((size_t)cp.band_total), L((size_t)cp.lmul_total);
+    std::vector<unsigned char> P((size_t)cp.piv_total);
+    std::vector<double> vh(ny);
+    for (int j = 0; j < ny; ++j) vh[j] = vhat(c, cp.label, cp.ay.pts[j], cp.Ry);
+    std::vector<int> bad(cp.nl, 0);
+    const Comp* cpp = &cp;
+    parallel_for(cp.nl, [&](int il) {
+      const int l = c->M0 + il;
+      const double ll1 = (c->opts.z_eigs == 1) ? -cpp->Lz[il] : (double)l * (l + 1);
+      const int nc = cpp->chain_n[il], lo = cpp->chain_lo[il];
+      const int n = nc * ny, kl = (nc == 1) ? 2 : 2 * nc + 1, ku = kl, wb = 2 * kl + ku + 1, wu = kl + ku + 1;
+      std::vector<double> B((size_t)n * wb), Lm((size_t)n * kl);
+      std::vector<int> piv(n);
+      for (int ix = 0; ix < nx; ++ix) {
+        const double lx = cpp->Lx[(size_t)il * nx + ix];
+        std::fill(B.begin(), B.end(), 0.0);
+        for (int eta = 0; eta < ny; ++eta) {
+          const double y = cpp->ay.pts[eta];
+          for (int t = 0; t < 4; ++t) {
+            const int j = cpp->ay.base[eta] + t;
+            if (j < 0 || j >= ny) continue;
+            const double s = cpp->ay.S[eta * 4 + t], d2 = cpp->ay.D2[eta * 4 + t];
+            const double a1 = -d2 + (vh[eta] - Estar + lx) * s;
+            const double a2 = s / (y * y);
+            for (int cc = 0; cc < nc; ++cc) {
+              const int Mp = c->Mps[lo + cc];
+              const int row = eta * nc + cc;
+              auto put = [&](int col, double v) { B[(size_t)row * wb + (col - row + kl)] += v; };
+              put(j * nc + cc, a1 + (J * (J + 1.0) - 2.0 * Mp * Mp + ll1) * a2);
+              if (cc + 1 < nc) put(j * nc + cc + 1, lam_hat_plus(J, Mp) * (-lam(l, Mp)) * a2);
+              if (cc >= 1) put(j * nc + cc - 1, -lam_hat_minus(J, Mp) * lam(l, -Mp) * a2);
+            }
+          }
+        }
+        if (!fmh::band_lu(n, kl, ku, B.data(), Lm.data(), piv.data())) {
+          bad[il] = 1;
+          return;
+        }
+        double* Ug = &U[cpp->band_off[il]];
+        double* Lg = &L[cpp->lmul_off[il]];
+        unsigned char* Pg = &P[cpp->piv_off[il]];
+        for (int r = 0; r < n; ++r) {
+          for (int d = 0; d < wu; ++d) Ug[((size_t)r * wu + d) * nx + ix] = B[(size_t)r * wb + kl + d];
+          for (int d = 0; d < kl; ++d) Lg[((size_t)r * kl + d) * nx + ix] = Lm[(size_t)r * kl + d];
+          Pg[(size_t)r * nx + ix] = (unsigned char)(piv[r] - r);
+        }
+      }
+    });
+    for (int b : bad)
+      if (b) return FM_ERR_NUMERIC;
+    FM_CUDA(cudaMemcpyAsync(cp.yU, U.data(), U.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    FM_CUDA(cudaMemcpyAsync(cp.yL, L.data(), L.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    FM_CUDA(cudaMemcpyAsync(cp.yP, P.data(), P.size(), cudaMemcpyHostToDevice, c->stream));
+    std::vector<float> U32(U.begin(), U.end()), L32(L.begin(), L.end());
+    FM_CUDA(cudaMemcpyAsync(cp.yU32, U32.data(), U32.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    FM_CUDA(cudaMemcpyAsync(cp.yL32, L32.data(), L32.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    FM_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  c->Estar = Estar;
+  c->have_shift = true;
+  (void)rc;
+  return FM_OK;
+}
+
+}  // namespace fmi

@@ -1,0 +1,204 @@
+"""GPU parity: libfm (CUDA, through the C ABI) against the CPU oracle on the same
+seeded inputs.  Sizes span several kernel tiles with ragged tails; the large
+configuration is checked on sampled rows."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from fm_inputs import workload, rand_vec, MERKURIEV, NO_SPLIT, SCHRODINGER
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2005_05398_gb300 as p
+    from paper_2005_05398_gb300 import build
+    build.build()
+    p.lib()
+    return p
+
+
+def _dev(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+CASES = {
+    "he_l0_merkuriev": dict(nint=(7, 9, 5), R=(20.0, 17.0)),
+    "he_l0_nosplit": dict(nint=(7, 9, 5), R=(20.0, 17.0), mode=NO_SPLIT),
+    "he_l0_schrodinger": dict(nint=(7, 9, 5), R=(20.0, 17.0), mode=SCHRODINGER),
+    "he_l1": dict(J=1, nint=(6, 7, 4), R=(20.0, 17.0)),
+    "he_l2_odd": dict(J=2, tau=-1, nint=(5, 6, 4), R=(15.0, 17.0)),
+    "psm_l2": dict(J=2, nint=(6, 5, 4), R=(30.0, 27.0), mass=(1.0, 1.0, 1.0), charge=(-1.0, -1.0, 1.0), shift=-0.27),
+    "he_l1_percomp": dict(J=1, nint=(6, 6, 4), R=(20.0, 20.0), grids={3: {"nint": (4, 3, 3), "R": (9.0, 6.0)}}),
+    "distinct_l1": dict(J=1, nint=(5, 5, 3), R=(12.0, 11.0), identical_pair=0, mass=(1.0, 3.0, 7.0),
+                        charge=(-1.0, 2.0, -1.0)),
+}
+
+
+def _wl(name):
+    kw = dict(CASES[name])
+    return workload("he_l0_24x24x8", **kw)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_matches_oracle(pkg, name):
+    from oracle.system import FMSystem
+    wl = _wl(name)
+    s = FMSystem(wl)
+    ctx = pkg.Context(wl)
+    assert ctx.n == s.N
+    H, S = s.H(), s.S()
+    for seed, E in ((1, -2.9), (2, 0.3)):
+        x = rand_vec(s.N, seed)
+        ref = H @ x - E * (S @ x)
+        y = torch.empty(s.N, dtype=torch.float64, device="cuda")
+        ctx.fm_apply(E, _dev(x), y)
+        got = y.cpu().numpy()
+        scale = np.abs(H).max(axis=1).toarray().ravel() * np.abs(x).max() + 1e-300
+        assert np.max(np.abs(got - ref) / scale) < 1e-13, name
+    ys = torch.empty(s.N, dtype=torch.float64, device="cuda")
+    ctx.fm_apply_S(_dev(x), ys)
+    assert np.max(np.abs(ys.cpu().numpy() - S @ x)) < 1e-13 * np.abs(x).max() * 4
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["he_l0_merkuriev", "he_l1", "he_l2_odd", "psm_l2", "he_l1_percomp"])
+def test_precond_fp64_matches_paper_form(pkg, name):
+    """The GPU preconditioner (z/x mode products + banded y solves) equals the
+    paper's Eq. prec-2 with y eigen-transforms and tridiagonal M' chains."""
+    from oracle.system import FMSystem
+    from oracle.precond import Preconditioner
+    wl = _wl(name)
+    s = FMSystem(wl)
+    E = wl["shift"] + 0.013
+    P = Preconditioner(s, E)
+    ctx = pkg.Context(wl)
+    ctx.fm_set_shift(E)
+    v = rand_vec(s.N, 3)
+    ref = P.apply(v)
+    y = torch.empty(s.N, dtype=torch.float64, device="cuda")
+    ctx.fm_precond_apply(_dev(v), y)
+    got = y.cpu().numpy()
+    assert np.linalg.norm(got - ref) < 1e-10 * np.linalg.norm(ref), name
+    assert np.max(np.abs(got - ref)) < 1e-9 * np.max(np.abs(ref))
+    ctx.close()
+
+
+def test_precond_fp32_close_to_fp64(pkg):
+    wl = _wl("he_l1")
+    ctx64 = pkg.Context(wl)
+    ctx32 = pkg.Context(wl, precision=1)
+    for c in (ctx64, ctx32):
+        c.fm_set_shift(-2.1)
+    v = _dev(rand_vec(ctx64.n, 4))
+    a = torch.empty_like(v)
+    b = torch.empty_like(v)
+    ctx64.fm_precond_apply(v, a)
+    ctx32.fm_precond_apply(v, b)
+    assert (torch.linalg.norm(a - b) / torch.linalg.norm(a)).item() < 1e-4
+
+
+def test_computed_z_gives_exact_inverse_of_fmfin(pkg):
+    """n_M = 1 with the computed z eigenvalues: L^{-1} is the exact inverse of Eq. FM-fin's left operator."""
+    from oracle.system import FMSystem
+    from oracle.precond import Preconditioner
+    wl = workload("he_l0_24x24x8", nint=(4, 5, 3), R=(10.0, 12.0))
+    s = FMSystem(wl)
+    E = -2.7
+    P = Preconditioner(s, E, z_eigs="computed")
+    ctx = pkg.Context(wl, z_eigs=1)
+    ctx.fm_set_shift(E)
+    v = rand_vec(s.N, 5)
+    Lv = np.zeros(s.N)
+    for a in s.comps:
+        g = s.g[a]
+        Lv[s.off[a]:s.off[a] + g.csize] = P.dense_L_fmfin(a) @ v[s.off[a]:s.off[a] + g.csize]
+    y = torch.empty(s.N, dtype=torch.float64, device="cuda")
+    ctx.fm_precond_apply(_dev(Lv), y)
+    assert np.linalg.norm(y.cpu().numpy() - v) < 1e-10 * np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_matches_sparse_lu(pkg, precision):
+    from oracle.system import FMSystem
+    from oracle import solvers
+    wl = _wl("he_l0_merkuriev")
+    s = FMSystem(wl)
+    H, S = s.H(), s.S()
+    E = -2.5
+    b = rand_vec(s.N, 6)
+    ref = solvers.solve(H, S, E, b)
+    ctx = pkg.Context(wl, precision=precision, restart_m=40)
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    info = ctx.fm_solve(E, _dev(b), x)
+    got = x.cpu().numpy()
+    assert info["converged"] == 1 and info["resid"] <= 1e-12
+    r = np.linalg.norm(H @ got - E * (S @ got) - b) / np.linalg.norm(b)
+    assert r < 1e-11
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8
+
+
+@pytest.mark.parametrize("name,k", [("he_l0_merkuriev", 1), ("he_l0_merkuriev", 3), ("he_l1", 2), ("psm_l2", 2)])
+def test_eigs_match_oracle(pkg, name, k):
+    from oracle.system import FMSystem
+    from oracle import solvers
+    wl = _wl(name)
+    s = FMSystem(wl)
+    H, S = s.H(), s.S()
+    shift = wl["shift"] if name != "he_l1" else -2.12
+    Eo, vo = solvers.eigs_near(H, S, shift, k)
+    ctx = pkg.Context(wl, restart_m=40)
+    evecs = torch.empty(k * s.N, dtype=torch.float64, device="cuda")
+    ev, info = ctx.fm_eigs(shift, k, evecs=evecs)
+    assert info["converged"] == 1
+    Eo = Eo.real
+    for i in range(k):
+        assert abs(ev[i] - Eo[i]) <= 1e-9 * abs(Eo[i]), (ev, Eo)
+    # eigenvector of the nearest level: unit norm, largest entry positive, parallel to the oracle's
+    c = evecs[: s.N].cpu().numpy()
+    o = np.real(vo[:, 0])
+    o = o / np.linalg.norm(o)
+    o = o * np.sign(o[np.argmax(np.abs(o))])
+    assert abs(np.linalg.norm(c) - 1) < 1e-12 and c[np.argmax(np.abs(c))] > 0
+    assert np.linalg.norm(c - o) < 1e-7
+    assert solvers.residual(H, S, ev[0], c) < 1e-9
+
+
+def test_eigs_small_case_matches_golden(pkg):
+    """He L=0, 24x24x8 intervals: the lowest level against the stored oracle value."""
+    gold = json.load(open(os.path.join(GOLDEN, "oracle_he_l0_24x24x8.json")))
+    wl = workload("he_l0_24x24x8")
+    ctx = pkg.Context(wl, restart_m=40)
+    assert ctx.n == gold["N"]
+    ev, info = ctx.fm_eigs(wl["shift"], 2)
+    assert info["converged"] == 1
+    for i in range(2):
+        assert abs(ev[i] - gold["E"][i]) <= 1e-9 * abs(gold["E"][i])
+
+
+def test_large_case_sampled_rows(pkg):
+    """He L=0, 96x96x24 intervals (3.7M unknowns): fm_apply on sampled rows against the oracle's rows of H."""
+    from oracle.system import FMSystem
+    wl = workload("he_l0_96x96x24")
+    s = FMSystem(wl)
+    ctx = pkg.Context(wl, restart_m=8, ncv=4)
+    assert ctx.n == s.N == 3686400
+    rng = np.random.default_rng(9)
+    rows = np.sort(rng.choice(s.N, 3000, replace=False))
+    x = rand_vec(s.N, 7)
+    Hr, Sr = s.H(rows), s.S(rows)
+    E = -2.9
+    ref = Hr @ x - E * (Sr @ x)
+    y = torch.empty(s.N, dtype=torch.float64, device="cuda")
+    ctx.fm_apply(E, _dev(x), y)
+    got = y.cpu().numpy()[rows]
+    scale = np.abs(Hr).max(axis=1).toarray().ravel() * np.abs(x).max()
+    assert np.max(np.abs(got - ref) / scale) < 1e-13
