@@ -1,0 +1,310 @@
+"""Benchmark of the GB300 Faddeev-Merkuriev solver.
+
+One step = one shift-invert eigen-solve (fm_eigs, k = 1, shift -2.95) of the
+He-like L = 0 system on 96 x 96 x 24 spline intervals (3,686,400 unknowns):
+restarted Arnoldi on (H - E* S)^{-1} S, every operator application an FGMRES
+solve to 1e-12 with the tensor-trick preconditioner, every FGMRES iteration an
+operator apply, a preconditioner apply and a Gram-Schmidt step.  All of it
+runs in libfm's kernels; the start vector is seeded and resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank solves its own
+replica (independent start vector, no data-path collective: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from fm_inputs import workload, rand_vec, SEED_BASE  # noqa: E402
+
+METRIC = "Krylov iters/sec at 1e-9 eigval accuracy (time-to-solution of fm_eigs)"
+UNIT = "iters/s"
+WORKLOAD = "he_l0_96x96x24"
+SMALL = "he_l0_24x24x8"
+FP64_PEAK_TFLOPS = 1.25   # FP64 nominal of GB300 (vector and tensor pipes alike); 1.19 measured by DFMA loop
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        out_dir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv", dir=out_dir)
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def roofline(prof, peaks):
+    """The dominant kernel class (largest device time) against its roofline."""
+    bound_of = {"apply_xy": "alu", "apply_z": "alu", "coupling": "alu", "dot": "alu", "axpy": "alu",
+                "zmix": "hbm", "xmix": "hbm", "ysolve": "hbm", "other": "hbm"}
+    name = max(prof, key=lambda k: prof[k]["ms"])
+    p = prof[name]
+    n = max(p["launches"], 1)
+    per_launch_ms = p["ms"] / n
+    if bound_of[name] == "alu":
+        achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS
+        unit = "TFLOP/s"
+    else:
+        achieved = p["bytes"] / (p["ms"] * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        unit = "GB/s"
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        traffic = tr.get(WORKLOAD, {}).get(name)
+    except Exception:
+        pass
+    return {"kernel": name, "bound": bound_of[name], "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": traffic, "launches": p["launches"],
+            "ms_per_launch": per_launch_ms,
+            "peak_source": ("FP64 nominal 1.25 TFLOP/s (DFMA loop measured 1.19)" if bound_of[name] == "alu"
+                            else "MEASURED_PEAKS.json hbm_gbs")}
+
+
+def cpu_baseline_sample(seconds=20.0):
+    """The oracle (as it stands) on the host cores: preconditioned FGMRES iterations on the
+    24 x 24 x 8 He L=0 problem for a bounded time, scaled to the 96 x 96 x 24 unit count."""
+    from oracle.system import FMSystem
+    from oracle.precond import Preconditioner
+    from oracle.krylov import fgmres
+    wl = workload(SMALL)
+    big_n = 2 * 50 * 192 * 192
+    t0 = time.perf_counter()
+    s = FMSystem(wl)
+    H, S = s.H(), s.S()
+    P = Preconditioner(s, wl["shift"])
+    setup = time.perf_counter() - t0
+    b = S @ rand_vec(s.N, SEED_BASE)
+    E = wl["shift"]
+    x, info = fgmres(lambda v: H @ v - E * (S @ v), P.apply, b, tol=1e-12, m=64, max_seconds=seconds)
+    its = info["iters"] / info["seconds"]
+    return {"value": its * s.N / big_n, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"oracle preconditioned FGMRES on He L=0 24x24x8 (N={s.N}) for {info['seconds']:.1f} s "
+                       f"({info['iters']} iterations, {its:.3f} it/s at N={s.N}; setup {setup:.1f} s), "
+                       f"scaled by N to 96x96x24 (N={big_n}); NumPy/SciPy threads = host cores, SuperLU unused"),
+            "iters_per_s_small": its}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    steps = []
+    t_all = time.perf_counter()
+    for _ in range(args.warmup):
+        cpu_baseline_sample(seconds=5.0)
+    for _ in range(args.steps):
+        r = cpu_baseline_sample(seconds=args.ref_seconds)
+        steps.append(r)
+    value = statistics.mean(r["value"] for r in steps)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * (time.perf_counter() - t_all) / max(args.steps, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded N(0,1) right-hand side)", "impl": "reference",
+           "config": {"workload": WORKLOAD, "oracle_sample": SMALL},
+           "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "sample": steps[0]["sample"], "value": value,
+                            "unit": UNIT},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2005_05398_gb300 as pkg
+    from paper_2005_05398_gb300 import build
+    build.build()
+    wl = workload(args.workload)
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    ctx = pkg.Context(wl, precision=1 if args.precision == "fp32" else 0, restart_m=args.restart, ncv=args.ncv,
+                      device=local, stream=stream)
+    ctx.fm_set_shift(wl["shift"])
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    n = ctx.n
+    rng_seeds = [SEED_BASE + 1000 * rank + i for i in range(args.steps + args.warmup)]
+    v0s = [torch.tensor(rand_vec(n, sd), dtype=torch.float64, device=f"cuda:{local}") for sd in rng_seeds]
+    torch.cuda.synchronize()
+    evals = []
+    for i in range(args.warmup):
+        ev, info = ctx.fm_eigs(wl["shift"], args.k, v0=v0s[args.steps + i])
+    launches0 = ctx.fm_stats()["launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.fm_profile(1)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for i in range(args.steps):
+        ev, info = ctx.fm_eigs(wl["shift"], args.k, v0=v0s[i])
+        evals.append(ev)
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.fm_profile_read()
+    ctx.fm_profile(0)
+    clk = clocks.stop()
+    launches = ctx.fm_stats()["launches"] - launches0
+    iters = sum(i["iters"] for i in infos)
+    if dist:
+        t = torch.tensor([ms, float(iters)], dtype=torch.float64, device=f"cuda:{local}")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, iters_all = tmax[0].item(), t[1].item()
+    else:
+        ms_max, iters_all = ms, float(iters)
+    value = iters_all / (ms_max * 1e-3)
+    # end to end through the C ABI with host buffers: pinned start vector in, eigenvector out
+    e2e = None
+    if not args.no_e2e:
+        v0h = torch.tensor(rand_vec(n, SEED_BASE + 77 + rank), dtype=torch.float64).pin_memory()
+        evh = torch.empty(n * args.k, dtype=torch.float64).pin_memory()
+        ctx.fm_eigs_host(wl["shift"], args.k, v0_host=v0h, evecs_host=evh)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        it_e2e = 0
+        for i in range(args.steps):
+            _, info = ctx.fm_eigs_host(wl["shift"], args.k, v0_host=v0h, evecs_host=evh)
+            it_e2e += info["iters"]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t1
+        e2e = {"value": it_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8 * args.k + 8 * args.k,
+               "ms_per_step": 1e3 * dt / args.steps}
+    out = None
+    if rank == 0:
+        peaks = measured_peaks()
+        rl = roofline(prof, peaks)
+        kern = {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                    "share": round(v["ms"] / max(sum(p["ms"] for p in prof.values()), 1e-9), 4)} for k, v in prof.items()}
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64", "data": "synthetic (seeded N(0,1) Arnoldi start vectors)",
+               "config": {"workload": WORKLOAD, "system": "He-like L=0 (Z=2, two electrons, infinite core)",
+                          "grid": "96x96x24 intervals, cubic Hermite, R=40", "n_unknowns": n, "k": args.k,
+                          "shift": wl["shift"], "precond_precision": args.precision, "restart_m": args.restart,
+                          "ncv": args.ncv, "l2": "inputs larger than L2 (Krylov basis and factors > 129 MB)",
+                          "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+               "time_to_solution_s": ms_max / args.steps / 1e3,
+               "eigenvalue": evals[0][0], "inner_iters_per_step": iters / args.steps,
+               "setup_s": setup_s, "gpu_launches": launches, "kernels": kern,
+               "roofline": rl, "clocks": clk, "e2e": e2e}
+        if ws == 1 and not args.no_cpu_baseline:
+            cb = cpu_baseline_sample(seconds=args.ref_seconds)
+            cb.pop("iters_per_s_small", None)
+            out["cpu_baseline"] = cb
+        print(json.dumps(out))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--restart", type=int, default=40)
+    ap.add_argument("--ncv", type=int, default=20)
+    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--ref-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -174,6 +174,38 @@ const char* fm_strerror(int status);
  * created (launches) and bytes of device memory the context holds. */
 int fm_stats(const fm_ctx* ctx, int64_t* launches, int64_t* device_bytes);
 
+/* Host-side diagnostic (no GPU involved): the 1D decomposition D(A1, A2) of
+ * Eq. WW-scale exactly as fm_create computes it for the preconditioner: W-bar A1 W =
+ * diag(lam), W-bar A2 W = I, eigenvalues ascending (descending if 'descending').
+ * Row-major n x n arrays owned by the caller.  FM_ERR_COMPLEX_SPECTRUM when the
+ * pencil has complex eigenvalues, FM_ERR_NUMERIC when A2 or W is singular. */
+int fm_host_decompose(int n, const double* A1, const double* A2, int descending, double* Wbar, double* W,
+                      double* lam);
+
+/* Kernel classes of the per-kernel timing below. */
+enum {
+  FM_KERNEL_APPLY_XY = 0,  /* operator apply, y and x passes */
+  FM_KERNEL_APPLY_Z,       /* operator apply, z pass + pointwise terms + M' couplings */
+  FM_KERNEL_COUPLING,      /* V^(s) coupling gather */
+  FM_KERNEL_ZMIX,          /* preconditioner z mode products */
+  FM_KERNEL_XMIX,          /* preconditioner x mode products */
+  FM_KERNEL_YSOLVE,        /* preconditioner banded y solves */
+  FM_KERNEL_DOT,           /* Krylov multi-dot products */
+  FM_KERNEL_AXPY,          /* Krylov multi-axpy updates */
+  FM_KERNEL_OTHER,         /* copies, scalings, start vectors, combinations */
+  FM_NUM_KERNEL_CLASSES
+};
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around every
+ * launch.  enable = 1 clears the accumulators and starts recording, 0 stops. */
+int fm_profile(fm_ctx* ctx, int enable);
+
+/* Accumulated device time (ms), launch counts and algorithmic work (FLOPs and DRAM-level
+ * bytes by the per-kernel formulas of the library's documentation; flops and bytes may be
+ * NULL) per kernel class since fm_profile(ctx, 1).  Arrays have FM_NUM_KERNEL_CLASSES
+ * entries.  Synchronises the stream. */
+int fm_profile_read(fm_ctx* ctx, double* ms, int64_t* launches, double* flops, double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,7 @@ class fm_info(ctypes.Structure):
 
 
 FM_OK, FM_ERR_NOT_CONVERGED = 0, -4
+KERNEL_CLASSES = ["apply_xy", "apply_z", "coupling", "zmix", "xmix", "ysolve", "dot", "axpy", "other"]
 
 _LIB = None
 
@@ -67,6 +68,10 @@ SIGNATURES = {
     "fm_destroy": (None, [c_void_p]),
     "fm_strerror": (ctypes.c_char_p, [c_int]),
     "fm_stats": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)]),
+    "fm_profile": (c_int, [c_void_p, c_int]),
+    "fm_host_decompose": (c_int, [c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "fm_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64), ctypes.POINTER(c_double),
+                                ctypes.POINTER(c_double)]),
 }
 
 
@@ -131,6 +136,18 @@ def make_structs(wl):
     sp.y0 = wl["y0"] if math.isfinite(wl["y0"]) else float("inf")
     sp.vs_cut = wl.get("vs_cut", 0.0)
     return s, grids, len(gl), sp
+
+
+def fm_host_decompose(A1, A2, descending=False):
+    """(W-bar, W, lam) from libfm's host set-up code (numpy arrays; no GPU)."""
+    import numpy as np
+    A1 = np.ascontiguousarray(A1, dtype=np.float64)
+    A2 = np.ascontiguousarray(A2, dtype=np.float64)
+    n = A1.shape[0]
+    Wb, W, lam = np.empty((n, n)), np.empty((n, n)), np.empty(n)
+    p = lambda a: a.ctypes.data_as(c_void_p)
+    _check("fm_host_decompose", lib().fm_host_decompose(n, p(A1), p(A2), int(descending), p(Wb), p(W), p(lam)))
+    return Wb, W, lam
 
 
 class Context:
@@ -204,6 +221,15 @@ class Context:
         a, b = c_int64(), c_int64()
         _check("fm_stats", lib().fm_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
         return {"launches": a.value, "device_bytes": b.value}
+
+    def fm_profile(self, enable):
+        _check("fm_profile", lib().fm_profile(self.h, int(bool(enable))))
+
+    def fm_profile_read(self):
+        K = len(KERNEL_CLASSES)
+        ms, n, fl, by = (c_double * K)(), (c_int64 * K)(), (c_double * K)(), (c_double * K)()
+        _check("fm_profile_read", lib().fm_profile_read(self.h, ms, n, fl, by))
+        return {k: {"ms": ms[i], "launches": n[i], "flops": fl[i], "bytes": by[i]} for i, k in enumerate(KERNEL_CLASSES)}
 
     def fm_destroy(self):
         if getattr(self, "h", None):

@@ -200,6 +200,11 @@ void fm_destroy(fm_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->ev_free) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
   delete c;
@@ -289,6 +294,46 @@ int fm_stats(const fm_ctx* c, int64_t* launches, int64_t* bytes) {
   if (!c) return FM_ERR_ARG;
   if (launches) *launches = c->launches;
   if (bytes) *bytes = c->device_bytes;
+  return FM_OK;
+}
+
+int fm_host_decompose(int n, const double* A1, const double* A2, int descending, double* Wbar, double* W,
+                      double* lam) {
+  if (n < 1 || !A1 || !A2 || !Wbar || !W || !lam) return FM_ERR_ARG;
+  const int e = fmh::decompose(n, A1, A2, descending != 0, Wbar, W, lam);
+  if (e == -1) return FM_ERR_COMPLEX_SPECTRUM;
+  if (e != 0) return FM_ERR_NUMERIC;
+  return FM_OK;
+}
+
+int fm_profile(fm_ctx* c, int enable) {
+  if (!c) return FM_ERR_ARG;
+  FM_CUDA(cudaSetDevice(c->device));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  prof_harvest(c);
+  if (enable) {
+    for (int i = 0; i < FM_NUM_KERNEL_CLASSES; ++i) {
+      c->prof_ms[i] = 0.0;
+      c->prof_n[i] = 0;
+      c->prof_flops[i] = 0.0;
+      c->prof_bytes[i] = 0.0;
+    }
+  }
+  c->prof = enable != 0;
+  return FM_OK;
+}
+
+int fm_profile_read(fm_ctx* c, double* ms, int64_t* n, double* flops, double* bytes) {
+  if (!c || !ms || !n) return FM_ERR_ARG;
+  FM_CUDA(cudaSetDevice(c->device));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  prof_harvest(c);
+  for (int i = 0; i < FM_NUM_KERNEL_CLASSES; ++i) {
+    ms[i] = c->prof_ms[i];
+    n[i] = c->prof_n[i];
+    if (flops) flops[i] = c->prof_flops[i];
+    if (bytes) bytes[i] = c->prof_bytes[i];
+  }
   return FM_OK;
 }
 

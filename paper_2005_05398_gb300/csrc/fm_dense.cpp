@@ -78,7 +78,7 @@ static void balance(int n, double* A, double* D) {
         c += std::fabs(at(A, n, j, i));
         r += std::fabs(at(A, n, i, j));
       }
-      if (c == 0.0 || r == 0.0) continue;
+      if (c == 0.0 || r == 0.0 || !std::isfinite(c) || !std::isfinite(r)) continue;
       const double total = c + r;
       double f = 1.0;
       while (c * f < r / f * 0.5) f *= 2.0;
@@ -190,10 +190,10 @@ int hess_eigvals(int n, const double* Hin, double* re, double* im) {
       const double mid = 0.5 * (a + d);
       if (disc >= 0.0) {
         const double sq = std::sqrt(disc);
-        const double r1 = mid + (p >= 0.0 ? sq : -sq);
-        // the other root via the determinant for accuracy
+        // root of larger magnitude first (no cancellation), the other from the determinant
+        const double r1 = mid + (mid >= 0.0 ? sq : -sq);
         const double det = a * d - b * c;
-        const double r2 = (r1 != 0.0) ? det / r1 : mid - (p >= 0.0 ? sq : -sq);
+        const double r2 = (r1 != 0.0) ? det / r1 : 0.0;
         re[hi - 1] = r1; re[hi] = r2;
         im[hi - 1] = im[hi] = 0.0;
       } else {

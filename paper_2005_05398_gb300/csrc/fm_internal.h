@@ -123,6 +123,15 @@ struct fm_ctx {
   int evec_stage_k = 0;
   int64_t launches = 0;
   int64_t device_bytes = 0;
+  // per-kernel timing (fm_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_free;
+  struct ProfRec { int cls; cudaEvent_t a, b; };
+  std::vector<ProfRec> recs;
+  double prof_ms[FM_NUM_KERNEL_CLASSES]{};
+  int64_t prof_n[FM_NUM_KERNEL_CLASSES]{};
+  double prof_flops[FM_NUM_KERNEL_CLASSES]{};   // algorithmic work of the recorded launches
+  double prof_bytes[FM_NUM_KERNEL_CLASSES]{};
   std::vector<void*> allocs;
 };
 
@@ -143,6 +152,10 @@ int fill_normal(fm_ctx* c, double* x, uint64_t seed);
 int combine(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* Q_host, int nc, double* out, int64_t ldo);
 int absmax(fm_ctx* c, const double* x, double* val);
 int kernels_init(fm_ctx* c);
+// timing helpers: begin() returns a token for end(); no-ops unless profiling
+int prof_begin(fm_ctx* c, int cls);
+void prof_end(fm_ctx* c, int token, double flops, double bytes);
+int prof_harvest(fm_ctx* c);   // after a stream synchronisation: fold finished records
 }  // namespace fmi
 
 #define FM_CUDA(call)                                   \

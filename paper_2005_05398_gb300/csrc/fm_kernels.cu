@@ -507,8 +507,12 @@ int launch_apply(fm_ctx* c, double E, const double* x, double* y, bool only_S) {
     constexpr int TX = 8;
     const size_t smem = (size_t)3 * (TX + 2) * cp.ny * sizeof(double);
     dim3 g1((cp.nx + TX - 1) / TX, cp.nz * c->nM);
-    k_apply_xy<TX><<<g1, 256, smem, c->stream>>>(x + off, c->P + off, c->Q + off, c->R + off, cp.nx, cp.ny, cp.dx.base,
+    {
+      const int tk_ = prof_begin(c, FM_KERNEL_APPLY_XY);
+      k_apply_xy<TX><<<g1, 256, smem, c->stream>>>(x + off, c->P + off, c->Q + off, c->R + off, cp.nx, cp.ny, cp.dx.base,
                                                  cp.dx.S, cp.dx.D2, cp.dy.base, cp.dy.S, cp.dy.D2, only_S);
+      prof_end(c, tk_, (double)cp.npts * c->nM * (only_S ? 16.0 : 40.0), (double)cp.npts * c->nM * (only_S ? 16.0 : 32.0));
+    }
     c->launches++;
     ZPassArgs a;
     a.P = c->P + off; a.Q = c->Q + off; a.R = c->R + off; a.y = y + off; a.W = cp.W;
@@ -527,7 +531,11 @@ int launch_apply(fm_ctx* c, double E, const double* x, double* y, bool only_S) {
       a.lamm[iM] = lm * sqrt(1.0 + (Mp == 1 ? 1.0 : 0.0));
     }
     const int64_t tot = cp.npts * c->nM;
-    k_apply_z<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(a, only_S);
+    {
+      const int tk_ = prof_begin(c, FM_KERNEL_APPLY_Z);
+      k_apply_z<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(a, only_S);
+      prof_end(c, tk_, (double)tot * (only_S ? 8.0 : (56.0 + (c->nM > 1 ? 32.0 : 0.0))), (double)tot * (only_S ? 16.0 : 40.0));
+    }
     c->launches++;
   }
   if (!only_S) {
@@ -544,7 +552,11 @@ int launch_apply(fm_ctx* c, double E, const double* x, double* y, bool only_S) {
         a.src_off[s] = src.off; a.src_npts[s] = src.npts;
         a.snx[s] = src.nx; a.sny[s] = src.ny; a.snz[s] = src.nz;
       }
-      k_apply_coupling<<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
+      {
+        const int tk_ = prof_begin(c, FM_KERNEL_COUPLING);
+        k_apply_coupling<<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
+        prof_end(c, tk_, (double)cp.n_act * a.ns * (168.0 * c->nM + 2.0 * c->nM * c->nM), (double)cp.n_act * (4.0 + 16.0 * c->nM + a.ns * (108.0 + 8.0 * c->nM * c->nM)));
+      }
       c->launches++;
     }
   }
@@ -563,19 +575,47 @@ static int precond_impl(fm_ctx* c, const double* x, double* y, T* t) {
     const T* U = std::is_same<T, double>::value ? (const T*)cp.yU : (const T*)cp.yU32;
     const T* L = std::is_same<T, double>::value ? (const T*)cp.yL : (const T*)cp.yL32;
     T* u = std::is_same<T, double>::value ? (T*)c->u64 : (T*)c->u32;
+    const double ncomp = (double)nxy * cp.nz * c->nM;  // unknowns of this component
+    const double ts = (double)sizeof(T);
+    double yfl = 0.0, yby = 0.0;  // banded y solves: per line 2n(2kl+ku) + n flops; factors + vector bytes
+    for (int il = 0; il < cp.nl; ++il) {
+      const int nc = cp.chain_n[il], n = nc * cp.ny, kl = (nc == 1) ? 2 : 2 * nc + 1;
+      yfl += (double)cp.nx * (2.0 * n * (3.0 * kl) + n);
+      yby += (double)cp.nx * ((double)n * (3.0 * kl + 1.0) * ts + n + 2.0 * n * ts);
+    }
     dim3 gz((unsigned)((nxy + 127) / 128), c->nM);
     const size_t smz = (size_t)cp.nz * cp.nz * sizeof(T);
-    k_zmix<double, T, T><<<gz, 128, smz, c->stream>>>(Wzb, x, t, cp.nz, nxy, cp.off);
+    {
+      const int tk_ = prof_begin(c, FM_KERNEL_ZMIX);
+      k_zmix<double, T, T><<<gz, 128, smz, c->stream>>>(Wzb, x, t, cp.nz, nxy, cp.off);
+      prof_end(c, tk_, 2.0 * cp.nz * ncomp, ncomp * (8.0 + ts));
+    }
     dim3 gx((cp.ny + 63) / 64, (cp.nx + 63) / 64, c->nM * cp.nz);
-    k_xmix<T><<<gx, 256, 0, c->stream>>>(Wxb, t, u, cp.nx, cp.ny, cp.nz, cp.off, c->M0);
+    {
+      const int tk_ = prof_begin(c, FM_KERNEL_XMIX);
+      k_xmix<T><<<gx, 256, 0, c->stream>>>(Wxb, t, u, cp.nx, cp.ny, cp.nz, cp.off, c->M0);
+      prof_end(c, tk_, 2.0 * cp.nx * ncomp, 2.0 * ncomp * ts);
+    }
     YArgs ya;
     ya.nx = cp.nx; ya.ny = cp.ny; ya.nz = cp.nz; ya.M0 = c->M0; ya.nl = cp.nl; ya.comp_off = cp.off;
     ya.chain_lo = (const int*)cp.d_chain_lo; ya.chain_n = (const int*)cp.d_chain_n;
     ya.band_off = cp.d_band_off; ya.lmul_off = cp.d_lmul_off; ya.piv_off = cp.d_piv_off;
     dim3 gy((cp.nx + 127) / 128, cp.nl);
-    k_ysolve<T><<<gy, 128, 0, c->stream>>>(ya, U, L, cp.yP, u);
-    k_xmix<T><<<gx, 256, 0, c->stream>>>(Wx, u, t, cp.nx, cp.ny, cp.nz, cp.off, c->M0);
-    k_zmix<T, double, T><<<gz, 128, smz, c->stream>>>(Wz, t, y, cp.nz, nxy, cp.off);
+    {
+      const int tk_ = prof_begin(c, FM_KERNEL_YSOLVE);
+      k_ysolve<T><<<gy, 128, 0, c->stream>>>(ya, U, L, cp.yP, u);
+      prof_end(c, tk_, yfl, yby);
+    }
+    {
+      const int tk_ = prof_begin(c, FM_KERNEL_XMIX);
+      k_xmix<T><<<gx, 256, 0, c->stream>>>(Wx, u, t, cp.nx, cp.ny, cp.nz, cp.off, c->M0);
+      prof_end(c, tk_, 2.0 * cp.nx * ncomp, 2.0 * ncomp * ts);
+    }
+    {
+      const int tk_ = prof_begin(c, FM_KERNEL_ZMIX);
+      k_zmix<T, double, T><<<gz, 128, smz, c->stream>>>(Wz, t, y, cp.nz, nxy, cp.off);
+      prof_end(c, tk_, 2.0 * cp.nz * ncomp, ncomp * (8.0 + ts));
+    }
     c->launches += 5;
   }
   FM_CUDA(cudaGetLastError());
@@ -589,32 +629,52 @@ int launch_precond(fm_ctx* c, const double* x, double* y) {
 
 int dot_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, double* h_host) {
   const int nb = c->red_blocks;
-  k_dot_many<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red);
-  k_dot_finish<<<(nv + 63) / 64, 64, 0, c->stream>>>(c->red, nb, nv, c->red + (int64_t)nb * 256);
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+    k_dot_many<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red);
+    prof_end(c, tk_, 2.0 * nv * (double)c->N, (nv + 1.0) * 8.0 * (double)c->N);
+  }
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+    k_dot_finish<<<(nv + 63) / 64, 64, 0, c->stream>>>(c->red, nb, nv, c->red + (int64_t)nb * 256);
+    prof_end(c, tk_, 0.0, 0.0);
+  }
   c->launches += 2;
   FM_CUDA(cudaMemcpyAsync(h_host, c->red + (int64_t)nb * 256, nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   FM_CUDA(cudaStreamSynchronize(c->stream));
-  return FM_OK;
+  return prof_harvest(c);
 }
 
 int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double sign) {
   double* hd = c->red + (int64_t)c->red_blocks * 256 + 512;
   FM_CUDA(cudaMemcpyAsync(hd, h_host, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  k_axpy_many<<<grid_for(c->N, 256), 256, 0, c->stream>>>(V, ldv, nv, hd, sign, w, c->N);
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+    k_axpy_many<<<grid_for(c->N, 256), 256, 0, c->stream>>>(V, ldv, nv, hd, sign, w, c->N);
+    prof_end(c, tk_, 2.0 * nv * (double)c->N, (nv + 2.0) * 8.0 * (double)c->N);
+  }
   c->launches++;
   FM_CUDA(cudaGetLastError());
   return FM_OK;
 }
 
 int scale_copy(fm_ctx* c, const double* x, double a, double* y) {
-  k_axpby<<<grid_for(c->N, 256), 256, 0, c->stream>>>(a, x, 0.0, y, c->N);
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+    k_axpby<<<grid_for(c->N, 256), 256, 0, c->stream>>>(a, x, 0.0, y, c->N);
+    prof_end(c, tk_, 0.0, 0.0);
+  }
   c->launches++;
   FM_CUDA(cudaGetLastError());
   return FM_OK;
 }
 
 int axpby(fm_ctx* c, double a, const double* x, double b, double* y) {
-  k_axpby<<<grid_for(c->N, 256), 256, 0, c->stream>>>(a, x, b, y, c->N);
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+    k_axpby<<<grid_for(c->N, 256), 256, 0, c->stream>>>(a, x, b, y, c->N);
+    prof_end(c, tk_, 0.0, 0.0);
+  }
   c->launches++;
   FM_CUDA(cudaGetLastError());
   return FM_OK;
@@ -624,7 +684,11 @@ int combine(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* Q_hos
   double* qd = c->red + (int64_t)c->red_blocks * 256 + 512;
   if (nv * nc > 7680) return FM_ERR_ARG;
   FM_CUDA(cudaMemcpyAsync(qd, Q_host, (size_t)nv * nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  k_combine<<<grid_for(c->N, 256), 256, 0, c->stream>>>(V, ldv, nv, qd, nc, out, ldo, c->N);
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+    k_combine<<<grid_for(c->N, 256), 256, 0, c->stream>>>(V, ldv, nv, qd, nc, out, ldo, c->N);
+    prof_end(c, tk_, 0.0, 0.0);
+  }
   c->launches++;
   FM_CUDA(cudaGetLastError());
   FM_CUDA(cudaStreamSynchronize(c->stream));
@@ -635,7 +699,11 @@ int absmax(fm_ctx* c, const double* x, double* val) {
   const int nb = c->red_blocks;
   double* pv = c->red;
   long long* pi = (long long*)(c->red + nb);
-  k_absmax<<<nb, 256, 0, c->stream>>>(x, c->N, pv, pi);
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+    k_absmax<<<nb, 256, 0, c->stream>>>(x, c->N, pv, pi);
+    prof_end(c, tk_, 0.0, 0.0);
+  }
   c->launches++;
   std::vector<double> hv(nb);
   std::vector<long long> hi(nb);
@@ -652,6 +720,52 @@ int absmax(fm_ctx* c, const double* x, double* val) {
   return FM_OK;
 }
 
+int prof_begin(fm_ctx* c, int cls) {
+  if (!c->prof) return -1;
+  cudaEvent_t a, b;
+  for (cudaEvent_t* e : {&a, &b}) {
+    if (!c->ev_free.empty()) {
+      *e = c->ev_free.back();
+      c->ev_free.pop_back();
+    } else if (cudaEventCreate(e) != cudaSuccess) {
+      return -1;
+    }
+  }
+  cudaEventRecord(a, c->stream);
+  c->recs.push_back({cls, a, b});
+  return (int)c->recs.size() - 1;
+}
+
+void prof_end(fm_ctx* c, int token, double flops, double bytes) {
+  if (token < 0 || token >= (int)c->recs.size()) return;
+  cudaEventRecord(c->recs[token].b, c->stream);
+  c->prof_flops[c->recs[token].cls] += flops;
+  c->prof_bytes[c->recs[token].cls] += bytes;
+}
+
+int prof_harvest(fm_ctx* c) {
+  if (c->recs.empty()) return FM_OK;
+  std::vector<fm_ctx::ProfRec> keep;
+  for (auto& r : c->recs) {
+    if (cudaEventQuery(r.b) != cudaSuccess) {
+      cudaGetLastError();
+      keep.push_back(r);
+      continue;
+    }
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.cls] += ms;
+      c->prof_n[r.cls] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->ev_free.push_back(r.a);
+    c->ev_free.push_back(r.b);
+  }
+  c->recs.swap(keep);
+  return FM_OK;
+}
+
 int kernels_init(fm_ctx* c) {
   (void)c;
   FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -662,7 +776,11 @@ int kernels_init(fm_ctx* c) {
 }
 
 int fill_normal(fm_ctx* c, double* x, uint64_t seed) {
-  k_fill_normal<<<grid_for(c->N, 256), 256, 0, c->stream>>>(x, c->N, seed);
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+    k_fill_normal<<<grid_for(c->N, 256), 256, 0, c->stream>>>(x, c->N, seed);
+    prof_end(c, tk_, 0.0, 0.0);
+  }
   c->launches++;
   FM_CUDA(cudaGetLastError());
   return FM_OK;

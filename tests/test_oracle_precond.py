@@ -96,3 +96,20 @@ def test_computed_z_gives_exact_inverse(J, tau):
         full = np.zeros(s.N)
         full[s.off[a]:s.off[a] + g.csize] = L @ v
         assert np.linalg.norm(P.apply(full)[s.off[a]:s.off[a] + g.csize] - v) < 1e-12 * np.linalg.norm(v)
+
+
+def test_oracle_fgmres_matches_sparse_lu():
+    """The oracle's preconditioned GMRES reaches the sparse-LU solution of (H - E S) x = b."""
+    from oracle import solvers
+    from oracle.krylov import fgmres
+    wl = workload("he_l0_24x24x8", nint=(6, 7, 4), R=(18.0, 16.0))
+    s = FMSystem(wl)
+    H, S = s.H(), s.S()
+    E = -2.6
+    P = Preconditioner(s, E)
+    b = np.random.default_rng(14).standard_normal(s.N)
+    x, info = fgmres(lambda v: H @ v - E * (S @ v), P.apply, b, tol=1e-12, m=40)
+    ref = solvers.solve(H, S, E, b)
+    assert info["resid"] < 1e-12
+    assert np.linalg.norm(x - ref) < 1e-9 * np.linalg.norm(ref)
+    assert info["iters"] < 100  # the preconditioner is effective (unpreconditioned GMRES stalls)
