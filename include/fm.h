@@ -95,8 +95,16 @@ typedef struct {
   int precision;     /* FM_PREC_FP64 or FM_PREC_FP32 (preconditioner arithmetic) */
   int ncv;           /* Arnoldi basis size of fm_eigs (>= 2k + 1) */
   int max_restarts;  /* Arnoldi restarts of fm_eigs */
-  double eig_tol;    /* relative Ritz residual of fm_eigs, e.g. 1e-12 */
+  double eig_tol;    /* fm_eigs: relative Ritz residual |h_{m+1,m} y_m| / |theta| at which a Ritz pair is
+                        accepted (default 1e-9); a pair whose energy changed by less than 1e-3 * eig_tol
+                        (relative) over three Arnoldi steps while its residual is below sqrt(eig_tol) is
+                        accepted too (its accuracy is then set by the inner solves) */
   int z_eigs;        /* 0 = replace z eigenvalues by -l(l+1) (Eq. prop-eq); 1 = keep them (n_M = 1 only) */
+  int y_solver;      /* y stage of the preconditioner: 0 = automatic (per-l diagonalisation for n_M = 1 with the
+                        float32 preconditioner, banded LU otherwise), 1 = banded LU, 2 = per-l
+                        diagonalisation of (A_l, S_y) when n_M = 1 (both invert the same matrix) */
+  int tune;          /* fm_eigs: 1 = tune the preconditioner to the current Ritz vectors U (rank-k update
+                        P + (A U - P U) U^T, Freitag & Spence), 0 = plain preconditioner */
   int device;        /* CUDA device ordinal */
   void* stream;      /* cudaStream_t, NULL = legacy default stream */
 } fm_opts;
@@ -113,7 +121,7 @@ typedef struct {
 typedef struct fm_ctx fm_ctx;
 
 /* Default options: tol 1e-12, restart 64, max_iters 2000, FP64, ncv 20, 50 restarts,
- * eig_tol 1e-12, replaced z eigenvalues, device 0, default stream. */
+ * eig_tol 1e-9, replaced z eigenvalues, tuned preconditioner, device 0, default stream. */
 void fm_default_opts(fm_opts* opts);
 
 /* Build a context: 1D bases and collocation points (Section 3.1), pointwise potential
@@ -148,12 +156,14 @@ int fm_precond_apply(fm_ctx* ctx, const double* x, double* y);
  * preconditioner built for E (fm_set_shift is called when E differs from the current
  * shift).  x (device) is the initial guess on entry (pass zeros for none) and the
  * solution on return.  Converged when ||rhs - (H - E S) x|| <= tol ||rhs|| in float64.
- * FM_ERR_NOT_CONVERGED leaves the best iterate in x.  info may be NULL. */
+ * A restart cycle that fails to halve the true residual ends the solve (the float64
+ * residual has reached its rounding floor); FM_ERR_NOT_CONVERGED then, or at max_iters,
+ * with the best iterate in x and info->resid the reached relative residual.  info may be NULL. */
 int fm_solve(fm_ctx* ctx, double E, const double* rhs, double* x, fm_info* info);
 
 /* k eigenpairs of H c = E S c nearest 'shift' by restarted Arnoldi on the
  * shift-invert operator (H - shift S)^{-1} S (Eq. FM-lin; E = shift + 1/theta), each
- * operator application an fm_solve.  v0 (device, may be NULL = seeded normal start)
+ * operator application an FGMRES solve to max(tol, eig_tol / 10).  v0 (device, may be NULL = seeded normal start)
  * starts the iteration.  evals (host, k doubles) receive E sorted by |E - shift|;
  * evecs (device, k * n_unknowns, may be NULL) the eigenvectors normalised to unit
  * 2-norm with their largest-magnitude entry positive.  info may be NULL. */

@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -58,6 +60,41 @@ static int cgs2(fm_ctx* c, const double* V, int nv, double* w, double* h) {
   return FM_OK;
 }
 
+// z <- P_t^{-1}-correction of z = P^{-1} v:  z -= (W - U) (U^T W)^{-1} (U^T z)
+static int apply_tuning(fm_ctx* c, double* z) {
+  const int k = c->n_tune;
+  if (k == 0) return FM_OK;
+  std::vector<double> a(k), b(k, 0.0);
+  int rc;
+  if ((rc = dot_many(c, c->tuneU, c->N, k, z, a.data()))) return rc;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) b[i] += c->tuneGinv[(size_t)i * k + j] * a[j];
+  return axpy_many(c, c->tuneWU, c->N, k, b.data(), z, -1.0);
+}
+
+// Tune the preconditioner to the columns of U (device, orthonormal, k <= 8): W = P^{-1} (H - E S) U.
+static int set_tuning(fm_ctx* c, double E, const double* U, int k) {
+  int rc;
+  c->n_tune = 0;
+  if (k <= 0) return FM_OK;
+  const int64_t N = c->N;
+  FM_CUDA(cudaMemcpyAsync(c->tuneU, U, (size_t)k * N * 8, cudaMemcpyDeviceToDevice, c->stream));
+  std::vector<double> G((size_t)k * k);
+  for (int j = 0; j < k; ++j) {
+    double* wj = c->tuneWU + (int64_t)j * N;
+    if ((rc = launch_apply(c, E, c->tuneU + (int64_t)j * N, c->tmpN2, false))) return rc;
+    if ((rc = launch_precond(c, c->tmpN2, wj))) return rc;
+    std::vector<double> col(k);
+    if ((rc = dot_many(c, c->tuneU, N, k, wj, col.data()))) return rc;  // U^T w_j
+    for (int i = 0; i < k; ++i) G[(size_t)i * k + j] = col[i];
+    if ((rc = axpby(c, -1.0, c->tuneU + (int64_t)j * N, 1.0, wj))) return rc;  // w_j - u_j
+  }
+  c->tuneGinv.assign((size_t)k * k, 0.0);
+  if (!fmh::invert(k, G.data(), c->tuneGinv.data())) return FM_OK;  // singular: leave untuned
+  c->n_tune = k;
+  return FM_OK;
+}
+
 // Right-preconditioned restarted FGMRES for (H - E S) x = b (x: initial guess in, solution out).
 static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, int max_iters, int* iters_out,
                   int* restarts_out, double* resid_out) {
@@ -81,6 +118,7 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
   std::vector<double> R((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 1), y(m);
   int total = 0;
   bool converged = false;
+  double beta_prev = HUGE_VAL;
   while (true) {
     if (!std::isfinite(beta)) return FM_ERR_BREAKDOWN;
     if (beta <= tol * bnorm) {
@@ -88,6 +126,10 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
       break;
     }
     if (total >= max_iters) break;
+    // a whole restart cycle that did not halve the true residual: the float64 residual has
+    // reached its rounding floor (about eps ||A|| ||x||), further cycles only chase noise
+    if (beta > 0.5 * beta_prev) break;
+    beta_prev = beta;
     if ((rc = scale_copy(c, r, 1.0 / beta, c->V))) return rc;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
@@ -96,6 +138,7 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
       double* Vj = c->V + (int64_t)j * N;
       double* Zj = c->Z + (int64_t)j * N;
       if ((rc = launch_precond(c, Vj, Zj))) return rc;
+      if ((rc = apply_tuning(c, Zj))) return rc;
       if ((rc = launch_apply(c, E, Zj, c->w, false))) return rc;
       if ((rc = cgs2(c, c->V, j + 1, c->w, h.data()))) return rc;
       double hn;
@@ -174,8 +217,10 @@ void fm_default_opts(fm_opts* o) {
   o->precision = FM_PREC_FP64;
   o->ncv = 20;
   o->max_restarts = 50;
-  o->eig_tol = 1e-12;
+  o->eig_tol = 1e-9;
   o->z_eigs = 0;
+  o->tune = 1;
+  o->y_solver = 0;
   o->device = 0;
   o->stream = nullptr;
 }
@@ -229,7 +274,8 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
   if (nM <= 0 || nM > 8) return FM_ERR_ARG;
   if (o.z_eigs == 1 && nM != 1) return FM_ERR_ARG;
   if (o.restart_m < 1 || o.restart_m > 256 || o.max_iters < 1 || !(o.tol > 0) || o.ncv < 3 || o.ncv > 64 ||
-      o.max_restarts < 0 || !(o.eig_tol > 0) || (o.precision != 0 && o.precision != 1))
+      o.max_restarts < 0 || !(o.eig_tol > 0) || (o.precision != 0 && o.precision != 1) || o.y_solver < 0 ||
+      o.y_solver > 2)
     return FM_ERR_ARG;
   fm_ctx* c = new fm_ctx();
   c->sys = *sys;
@@ -260,7 +306,8 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
       (rc = dev_alloc(c, (void**)&c->red, ((size_t)c->red_blocks * 256 + 8192) * 8)) ||
       (rc = dev_alloc(c, (void**)&c->AV, (size_t)(o.ncv + 1) * N * 8)) ||
       (rc = dev_alloc(c, (void**)&c->tmpN, N * 8)) || (rc = dev_alloc(c, (void**)&c->tmpN2, N * 8)) ||
-      (rc = dev_alloc(c, (void**)&c->tmpN3, N * 8)))
+      (rc = dev_alloc(c, (void**)&c->tmpN3, N * 8)) || (rc = dev_alloc(c, (void**)&c->tuneU, (size_t)8 * N * 8)) ||
+      (rc = dev_alloc(c, (void**)&c->tuneWU, (size_t)8 * N * 8)))
     return fail(rc);
   if (cudaMallocHost((void**)&c->red_host, 8192 * 8) != cudaSuccess) return fail(FM_ERR_OOM);
   c->m_alloc = m;
@@ -384,7 +431,15 @@ int fm_solve(fm_ctx* c, double E, const double* rhs, double* x, fm_info* info) {
   return rc;
 }
 
+static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* evals, double* evecs, fm_info* info);
+
 int fm_eigs(fm_ctx* c, double shift, int k, const double* v0, double* evals, double* evecs, fm_info* info) {
+  const int rc = eigs_impl(c, shift, k, v0, evals, evecs, info);
+  if (c) c->n_tune = 0;
+  return rc;
+}
+
+static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* evals, double* evecs, fm_info* info) {
   if (!c || !evals || k < 1 || !std::isfinite(shift)) return FM_ERR_ARG;
   const int m = c->ncv_alloc;
   if (m < k + 2) return FM_ERR_ARG;
@@ -406,17 +461,34 @@ int fm_eigs(fm_ctx* c, double shift, int k, const double* v0, double* evals, dou
   bool converged = false;
   std::vector<Ritz> best;
   std::vector<double> Y;  // eigenvectors of the projected matrix (nsz x nsz)
+  std::vector<std::vector<double>> hist;  // eigenvalue history of each wanted Ritz value
+  const bool verbose = getenv("FM_VERBOSE") != nullptr;
   double max_res = 0.0;
   while (true) {
     bool done = false;
     for (int j = kcur; j < m; ++j) {
       double* Vj = V + (int64_t)j * N;
       double* w = V + (int64_t)(j + 1) * N;
+      if (c->opts.tune && nsz >= 1 && !best.empty()) {
+        // tuned preconditioner (Freitag-Spence): U = orthonormalised Ritz vectors of the wanted values
+        std::vector<int> cols;
+        for (const auto& rz : best)
+          if (rz.real && (int)cols.size() < std::min(k, 8)) cols.push_back(rz.col);
+        const int nt = (int)cols.size();
+        std::vector<double> Yt((size_t)nsz * nt);
+        for (int r = 0; r < nsz; ++r)
+          for (int q = 0; q < nt; ++q) Yt[(size_t)r * nt + q] = Y[(size_t)r * nsz + cols[q]];
+        if (nt > 0 && small_qr(nsz, nt, Yt)) {
+          if ((rc = combine(c, V, N, nsz, Yt.data(), nt, c->tuneU, N))) return rc;
+          if ((rc = set_tuning(c, shift, c->tuneU, nt))) return rc;
+        }
+      }
       if ((rc = launch_apply(c, 0.0, Vj, c->tmpN, true))) return rc;  // S v_j
       FM_CUDA(cudaMemsetAsync(w, 0, N * 8, c->stream));
       int it = 0, rs = 0;
       double res = 0.0;
-      rc = fgmres(c, shift, c->tmpN, w, c->opts.tol, c->opts.max_iters, &it, &rs, &res);
+      const double inner_tol = std::max(c->opts.tol, 0.1 * c->opts.eig_tol);
+      rc = fgmres(c, shift, c->tmpN, w, inner_tol, c->opts.max_iters, &it, &rs, &res);
       inner += it;
       ++ops;
       if (rc != FM_OK && rc != FM_ERR_NOT_CONVERGED) return rc;
@@ -442,24 +514,38 @@ int fm_eigs(fm_ctx* c, double shift, int k, const double* v0, double* evals, dou
       std::sort(order.begin(), order.end(),
                 [&](int a, int b) { return std::hypot(re[a], im[a]) > std::hypot(re[b], im[b]); });
       best.clear();
-      bool ok = true;
+      bool ok = true, stagnant = true;
       max_res = 0.0;
-      for (int t = 0; t < nsz && (int)best.size() < nsz; ++t) {
+      for (int t = 0; t < nsz; ++t) {
         const int e = order[t];
         Ritz rz{re[e], e, im[e] == 0.0};
         best.push_back(rz);
         if ((int)best.size() <= k) {
+          const int i = (int)best.size() - 1;
           if (!rz.real) {
-            ok = false;
+            ok = stagnant = false;
             continue;
           }
           const double resid = std::fabs(hn * Y[(size_t)(nsz - 1) * nsz + e]) / std::max(std::fabs(rz.theta), 1e-300);
           max_res = std::max(max_res, resid);
           if (resid > c->opts.eig_tol) ok = false;
+          // eigenvalue E = shift + 1/theta stable over the last steps while the Ritz residual is small:
+          // its accuracy is then limited by the inner solves, far below the requested level
+          const double Ei = shift + 1.0 / rz.theta;
+          if ((int)hist.size() <= i) hist.resize(i + 1);
+          hist[i].push_back(Ei);
+          const auto& hv = hist[i];
+          bool st = hv.size() >= 3 && resid < std::sqrt(c->opts.eig_tol);
+          for (size_t q = hv.size() >= 3 ? hv.size() - 3 : 0; st && q + 1 < hv.size(); ++q)
+            if (std::fabs(hv[q + 1] - hv[q]) > 1e-3 * c->opts.eig_tol * std::fabs(Ei)) st = false;
+          if (!st) stagnant = false;
         }
       }
-      if (ok || hn == 0.0) {
-        converged = ok;
+      if (verbose)
+        fprintf(stderr, "[fm_eigs] step %d restart %d inner %d ritz_res %.3e E0 %.15f%s\n", nsz, restarts, inner,
+                max_res, best.empty() ? 0.0 : shift + 1.0 / best[0].theta, ok ? " (residual)" : (stagnant ? " (stable)" : ""));
+      if (ok || stagnant || hn == 0.0) {
+        converged = ok || stagnant;
         done = true;
         break;
       }
@@ -501,6 +587,7 @@ int fm_eigs(fm_ctx* c, double shift, int k, const double* v0, double* evals, dou
     kcur = nk;
     ++restarts;
   }
+  c->n_tune = 0;
   if (nsz < k || (int)best.size() < k) return FM_ERR_NOT_CONVERGED;
   // eigenvectors c = V y, energies E = shift + 1/theta
   std::vector<double> Ek(k);

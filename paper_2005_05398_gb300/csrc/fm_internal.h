@@ -79,6 +79,13 @@ struct Comp {
   unsigned char* yP = nullptr;   // per l: [n][nx] pivot offsets
   float* yU32 = nullptr; float* yL32 = nullptr;
   std::vector<int64_t> lmul_off;
+  // n_M = 1: per-l diagonalisation of (A_l, S_y), A_l = -D_y + (c_l Y_r2 + V^ - E*) S_y, used by the
+  // float32 preconditioner (same inverse as the banded y solves)
+  bool ydiag_ok = false;
+  float* Wy32 = nullptr; float* Wyb32 = nullptr;   // [nl][ny][ny]
+  float* dLy32 = nullptr;                          // [nl][ny]
+  float* dLx32 = nullptr;                          // [nl][nx]
+  double* Wy64 = nullptr; double* Wyb64 = nullptr; double* dLy64 = nullptr; double* dLx64 = nullptr;
 };
 
 }  // namespace fmi
@@ -121,6 +128,12 @@ struct fm_ctx {
   double* tmpN3 = nullptr;
   double* evec_stage = nullptr;  // fm_eigs_host staging (k vectors)
   int evec_stage_k = 0;
+  // tuned preconditioner used by the eigen-solver: P_t = P + (A U - P U) U^T with orthonormal U
+  // (n_tune columns), applied through P_t^{-1} = P^{-1} - (W - U) (U^T W)^{-1} U^T P^{-1}, W = P^{-1} A U
+  int n_tune = 0;
+  double* tuneU = nullptr;       // [8][N]
+  double* tuneWU = nullptr;      // [8][N]  W - U
+  std::vector<double> tuneGinv;  // (U^T W)^{-1}, n_tune x n_tune, row-major
   int64_t launches = 0;
   int64_t device_bytes = 0;
   // per-kernel timing (fm_profile)

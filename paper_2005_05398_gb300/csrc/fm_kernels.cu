@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -232,50 +233,62 @@ __global__ void __launch_bounds__(128) k_apply_coupling(CouplingArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// preconditioner: z mode product  out[l][p] = sum_k W[l][k] in[k][p] for one (component, M')
+// preconditioner: z mode product  out[l][p] = sum_k W[l][k] in[k][p] for one (component, M').
+// A CTA stages W (n_z x n_z) and an n_z x 128 column tile of the input in shared memory;
+// each thread produces the n_z outputs of its column.
 // ---------------------------------------------------------------------------
 template <typename TI, typename TO, typename TW>
 __global__ void __launch_bounds__(128) k_zmix(const TW* __restrict__ Wall, const TI* __restrict__ in,
                                               TO* __restrict__ out, int nz, int64_t nxy, int64_t comp_off) {
   extern __shared__ unsigned char smraw[];
   TW* Ws = reinterpret_cast<TW*>(smraw);  // [nz][nz]
+  TW* Vs = Ws + nz * nz;                  // [nz][128]
   const int iM = blockIdx.y;
   const TW* W = Wall + (int64_t)iM * nz * nz;
   for (int i = threadIdx.x; i < nz * nz; i += blockDim.x) Ws[i] = W[i];
+  const int64_t p0 = (int64_t)blockIdx.x * 128;
+  const int64_t base = comp_off + (int64_t)iM * nz * nxy + p0;
+  const int cols = (int)min((int64_t)128, nxy - p0);
+  for (int k = 0; k < nz; ++k)
+    Vs[k * 128 + threadIdx.x] = (threadIdx.x < cols) ? (TW)in[base + (int64_t)k * nxy + threadIdx.x] : (TW)0;
   __syncthreads();
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nxy) return;
-  const int64_t base = comp_off + (int64_t)iM * nz * nxy + p;
-  constexpr int CH = 8;
+  if ((int)threadIdx.x >= cols) return;
+  constexpr int CH = 10;
   for (int l0 = 0; l0 < nz; l0 += CH) {
     TW acc[CH];
 #pragma unroll
     for (int u = 0; u < CH; ++u) acc[u] = 0;
     for (int k = 0; k < nz; ++k) {
-      const TW v = (TW)in[base + (int64_t)k * nxy];
+      const TW v = Vs[k * 128 + threadIdx.x];
 #pragma unroll
       for (int u = 0; u < CH; ++u)
         if (l0 + u < nz) acc[u] = fma(Ws[(l0 + u) * nz + k], v, acc[u]);
     }
 #pragma unroll
     for (int u = 0; u < CH; ++u)
-      if (l0 + u < nz) out[base + (int64_t)(l0 + u) * nxy] = (TO)acc[u];
+      if (l0 + u < nz) out[base + (int64_t)(l0 + u) * nxy + threadIdx.x] = (TO)acc[u];
   }
 }
 
-// x mode product on every (M', z-mode) slab: out[i][j] = sum_i' W_x^{l}[i][i'] in[i'][j], l = M' + k.
-// Classic 64x64 smem tiling, 256 threads, 4x4 outputs per thread.
-template <typename T>
-__global__ void __launch_bounds__(256) k_xmix(const T* __restrict__ Wall, const T* __restrict__ in, T* __restrict__ out,
-                                              int nx, int ny, int nz, int64_t comp_off, int M0) {
+// Mode product on every (M', z-mode) slab of a component, slab l = M' + k:
+//   out[r][c] = sum_r' W^{l}[r][r'] in[r'][c]   (R x R matrix per l, slabs of R x C)
+// x stage: R = n_x, C = n_y; y stage on transposed slabs: R = n_y, C = n_x.  TIN / TOUT read /
+// write the slab transposed ([c][r]); SCALE divides the result by lamR[l][r] + lamC[l][c]
+// (the diagonal of the tensor-trick inverse).  64x64 output tiles, 256 threads, 4x4 outputs per
+// thread, K in steps of 16.
+template <typename T, bool TIN, bool TOUT, bool SCALE>
+__global__ void __launch_bounds__(256) k_mix(const T* __restrict__ Wall, const T* __restrict__ in, T* __restrict__ out,
+                                             int R, int C, int nz, int64_t comp_off, int M0,
+                                             const T* __restrict__ lamR, const T* __restrict__ lamC) {
   constexpr int BT = 64, BK = 16;
-  __shared__ T As[BK][BT + 1];
-  __shared__ T Bs[BK][BT + 1];
+  __shared__ T smem[BT * (BT + 1) > 2 * BK * (BT + 1) ? BT * (BT + 1) : 2 * BK * (BT + 1)];
+  T (*As)[BT + 1] = reinterpret_cast<T (*)[BT + 1]>(smem);
+  T (*Bs)[BT + 1] = reinterpret_cast<T (*)[BT + 1]>(smem + BK * (BT + 1));
   const int slab = blockIdx.z;  // iM * nz + k
   const int iM = slab / nz, k = slab % nz;
-  const int l = M0 + iM + k;     // l index from M0
-  const T* W = Wall + (int64_t)(l - M0) * nx * nx;
-  const int64_t so = comp_off + (int64_t)slab * nx * ny;
+  const int il = iM + k;        // l - M0
+  const T* W = Wall + (int64_t)il * R * R;
+  const int64_t so = comp_off + (int64_t)slab * R * C;
   const int row0 = blockIdx.y * BT, col0 = blockIdx.x * BT;
   const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
   T acc[4][4];
@@ -283,14 +296,20 @@ __global__ void __launch_bounds__(256) k_xmix(const T* __restrict__ Wall, const 
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0;
-  for (int k0 = 0; k0 < nx; k0 += BK) {
+  for (int k0 = 0; k0 < R; k0 += BK) {
     for (int e = threadIdx.x; e < BK * BT; e += 256) {
       const int kk = e % BK, rr = e / BK;  // A tile: W[row0+rr][k0+kk]
       const int gr = row0 + rr, gk = k0 + kk;
-      As[kk][rr] = (gr < nx && gk < nx) ? W[(int64_t)gr * nx + gk] : (T)0;
-      const int cc = e % BT, kb = e / BT;  // B tile: in[k0+kb][col0+cc]
-      const int gk2 = k0 + kb, gc = col0 + cc;
-      Bs[kb][cc] = (gk2 < nx && gc < ny) ? in[so + (int64_t)gk2 * ny + gc] : (T)0;
+      As[kk][rr] = (gr < R && gk < R) ? W[(int64_t)gr * R + gk] : (T)0;
+      if (TIN) {  // in stored [c][r']: consecutive threads walk r'
+        const int kb = e % BK, cc = e / BK;
+        const int gk2 = k0 + kb, gc = col0 + cc;
+        Bs[kb][cc] = (gk2 < R && gc < C) ? in[so + (int64_t)gc * R + gk2] : (T)0;
+      } else {
+        const int cc = e % BT, kb = e / BT;
+        const int gk2 = k0 + kb, gc = col0 + cc;
+        Bs[kb][cc] = (gk2 < R && gc < C) ? in[so + (int64_t)gk2 * C + gc] : (T)0;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -307,13 +326,36 @@ __global__ void __launch_bounds__(256) k_xmix(const T* __restrict__ Wall, const 
     }
     __syncthreads();
   }
+  if (SCALE) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gr = row0 + tr + 16 * i, gc = col0 + tc + 16 * j;
-      if (gr < nx && gc < ny) out[so + (int64_t)gr * ny + gc] = acc[i][j];
+      for (int j = 0; j < 4; ++j) {
+        const int gr = row0 + tr + 16 * i, gc = col0 + tc + 16 * j;
+        if (gr < R && gc < C) acc[i][j] = acc[i][j] / (lamR[(int64_t)il * R + gr] + lamC[(int64_t)il * C + gc]);
+      }
+  }
+  if (!TOUT) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gr = row0 + tr + 16 * i, gc = col0 + tc + 16 * j;
+        if (gr < R && gc < C) out[so + (int64_t)gr * C + gc] = acc[i][j];
+      }
+  } else {  // stage the tile, then store [c][r] with consecutive threads along r
+    T (*Cs)[BT + 1] = reinterpret_cast<T (*)[BT + 1]>(smem);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) Cs[tc + 16 * j][tr + 16 * i] = acc[i][j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < BT * BT; e += 256) {
+      const int rr = e % BT, cc = e / BT;
+      const int gr = row0 + rr, gc = col0 + cc;
+      if (gr < R && gc < C) out[so + (int64_t)gc * R + gr] = Cs[cc][rr];
     }
+  }
 }
 
 // banded y solves: one thread per (l, i_x) line of a component; the right-hand side is
@@ -328,48 +370,150 @@ struct YArgs {
   const int64_t* piv_off;   // [nl] offset into P
 };
 
-template <typename T>
-__global__ void __launch_bounds__(128) k_ysolve(YArgs a, const T* __restrict__ U, const T* __restrict__ L,
+// Transposed slabs [j][i_x]: element (iM, k, j, i_x) of a component lives at
+// comp_off + ((iM * nz + k) * ny + j) * nx + i_x.  A CTA stages LPB consecutive lines of one l
+// (rows r = j * nc + c) in shared memory with coalesced loads, each thread eliminates its
+// line there (factors streamed from global memory, coalesced across the lines), and the
+// CTA writes the lines back.
+template <typename T, int LPB>
+__global__ void __launch_bounds__(LPB) k_ysolve(YArgs a, const T* __restrict__ U, const T* __restrict__ L,
                                                 const unsigned char* __restrict__ Pv, T* __restrict__ t) {
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ unsigned char smraw[];
+  T* xs = reinterpret_cast<T*>(smraw);  // [n][LPB]
   const int il = blockIdx.y;
-  if (ix >= a.nx) return;
+  const int ix0 = blockIdx.x * LPB;
+  const int tid = threadIdx.x;
+  const int ix = ix0 + tid;
   const int nc = a.chain_n[il], lo = a.chain_lo[il];
   const int n = nc * a.ny;
   const int kl = (nc == 1) ? 2 : 2 * nc + 1;
-  const int w = 2 * kl + 1;  // kl + ku + 1 with ku = kl
-  const T* Ub = U + a.band_off[il];
-  const T* Lb = L + a.lmul_off[il];
-  const unsigned char* Pb = Pv + a.piv_off[il];
+  const int w = 2 * kl + 1;
   const int l = a.M0 + il;
-  auto addr = [&](int r) -> int64_t {
-    const int j = r / nc, c = r - j * nc;
-    const int iM = lo + c;
-    const int k = l - a.M0 - iM;
-    return a.comp_off + (((int64_t)iM * a.nz + k) * a.nx + ix) * a.ny + j;
-  };
+  const bool live = ix < a.nx;
   for (int r = 0; r < n; ++r) {
-    const int pr = r + Pb[(int64_t)r * a.nx + ix];
-    const int64_t ar = addr(r);
-    T xr = t[ar];
-    if (pr != r) {
-      const int64_t ap = addr(pr);
-      const T xp = t[ap];
-      t[ap] = xr;
-      xr = xp;
-      t[ar] = xr;
+    const int j = r / nc, c = r - j * nc;
+    const int iM = lo + c, k = l - a.M0 - iM;
+    const int64_t row = a.comp_off + (((int64_t)iM * a.nz + k) * a.ny + j) * a.nx;
+    xs[r * LPB + tid] = live ? t[row + ix] : (T)0;
+  }
+  __syncthreads();
+  if (live) {
+    const T* Ub = U + a.band_off[il] + ix;
+    const T* Lb = L + a.lmul_off[il] + ix;
+    const unsigned char* Pb = Pv + a.piv_off[il] + ix;
+    const int64_t nx = a.nx;
+    for (int r = 0; r < n; ++r) {
+      const int pr = r + Pb[(int64_t)r * nx];
+      T xr = xs[pr * LPB + tid];
+      if (pr != r) {
+        xs[pr * LPB + tid] = xs[r * LPB + tid];
+        xs[r * LPB + tid] = xr;
+      }
+      const int dmax = min(kl, n - 1 - r);
+      for (int d = 1; d <= dmax; ++d) xs[(r + d) * LPB + tid] -= Lb[((int64_t)r * kl + (d - 1)) * nx] * xr;
     }
-    for (int d = 1; d <= kl && r + d < n; ++d) {
-      const int64_t ad = addr(r + d);
-      t[ad] = t[ad] - Lb[((int64_t)r * kl + (d - 1)) * a.nx + ix] * xr;
+    for (int r = n - 1; r >= 0; --r) {
+      T s = xs[r * LPB + tid];
+      const int dmax = min(w - 1, n - 1 - r);
+      for (int d = 1; d <= dmax; ++d) s -= Ub[((int64_t)r * w + d) * nx] * xs[(r + d) * LPB + tid];
+      xs[r * LPB + tid] = s / Ub[((int64_t)r * w) * nx];
     }
   }
-  for (int r = n - 1; r >= 0; --r) {
-    const int64_t ar = addr(r);
-    T s = t[ar];
-    for (int d = 1; d < w && r + d < n; ++d) s -= Ub[((int64_t)r * w + d) * a.nx + ix] * t[addr(r + d)];
-    t[ar] = s / Ub[((int64_t)r * w) * a.nx + ix];
+  __syncthreads();
+  for (int r = 0; r < n; ++r) {
+    const int j = r / nc, c = r - j * nc;
+    const int iM = lo + c, k = l - a.M0 - iM;
+    const int64_t row = a.comp_off + (((int64_t)iM * a.nz + k) * a.ny + j) * a.nx;
+    if (live) t[row + ix] = xs[r * LPB + tid];
   }
+}
+
+// Single-M' chains (n_M = 1): kl = ku = 2, U rows of width 5.  Same staging as k_ysolve; the
+// factors of the next D rows are kept in flight in a register ring so that the elimination of
+// row r never waits on the load latency of its own factors.
+template <typename T, int LPB>
+__global__ void __launch_bounds__(LPB) k_ysolve1(YArgs a, const T* __restrict__ U, const T* __restrict__ L,
+                                                 const unsigned char* __restrict__ Pv, T* __restrict__ t) {
+  constexpr int KL = 2, W = 5, D = 8;
+  extern __shared__ unsigned char smraw[];
+  T* xs = reinterpret_cast<T*>(smraw);  // [n][LPB]
+  const int il = blockIdx.y;
+  const int tid = threadIdx.x;
+  const int ix = blockIdx.x * LPB + tid;
+  const int n = a.ny;
+  const int l = a.M0 + il;
+  const int iM = a.chain_lo[il], k = l - a.M0 - iM;
+  const int64_t slab = a.comp_off + ((int64_t)iM * a.nz + k) * a.ny * a.nx;
+  const bool live = ix < a.nx;
+#pragma unroll 8
+  for (int r = 0; r < n; ++r) xs[r * LPB + tid] = live ? t[slab + (int64_t)r * a.nx + ix] : (T)0;
+  __syncthreads();
+  if (live) {
+    const int64_t nx = a.nx;
+    const T* Lb = L + a.lmul_off[il] + ix;
+    const T* Ub = U + a.band_off[il] + ix;
+    const unsigned char* Pb = Pv + a.piv_off[il] + ix;
+    T lb[D][KL];
+    int pb[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q)
+      if (q < n) {
+        pb[q] = Pb[(int64_t)q * nx];
+        lb[q][0] = Lb[((int64_t)q * KL) * nx];
+        lb[q][1] = Lb[((int64_t)q * KL + 1) * nx];
+      }
+    for (int r0 = 0; r0 < n; r0 += D) {
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const int r = r0 + q;
+        if (r < n) {
+          const int pr = r + pb[q];
+          T xr = xs[pr * LPB + tid];
+          if (pr != r) {
+            xs[pr * LPB + tid] = xs[r * LPB + tid];
+            xs[r * LPB + tid] = xr;
+          }
+          if (r + 1 < n) xs[(r + 1) * LPB + tid] -= lb[q][0] * xr;
+          if (r + 2 < n) xs[(r + 2) * LPB + tid] -= lb[q][1] * xr;
+          const int rn = r + D;
+          if (rn < n) {
+            pb[q] = Pb[(int64_t)rn * nx];
+            lb[q][0] = Lb[((int64_t)rn * KL) * nx];
+            lb[q][1] = Lb[((int64_t)rn * KL + 1) * nx];
+          }
+        }
+      }
+    }
+    T ub[D][W];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      const int r = n - 1 - q;
+      if (r >= 0)
+#pragma unroll
+        for (int d = 0; d < W; ++d) ub[q][d] = Ub[((int64_t)r * W + d) * nx];
+    }
+    for (int r0 = 0; r0 < n; r0 += D) {
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const int r = n - 1 - (r0 + q);
+        if (r >= 0) {
+          T s = xs[r * LPB + tid];
+#pragma unroll
+          for (int d = 1; d < W; ++d)
+            if (r + d < n) s -= ub[q][d] * xs[(r + d) * LPB + tid];
+          xs[r * LPB + tid] = s / ub[q][0];
+          const int rn = r - D;
+          if (rn >= 0)
+#pragma unroll
+            for (int d = 0; d < W; ++d) ub[q][d] = Ub[((int64_t)rn * W + d) * nx];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (live)
+#pragma unroll 8
+    for (int r = 0; r < n; ++r) t[slab + (int64_t)r * a.nx + ix] = xs[r * LPB + tid];
 }
 
 // ---------------------------------------------------------------------------
@@ -584,7 +728,7 @@ static int precond_impl(fm_ctx* c, const double* x, double* y, T* t) {
       yby += (double)cp.nx * ((double)n * (3.0 * kl + 1.0) * ts + n + 2.0 * n * ts);
     }
     dim3 gz((unsigned)((nxy + 127) / 128), c->nM);
-    const size_t smz = (size_t)cp.nz * cp.nz * sizeof(T);
+    const size_t smz = ((size_t)cp.nz * cp.nz + (size_t)cp.nz * 128) * sizeof(T);
     {
       const int tk_ = prof_begin(c, FM_KERNEL_ZMIX);
       k_zmix<double, T, T><<<gz, 128, smz, c->stream>>>(Wzb, x, t, cp.nz, nxy, cp.off);
@@ -593,22 +737,58 @@ static int precond_impl(fm_ctx* c, const double* x, double* y, T* t) {
     dim3 gx((cp.ny + 63) / 64, (cp.nx + 63) / 64, c->nM * cp.nz);
     {
       const int tk_ = prof_begin(c, FM_KERNEL_XMIX);
-      k_xmix<T><<<gx, 256, 0, c->stream>>>(Wxb, t, u, cp.nx, cp.ny, cp.nz, cp.off, c->M0);
+      k_mix<T, false, true, false><<<gx, 256, 0, c->stream>>>(Wxb, t, u, cp.nx, cp.ny, cp.nz, cp.off, c->M0, nullptr, nullptr);
       prof_end(c, tk_, 2.0 * cp.nx * ncomp, 2.0 * ncomp * ts);
     }
+    const bool is32 = std::is_same<T, float>::value;
+    const bool ymda = cp.ydiag_ok && (c->opts.y_solver == 2 || (c->opts.y_solver == 0 && is32));
+    if (ymda) {
+      // n_M = 1: per-l diagonalisation of (A_l, S_y): W_y (Lambda_y + lambda_x)^{-1} W-bar_y on transposed slabs
+      const T* Wyb = is32 ? (const T*)cp.Wyb32 : (const T*)cp.Wyb64;
+      const T* Wy = is32 ? (const T*)cp.Wy32 : (const T*)cp.Wy64;
+      const T* dLy = is32 ? (const T*)cp.dLy32 : (const T*)cp.dLy64;
+      const T* dLx = is32 ? (const T*)cp.dLx32 : (const T*)cp.dLx64;
+      dim3 gyy((cp.nx + 63) / 64, (cp.ny + 63) / 64, c->nM * cp.nz);
+      {
+        const int tk_ = prof_begin(c, FM_KERNEL_YSOLVE);
+        k_mix<T, false, false, true><<<gyy, 256, 0, c->stream>>>(Wyb, u, t, cp.ny, cp.nx, cp.nz, cp.off, c->M0, dLy, dLx);
+        prof_end(c, tk_, 2.0 * cp.ny * ncomp, 2.0 * ncomp * ts);
+      }
+      {
+        const int tk_ = prof_begin(c, FM_KERNEL_YSOLVE);
+        k_mix<T, false, false, false><<<gyy, 256, 0, c->stream>>>(Wy, t, u, cp.ny, cp.nx, cp.nz, cp.off, c->M0, nullptr, nullptr);
+        prof_end(c, tk_, 2.0 * cp.ny * ncomp, 2.0 * ncomp * ts);
+      }
+    } else {
     YArgs ya;
     ya.nx = cp.nx; ya.ny = cp.ny; ya.nz = cp.nz; ya.M0 = c->M0; ya.nl = cp.nl; ya.comp_off = cp.off;
     ya.chain_lo = (const int*)cp.d_chain_lo; ya.chain_n = (const int*)cp.d_chain_n;
     ya.band_off = cp.d_band_off; ya.lmul_off = cp.d_lmul_off; ya.piv_off = cp.d_piv_off;
-    dim3 gy((cp.nx + 127) / 128, cp.nl);
+    int maxnc = 1;
+    for (int v : cp.chain_n) maxnc = std::max(maxnc, v);
+    const size_t line_bytes = (size_t)maxnc * cp.ny * sizeof(T);
     {
       const int tk_ = prof_begin(c, FM_KERNEL_YSOLVE);
-      k_ysolve<T><<<gy, 128, 0, c->stream>>>(ya, U, L, cp.yP, u);
+      if (maxnc == 1 && line_bytes * 32 <= 200 * 1024) {
+        dim3 gy((cp.nx + 31) / 32, cp.nl);
+        k_ysolve1<T, 32><<<gy, 32, line_bytes * 32, c->stream>>>(ya, U, L, cp.yP, u);
+      } else if (line_bytes * 64 <= 200 * 1024) {
+        dim3 gy((cp.nx + 63) / 64, cp.nl);
+        k_ysolve<T, 64><<<gy, 64, line_bytes * 64, c->stream>>>(ya, U, L, cp.yP, u);
+      } else if (line_bytes * 32 <= 200 * 1024) {
+        dim3 gy((cp.nx + 31) / 32, cp.nl);
+        k_ysolve<T, 32><<<gy, 32, line_bytes * 32, c->stream>>>(ya, U, L, cp.yP, u);
+      } else {
+        if (line_bytes * 8 > 200 * 1024) return FM_ERR_ARG;  // M' chains too long for one line in shared memory
+        dim3 gy((cp.nx + 7) / 8, cp.nl);
+        k_ysolve<T, 8><<<gy, 8, line_bytes * 8, c->stream>>>(ya, U, L, cp.yP, u);
+      }
       prof_end(c, tk_, yfl, yby);
+    }
     }
     {
       const int tk_ = prof_begin(c, FM_KERNEL_XMIX);
-      k_xmix<T><<<gx, 256, 0, c->stream>>>(Wx, u, t, cp.nx, cp.ny, cp.nz, cp.off, c->M0);
+      k_mix<T, true, false, false><<<gx, 256, 0, c->stream>>>(Wx, u, t, cp.nx, cp.ny, cp.nz, cp.off, c->M0, nullptr, nullptr);
       prof_end(c, tk_, 2.0 * cp.nx * ncomp, 2.0 * ncomp * ts);
     }
     {
@@ -772,6 +952,14 @@ int kernels_init(fm_ctx* c) {
   FM_CUDA(cudaFuncSetAttribute(k_zmix<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<double, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<float, double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_ysolve1<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_ysolve1<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_ysolve<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_ysolve<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_ysolve<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_ysolve<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_ysolve<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_ysolve<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   return FM_OK;
 }
 

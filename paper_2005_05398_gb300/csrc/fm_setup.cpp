@@ -533,6 +533,18 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
     if ((rc = dev_alloc(c, (void**)&cp.yP, po))) return rc;
     if ((rc = dev_alloc(c, (void**)&cp.yU32, bo * 4))) return rc;
     if ((rc = dev_alloc(c, (void**)&cp.yL32, lo * 4))) return rc;
+    if (nM == 1) {
+      const int ny = cp.ny;
+      if ((rc = dev_alloc(c, (void**)&cp.Wy32, (size_t)nl * ny * ny * 4))) return rc;
+      if ((rc = dev_alloc(c, (void**)&cp.Wyb32, (size_t)nl * ny * ny * 4))) return rc;
+      if ((rc = dev_alloc(c, (void**)&cp.dLy32, (size_t)nl * ny * 4))) return rc;
+      std::vector<float> lx32(cp.Lx.begin(), cp.Lx.end());
+      if ((rc = upload(c, (void**)&cp.dLx32, lx32.data(), lx32.size() * 4))) return rc;
+      if ((rc = dev_alloc(c, (void**)&cp.Wy64, (size_t)nl * ny * ny * 8))) return rc;
+      if ((rc = dev_alloc(c, (void**)&cp.Wyb64, (size_t)nl * ny * ny * 8))) return rc;
+      if ((rc = dev_alloc(c, (void**)&cp.dLy64, (size_t)nl * ny * 8))) return rc;
+      if ((rc = upload(c, (void**)&cp.dLx64, cp.Lx.data(), cp.Lx.size() * 8))) return rc;
+    }
   }
   return FM_OK;
 }
@@ -604,6 +616,41 @@ int setup_shift(fm_ctx* c, double Estar) {
     FM_CUDA(cudaMemcpyAsync(cp.yU32, U32.data(), U32.size() * 4, cudaMemcpyHostToDevice, c->stream));
     FM_CUDA(cudaMemcpyAsync(cp.yL32, L32.data(), L32.size() * 4, cudaMemcpyHostToDevice, c->stream));
     FM_CUDA(cudaStreamSynchronize(c->stream));
+    cp.ydiag_ok = false;
+    if (c->nM == 1 && cp.Wy32) {
+      // (W-bar_y^l, W_y^l, Lambda_y^l) = D(A_l, S_y) with A_l = -D_y + (c_l / y^2 + V^ - E*) S_y; the n_M = 1
+      // block of l is I (x) A_l + Lambda_x^l (x) S_y, inverted line by line as W_y (Lambda_y + lambda_x)^{-1} W-bar_y
+      const std::vector<double> Syd = dense_of(cp.ay, cp.ay.S), D2yd = dense_of(cp.ay, cp.ay.D2);
+      std::vector<double> Wy((size_t)cp.nl * ny * ny), Wyb((size_t)cp.nl * ny * ny), Ly((size_t)cp.nl * ny);
+      std::vector<int> err(cp.nl, 0);
+      const int Mp = c->Mps[0];
+      parallel_for(cp.nl, [&](int il) {
+        const int l = c->M0 + il;
+        const double ll1 = (c->opts.z_eigs == 1) ? -cpp->Lz[il] : (double)l * (l + 1);
+        const double cl = J * (J + 1.0) - 2.0 * Mp * Mp + ll1;
+        std::vector<double> A((size_t)ny * ny);
+        for (int q = 0; q < ny; ++q) {
+          const double y = cpp->ay.pts[q];
+          const double f = cl / (y * y) + vh[q] - Estar;
+          for (int j = 0; j < ny; ++j) A[(size_t)q * ny + j] = -D2yd[(size_t)q * ny + j] + f * Syd[(size_t)q * ny + j];
+        }
+        err[il] = fmh::decompose(ny, A.data(), Syd.data(), false, &Wyb[(size_t)il * ny * ny], &Wy[(size_t)il * ny * ny],
+                                 &Ly[(size_t)il * ny]);
+      });
+      bool ok = true;
+      for (int e : err) ok = ok && (e == 0);
+      if (ok) {
+        std::vector<float> a32(Wy.begin(), Wy.end()), b32(Wyb.begin(), Wyb.end()), l32(Ly.begin(), Ly.end());
+        FM_CUDA(cudaMemcpyAsync(cp.Wy32, a32.data(), a32.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        FM_CUDA(cudaMemcpyAsync(cp.Wyb32, b32.data(), b32.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        FM_CUDA(cudaMemcpyAsync(cp.dLy32, l32.data(), l32.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        FM_CUDA(cudaMemcpyAsync(cp.Wy64, Wy.data(), Wy.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        FM_CUDA(cudaMemcpyAsync(cp.Wyb64, Wyb.data(), Wyb.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        FM_CUDA(cudaMemcpyAsync(cp.dLy64, Ly.data(), Ly.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        FM_CUDA(cudaStreamSynchronize(c->stream));
+        cp.ydiag_ok = true;
+      }
+    }
   }
   c->Estar = Estar;
   c->have_shift = true;

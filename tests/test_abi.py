@@ -45,7 +45,7 @@ def test_library_loads_without_gpu_and_binds(libpath):
 
 def test_struct_fields_match_header():
     from paper_2005_05398_gb300 import _lib
-    src = open(os.path.join(ROOT, "include", "fm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "fm.h")).read(), flags=re.S)
     for cls, tag in ((_lib.fm_system, "fm_system"), (_lib.fm_grid, "fm_grid"), (_lib.fm_splitting, "fm_splitting"),
                      (_lib.fm_opts, "fm_opts"), (_lib.fm_info, "fm_info")):
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + tag + ";", src).group(1)

