@@ -43,7 +43,8 @@ typedef enum {
   FM_ERR_BREAKDOWN = -5,        /* Krylov breakdown (zero or non-finite norm) */
   FM_ERR_COMPLEX_SPECTRUM = -6, /* a 1D generalized eigenproblem has complex eigenvalues */
   FM_ERR_NO_SHIFT = -7,         /* preconditioner used before fm_set_shift */
-  FM_ERR_NUMERIC = -8           /* singular 1D or banded factor, non-finite setup value */
+  FM_ERR_NUMERIC = -8,          /* singular 1D or banded factor, non-finite setup value */
+  FM_ERR_SCRATCH_LIMIT = -9     /* problem larger than the fixed scratch of fm_apply_noalloc */
 } fm_status;
 
 /* Three particles (Section 2.1).  Masses in electron masses ("infinite" core: 1e15,
@@ -183,6 +184,24 @@ const char* fm_strerror(int status);
 /* Diagnostics: counts of the library's own kernel launches since the context was
  * created (launches) and bytes of device memory the context holds. */
 int fm_stats(const fm_ctx* ctx, int64_t* launches, int64_t* device_bytes);
+
+/* Largest n_unknowns accepted by fm_apply_noalloc. */
+#define FM_NOALLOC_MAX_UNKNOWNS (1 << 20)
+
+/* y = (H - E S) x like fm_apply, for callers that must not allocate device memory during
+ * the call: code whose device memory is owned by another allocator (a framework's caching
+ * allocator or a pool sized at start-up, where a cudaMalloc can fail or fragment the pool)
+ * and code on a time-critical path, where cudaMalloc / cudaFree can synchronise the device.
+ * The paper has no counterpart: it is an interface for such callers.  The context is built
+ * by fm_create beforehand (which does allocate); this call allocates nothing.  Its scratch
+ * (three planes of n_unknowns doubles) is a fixed array inside the library, 24 MiB that every
+ * GPU loading the library holds until the process exits; n_unknowns above
+ * FM_NOALLOC_MAX_UNKNOWNS gives FM_ERR_SCRATCH_LIMIT.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current).  All calls
+ * share the array: two calls whose kernels overlap on the GPU (different streams or
+ * contexts running concurrently) race on it and produce wrong results.  Nothing in the
+ * array needs clearing between calls.  Device buffers x and y must not overlap. */
+int fm_apply_noalloc(fm_ctx* ctx, double E, const double* x, double* y);
 
 /* Host-side diagnostic (no GPU involved): the 1D decomposition D(A1, A2) of
  * Eq. WW-scale exactly as fm_create computes it for the preconditioner: W-bar A1 W =

@@ -45,7 +45,7 @@ class fm_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-FM_OK, FM_ERR_NOT_CONVERGED = 0, -4
+FM_OK, FM_ERR_NOT_CONVERGED, FM_ERR_SCRATCH_LIMIT = 0, -4, -9
 KERNEL_CLASSES = ["apply_xy", "apply_z", "coupling", "zmix", "xmix", "ysolve", "dot", "axpy", "other"]
 
 _LIB = None
@@ -58,6 +58,7 @@ SIGNATURES = {
     "fm_component": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int64)]),
     "fm_apply": (c_int, [c_void_p, c_double, c_void_p, c_void_p]),
     "fm_apply_S": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "fm_apply_noalloc": (c_int, [c_void_p, c_double, c_void_p, c_void_p]),
     "fm_set_shift": (c_int, [c_void_p, c_double]),
     "fm_precond_apply": (c_int, [c_void_p, c_void_p, c_void_p]),
     "fm_solve": (c_int, [c_void_p, c_double, c_void_p, c_void_p, ctypes.POINTER(fm_info)]),
@@ -179,6 +180,10 @@ class Context:
 
     def fm_apply(self, E, x, y):
         _check("fm_apply", lib().fm_apply(self.h, float(E), _ptr(x), _ptr(y)))
+
+    def fm_apply_noalloc(self, E, x, y):
+        """(H - E S) x with the library's fixed scratch: allocates no device memory (see include/fm.h)."""
+        _check("fm_apply_noalloc", lib().fm_apply_noalloc(self.h, float(E), _ptr(x), _ptr(y)))
 
     def fm_apply_S(self, x, y):
         _check("fm_apply_S", lib().fm_apply_S(self.h, _ptr(x), _ptr(y)))

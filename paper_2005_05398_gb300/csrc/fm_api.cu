@@ -236,6 +236,7 @@ const char* fm_strerror(int s) {
     case FM_ERR_COMPLEX_SPECTRUM: return "a 1D generalized eigenproblem has complex eigenvalues";
     case FM_ERR_NO_SHIFT: return "preconditioner used before fm_set_shift";
     case FM_ERR_NUMERIC: return "singular or non-finite set-up quantity";
+    case FM_ERR_SCRATCH_LIMIT: return "problem larger than the fixed scratch of fm_apply_noalloc (FM_NOALLOC_MAX_UNKNOWNS)";
     default: return "unknown status";
   }
 }

@@ -165,6 +165,7 @@ int fill_normal(fm_ctx* c, double* x, uint64_t seed);
 int combine(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* Q_host, int nc, double* out, int64_t ldo);
 int absmax(fm_ctx* c, const double* x, double* val);
 int kernels_init(fm_ctx* c);
+int launch_apply_scratch(fm_ctx* c, double E, const double* x, double* y, double* P, double* Q, double* R);
 // timing helpers: begin() returns a token for end(); no-ops unless profiling
 int prof_begin(fm_ctx* c, int cls);
 void prof_end(fm_ctx* c, int token, double flops, double bytes);

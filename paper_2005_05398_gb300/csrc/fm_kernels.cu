@@ -708,6 +708,53 @@ int launch_apply(fm_ctx* c, double E, const double* x, double* y, bool only_S) {
   return FM_OK;
 }
 
+// The operator apply with caller-chosen scratch planes (used by the entry point that allocates
+// nothing, whose planes live in a fixed device array).  Same kernels and launch shapes as
+// launch_apply; no per-kernel timing.
+int launch_apply_scratch(fm_ctx* c, double E, const double* x, double* y, double* P, double* Q, double* R) {
+  for (auto& cp : c->comps) {
+    const int64_t off = cp.off;
+    constexpr int TX = 8;
+    const size_t smem = (size_t)3 * (TX + 2) * cp.ny * sizeof(double);
+    dim3 g1((cp.nx + TX - 1) / TX, cp.nz * c->nM);
+    k_apply_xy<TX><<<g1, 256, smem, c->stream>>>(x + off, P + off, Q + off, R + off, cp.nx, cp.ny, cp.dx.base, cp.dx.S,
+                                                 cp.dx.D2, cp.dy.base, cp.dy.S, cp.dy.D2, false);
+    ZPassArgs a;
+    a.P = P + off; a.Q = Q + off; a.R = R + off; a.y = y + off; a.W = cp.W;
+    a.bz = cp.dz.base; a.Sz = cp.dz.S; a.D1z = cp.dz.D1; a.D2z = cp.dz.D2;
+    a.zp = cp.dz.pts; a.xp = cp.dx.pts; a.yp = cp.dy.pts;
+    a.nx = cp.nx; a.ny = cp.ny; a.nz = cp.nz; a.nM = c->nM; a.M0 = c->M0; a.J = c->sys.J; a.E = E;
+    for (int i = 0; i < kMaxM; ++i) a.lamp[i] = a.lamm[i] = 0.0;
+    for (int iM = 0; iM < c->nM; ++iM) {
+      const int Mp = c->Mps[iM], J = c->sys.J;
+      const double vp = (double)(J * (J + 1) - Mp * (Mp + 1)), vm = (double)(J * (J + 1) - Mp * (Mp - 1));
+      a.lamp[iM] = (vp > 0 ? sqrt(vp) : 0.0) * sqrt(Mp == 0 ? 2.0 : 1.0);
+      a.lamm[iM] = (vm > 0 ? sqrt(vm) : 0.0) * sqrt(Mp == 1 ? 2.0 : 1.0);
+    }
+    const int64_t tot = cp.npts * c->nM;
+    k_apply_z<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(a, false);
+    c->launches += 2;
+  }
+  for (auto& cp : c->comps) {
+    if (cp.n_act == 0 || cp.sources.empty()) continue;
+    CouplingArgs a{};
+    a.x = x; a.y = y; a.row_off = cp.off; a.npts = cp.npts; a.n_act = cp.n_act; a.act_pt = cp.act_pt;
+    a.ns = (int)cp.sources.size(); a.nM = c->nM;
+    for (int s = 0; s < a.ns; ++s) {
+      const auto& src = c->comps[cp.sources[s].src];
+      a.base[s] = cp.cpl_base + (int64_t)s * 3 * cp.n_act;
+      a.val[s] = cp.cpl_val + (int64_t)s * 12 * cp.n_act;
+      a.w[s] = cp.cpl_w + (int64_t)s * c->nM * c->nM * cp.n_act;
+      a.src_off[s] = src.off; a.src_npts[s] = src.npts;
+      a.snx[s] = src.nx; a.sny[s] = src.ny; a.snz[s] = src.nz;
+    }
+    k_apply_coupling<<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
+    c->launches++;
+  }
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
 template <typename T>
 static int precond_impl(fm_ctx* c, const double* x, double* y, T* t) {
   for (auto& cp : c->comps) {
