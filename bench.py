@@ -286,6 +286,34 @@ def run_ours(args):
     return 0
 
 
+def run_kernel_loop(args):
+    """Repeat one library call on the full-size workload (for profiler captures of single kernels)."""
+    import torch
+    import paper_2005_05398_gb300 as pkg
+    from paper_2005_05398_gb300 import build
+    build.build()
+    wl = workload(args.workload)
+    ctx = pkg.Context(wl, precision=1 if args.precision == "fp32" else 0, restart_m=args.restart, ncv=4)
+    ctx.fm_set_shift(wl["shift"])
+    x = torch.tensor(rand_vec(ctx.n, SEED_BASE), dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    ctx.fm_profile(1)
+    for _ in range(args.loops):
+        if args.kernel_loop == "apply":
+            ctx.fm_apply(wl["shift"], x, y)
+        elif args.kernel_loop == "precond":
+            ctx.fm_precond_apply(x, y)
+        else:
+            x0 = torch.zeros_like(x)
+            ctx.fm_solve(wl["shift"], x, x0, allow_not_converged=True)
+    torch.cuda.synchronize()
+    prof = ctx.fm_profile_read()
+    print(json.dumps({"kernel_loop": args.kernel_loop, "workload": args.workload, "loops": args.loops,
+                      "kernels": {k: v for k, v in prof.items() if v["launches"]}}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,7 +328,12 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel-loop", choices=["apply", "precond", "solve"], default=None,
+                    help="repeat one call --loops times on the workload (profiler captures)")
+    ap.add_argument("--loops", type=int, default=5)
     args = ap.parse_args()
+    if args.kernel_loop:
+        return run_kernel_loop(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
