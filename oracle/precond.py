@@ -29,8 +29,9 @@ Readings:
   Lambda_z^{M'+-} of Eq. prop-eq hold for that normalisation.
 * ``z_eigs="computed"`` keeps Lambda~_z (allowed only with n_M = 1); then
   L_alpha = L exactly, the left-hand operator of Eq. FM-fin.
-* A 1D spectrum with max|Im| > 1e-10 max|lambda| is rejected (complex
-  arithmetic is not on this path).
+* A z pencil with complex-conjugate pairs (high modes of M' >= 2-3) is
+  represented by a real basis: see ``decompose_pairs``.  Any other complex 1D
+  spectrum is rejected (complex arithmetic is not on this path).
 """
 from __future__ import annotations
 
@@ -57,6 +58,35 @@ def decompose(A1, A2, order="ascending"):
     scale = np.einsum("ki,kl,li->i", VL, A2, W)  # vl_i^T A2 w_i
     Wbar = (VL / scale[None, :]).T
     return Wbar, W, lam
+
+
+def decompose_pairs(A1, A2, top):
+    """D(A1, A2) for a pencil with complex-conjugate pairs, as a real basis (reading).
+
+    Columns in descending order of the real part; a pair contributes the real and imaginary
+    parts of the eigenvector of its member with positive imaginary part, with the phase chosen
+    so that coefficient ``top`` (the value at z = 1) is real and positive.  W-bar = (A2 W)^{-1},
+    so W-bar A2 W = I and W-bar A1 W is block diagonal (2x2 blocks for the pairs).
+    Returns (W-bar, W, real parts, kinds) with kind 0 = real, 1 / 2 = real / imaginary part.
+    """
+    lam, VR = sla.eig(A1, A2)
+    cx = np.abs(lam.imag) > 1e-10 * np.max(np.abs(lam))
+    idx = [i for i in range(len(lam)) if (not cx[i]) or lam[i].imag > 0]
+    idx.sort(key=lambda i: -lam[i].real)
+    cols, lr, kinds = [], [], []
+    for i in idx:
+        if not cx[i]:
+            cols.append(VR[:, i].real)
+            lr.append(lam[i].real)
+            kinds.append(0)
+        else:
+            w = VR[:, i]
+            w = w * np.conj(w[top]) / abs(w[top])
+            cols += [w.real, w.imag]
+            lr += [lam[i].real, lam[i].real]
+            kinds += [1, 2]
+    W = np.stack(cols, axis=1)
+    return np.linalg.inv(A2 @ W), W, np.array(lr), kinds
 
 
 def g_at_one(l, Mp):
@@ -86,11 +116,20 @@ class Preconditioner:
         C = {"Wz": [], "Wzb": [], "Lz": [], "Wx": {}, "Wxb": {}, "Lx": {}, "Wy": {}, "Wyb": {}, "Ly": {}}
         # z decompositions per M' (Eq. z-dec), normalised to g_l^{M'}(1)
         onez = g.az.basis.matrix(np.array([1.0]), 0)[0]
+        top = 2 * g.az.basis.N  # value function of the node z = 1
         for Mp in s.Mps:
             Dz = (1 - z * z)[:, None] * D2z - (2 * (Mp + 1) * z)[:, None] * D1z - Mp * (Mp + 1) * Sz
-            Wb, W, lz = decompose(Dz, Sz, order="descending")
-            target = np.array([g_at_one(Mp + l, Mp) for l in range(g.nz)])
-            sc = target / (onez @ W)
+            try:
+                Wb, W, lz = decompose(Dz, Sz, order="descending")
+                kinds = [0] * g.nz
+            except ComplexSpectrum:
+                if self.z_eigs == "computed":
+                    raise
+                Wb, W, lz, kinds = decompose_pairs(Dz, Sz, top)
+            f1 = onez @ W
+            sc = np.empty(g.nz)
+            for l in range(g.nz):  # the imaginary-part column of a pair takes its partner's scale
+                sc[l] = sc[l - 1] if kinds[l] == 2 else g_at_one(Mp + l, Mp) / f1[l]
             C["Wz"].append(W * sc[None, :])
             C["Wzb"].append(Wb / sc[:, None])
             C["Lz"].append(lz)

@@ -48,15 +48,25 @@ static int nrm2(fm_ctx* c, const double* v, double* out) {
   return rc;
 }
 
-// classical Gram-Schmidt with one re-orthogonalisation against V[0..nv): h += V^T w, w -= V h
-static int cgs2(fm_ctx* c, const double* V, int nv, double* w, double* h) {
-  std::vector<double> h1(nv), h2(nv);
+// Classical Gram-Schmidt of w against the orthonormal V[0..nv) with the DGKS test: a second pass
+// runs only when the first removed more than 1 - 1/sqrt(2) of the norm (w lay close to span V).
+// h receives the coefficients, *nrm the norm of the orthogonalised w.
+static int orthogonalize(fm_ctx* c, const double* V, int nv, double* w, double* h, double* nrm) {
+  std::vector<double> h1(nv + 1), h2(nv + 1);
   int rc;
-  if ((rc = dot_many(c, V, c->N, nv, w, h1.data()))) return rc;
-  if ((rc = axpy_many(c, V, c->N, nv, h1.data(), w, -1.0))) return rc;
-  if ((rc = dot_many(c, V, c->N, nv, w, h2.data()))) return rc;
-  if ((rc = axpy_many(c, V, c->N, nv, h2.data(), w, -1.0))) return rc;
-  for (int i = 0; i < nv; ++i) h[i] = h1[i] + h2[i];
+  if ((rc = dot_many_x(c, V, c->N, nv, w, w, h1.data()))) return rc;  // V^T w and w.w
+  const double before = std::sqrt(std::max(h1[nv], 0.0));
+  double n2;
+  if ((rc = axpy_many_norm(c, V, c->N, nv, h1.data(), w, &n2))) return rc;
+  for (int i = 0; i < nv; ++i) h[i] = h1[i];
+  double after = std::sqrt(std::max(n2, 0.0));
+  if (after < 0.7071067811865476 * before) {
+    if ((rc = dot_many(c, V, c->N, nv, w, h2.data()))) return rc;
+    if ((rc = axpy_many_norm(c, V, c->N, nv, h2.data(), w, &n2))) return rc;
+    for (int i = 0; i < nv; ++i) h[i] += h2[i];
+    after = std::sqrt(std::max(n2, 0.0));
+  }
+  *nrm = after;
   return FM_OK;
 }
 
@@ -140,9 +150,8 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
       if ((rc = launch_precond(c, Vj, Zj))) return rc;
       if ((rc = apply_tuning(c, Zj))) return rc;
       if ((rc = launch_apply(c, E, Zj, c->w, false))) return rc;
-      if ((rc = cgs2(c, c->V, j + 1, c->w, h.data()))) return rc;
       double hn;
-      if ((rc = nrm2(c, c->w, &hn))) return rc;
+      if ((rc = orthogonalize(c, c->V, j + 1, c->w, h.data(), &hn))) return rc;
       if (!std::isfinite(hn)) return FM_ERR_BREAKDOWN;
       for (int i = 0; i < j; ++i) {  // previous Givens rotations
         const double t = cs[i] * h[i] + sn[i] * h[i + 1];
@@ -494,9 +503,8 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
       ++ops;
       if (rc != FM_OK && rc != FM_ERR_NOT_CONVERGED) return rc;
       std::vector<double> h(j + 1);
-      if ((rc = cgs2(c, V, j + 1, w, h.data()))) return rc;
       double hn;
-      if ((rc = nrm2(c, w, &hn))) return rc;
+      if ((rc = orthogonalize(c, V, j + 1, w, h.data(), &hn))) return rc;
       if (!std::isfinite(hn)) return FM_ERR_BREAKDOWN;
       for (int i = 0; i <= j; ++i) G[(size_t)i * m + j] = h[i];
       G[(size_t)(j + 1) * m + j] = hn;

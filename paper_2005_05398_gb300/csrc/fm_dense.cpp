@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <numeric>
 
@@ -297,10 +298,39 @@ static void hess_shifted_solve(int n, const double* H, double mu, double tiny, d
   }
 }
 
-// All eigenvalues (re, im) of A; eigenvectors (unit 2-norm) for the real ones, zero
-// columns for complex ones.  Returns -1 on no convergence, 1 if a complex eigenvalue
-// occurred, 0 otherwise.
-int eig_general(int n, const double* Ain, double* re, double* im, double* V) {
+using cplx = std::complex<double>;
+
+// Solve (H - mu I) y = b for upper-Hessenberg H and complex mu (adjacent-row pivoting).
+static void hess_shifted_solve_c(int n, const double* H, cplx mu, double tiny, cplx* b, cplx* M) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      M[(size_t)i * n + j] = (j >= i - 1) ? cplx(H[(size_t)i * n + j]) - (i == j ? mu : cplx(0.0)) : cplx(0.0);
+  for (int k = 0; k + 1 < n; ++k) {
+    cplx* rk = M + (size_t)k * n;
+    cplx* r1 = M + (size_t)(k + 1) * n;
+    if (std::abs(r1[k]) > std::abs(rk[k])) {
+      for (int j = k; j < n; ++j) std::swap(rk[j], r1[j]);
+      std::swap(b[k], b[k + 1]);
+    }
+    if (rk[k] == cplx(0.0)) rk[k] = tiny;
+    const cplx l = r1[k] / rk[k];
+    if (l != cplx(0.0)) {
+      for (int j = k; j < n; ++j) r1[j] -= l * rk[j];
+      b[k + 1] -= l * b[k];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    cplx* ri = M + (size_t)i * n;
+    if (ri[i] == cplx(0.0)) ri[i] = tiny;
+    cplx sacc = b[i];
+    for (int j = i + 1; j < n; ++j) sacc -= ri[j] * b[j];
+    b[i] = sacc / ri[i];
+  }
+}
+
+// All eigenvalues (re, im) of A and unit eigenvectors (real part Vr, imaginary part Vi; Vi = 0 for
+// real eigenvalues).  Returns -1 on no convergence, 1 if a complex eigenvalue occurred, 0 otherwise.
+int eig_general2(int n, const double* Ain, double* re, double* im, double* Vr, double* Vi) {
   std::vector<double> A(Ain, Ain + (size_t)n * n), D(n), Q((size_t)n * n);
   balance(n, A.data(), D.data());
   hessenberg(n, A.data(), Q.data());
@@ -309,35 +339,72 @@ int eig_general(int n, const double* Ain, double* re, double* im, double* V) {
   for (int i = 0; i < n; ++i) maxabs = std::max(maxabs, std::hypot(re[i], im[i]));
   for (size_t i = 0; i < A.size(); ++i) hn = std::max(hn, std::fabs(A[i]));
   int status = 0;
-  std::vector<double> work((size_t)n * n), y(n), z(n);
+  std::vector<double> work((size_t)n * n), y(n);
+  std::vector<cplx> cwork((size_t)n * n), cy(n);
   const double tiny = 1e-15 * (hn > 0 ? hn : 1.0);
   for (int e = 0; e < n; ++e) {
-    if (std::fabs(im[e]) > 1e-10 * maxabs) {
-      status = 1;
-      for (int i = 0; i < n; ++i) V[(size_t)i * n + e] = 0.0;
+    const bool cx = std::fabs(im[e]) > 1e-10 * maxabs;
+    if (!cx) {
+      im[e] = 0.0;
+      for (int i = 0; i < n; ++i) y[i] = 1.0 + 0.1 * std::sin(1.0 + 3.7 * i + 0.3 * e);
+      for (int it = 0; it < 3; ++it) {
+        hess_shifted_solve(n, A.data(), re[e], tiny, y.data(), work.data());
+        double nr = 0.0;
+        for (int i = 0; i < n; ++i) nr += y[i] * y[i];
+        nr = std::sqrt(nr);
+        if (!(nr > 0.0) || !std::isfinite(nr)) return -1;
+        for (int i = 0; i < n; ++i) y[i] /= nr;
+      }
+      double nr = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double sacc = 0.0;
+        for (int j = 0; j < n; ++j) sacc += Q[(size_t)i * n + j] * y[j];
+        Vr[(size_t)i * n + e] = D[i] * sacc;
+        nr += Vr[(size_t)i * n + e] * Vr[(size_t)i * n + e];
+      }
+      nr = std::sqrt(nr);
+      for (int i = 0; i < n; ++i) {
+        Vr[(size_t)i * n + e] /= nr;
+        Vi[(size_t)i * n + e] = 0.0;
+      }
       continue;
     }
-    im[e] = 0.0;
-    for (int i = 0; i < n; ++i) y[i] = 1.0 + 0.1 * std::sin(1.0 + 3.7 * i + 0.3 * e);
+    status = 1;
+    const cplx mu(re[e], im[e]);
+    for (int i = 0; i < n; ++i) cy[i] = cplx(1.0 + 0.1 * std::sin(1.0 + 3.7 * i + 0.3 * e), 0.05 * std::cos(0.7 * i));
     for (int it = 0; it < 3; ++it) {
-      hess_shifted_solve(n, A.data(), re[e], tiny, y.data(), work.data());
+      hess_shifted_solve_c(n, A.data(), mu, tiny, cy.data(), cwork.data());
       double nr = 0.0;
-      for (int i = 0; i < n; ++i) nr += y[i] * y[i];
+      for (int i = 0; i < n; ++i) nr += std::norm(cy[i]);
       nr = std::sqrt(nr);
       if (!(nr > 0.0) || !std::isfinite(nr)) return -1;
-      for (int i = 0; i < n; ++i) y[i] /= nr;
+      for (int i = 0; i < n; ++i) cy[i] /= nr;
     }
     double nr = 0.0;
+    std::vector<cplx> v(n);
     for (int i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (int j = 0; j < n; ++j) s += Q[(size_t)i * n + j] * y[j];
-      z[i] = D[i] * s;
-      nr += z[i] * z[i];
+      cplx sacc = 0.0;
+      for (int j = 0; j < n; ++j) sacc += Q[(size_t)i * n + j] * cy[j];
+      v[i] = D[i] * sacc;
+      nr += std::norm(v[i]);
     }
     nr = std::sqrt(nr);
-    for (int i = 0; i < n; ++i) V[(size_t)i * n + e] = z[i] / nr;
+    for (int i = 0; i < n; ++i) {
+      Vr[(size_t)i * n + e] = v[i].real() / nr;
+      Vi[(size_t)i * n + e] = v[i].imag() / nr;
+    }
   }
   return status;
+}
+
+int eig_general(int n, const double* Ain, double* re, double* im, double* V) {
+  std::vector<double> Vi((size_t)n * n);
+  const int st = eig_general2(n, Ain, re, im, V, Vi.data());
+  if (st < 0) return st;
+  for (int e = 0; e < n; ++e)
+    if (im[e] != 0.0)
+      for (int i = 0; i < n; ++i) V[(size_t)i * n + e] = 0.0;
+  return st;
 }
 
 int eig_real(int n, const double* Ain, double* lam, double* V) {
@@ -367,6 +434,59 @@ int decompose(int n, const double* A1, const double* A2, bool descending, double
     for (int i = 0; i < n; ++i) W[(size_t)i * n + e] = V[(size_t)i * n + order[e]];
   }
   // W-bar = (A2 W)^{-1}
+  std::vector<double> A2W((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      const double a = A2[(size_t)i * n + k];
+      if (a == 0.0) continue;
+      for (int j = 0; j < n; ++j) A2W[(size_t)i * n + j] += a * W[(size_t)k * n + j];
+    }
+  if (!invert(n, A2W.data(), Wbar)) return -2;
+  return 0;
+}
+
+int decompose_pairs(int n, const double* A1, const double* A2, int top, double* Wbar, double* W, double* lam,
+                    int* kind) {
+  std::vector<double> LU(A2, A2 + (size_t)n * n), C((size_t)n * n);
+  std::vector<int> piv(n);
+  if (!lu_factor(n, LU.data(), piv.data())) return -2;
+  std::vector<double> col(n);
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < n; ++i) col[i] = A1[(size_t)i * n + j];
+    lu_solve(n, LU.data(), piv.data(), col.data());
+    for (int i = 0; i < n; ++i) C[(size_t)i * n + j] = col[i];
+  }
+  std::vector<double> re(n), im(n), Vr((size_t)n * n), Vi((size_t)n * n);
+  if (eig_general2(n, C.data(), re.data(), im.data(), Vr.data(), Vi.data()) < 0) return -1;
+  std::vector<int> order;
+  for (int e = 0; e < n; ++e)
+    if (im[e] >= 0.0) order.push_back(e);  // one member of every conjugate pair
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return re[a] > re[b] || (re[a] == re[b] && a < b); });
+  int c = 0;
+  for (int e : order) {
+    if (im[e] == 0.0) {
+      for (int i = 0; i < n; ++i) W[(size_t)i * n + c] = Vr[(size_t)i * n + e];
+      lam[c] = re[e];
+      kind[c] = 0;
+      ++c;
+    } else {
+      if (c + 1 >= n) return -1;
+      // phase so that the value at z = 1 (coefficient 'top') is real and positive
+      const cplx f(Vr[(size_t)top * n + e], Vi[(size_t)top * n + e]);
+      if (std::abs(f) == 0.0) return -1;
+      const cplx ph = std::conj(f) / std::abs(f);
+      for (int i = 0; i < n; ++i) {
+        const cplx w = cplx(Vr[(size_t)i * n + e], Vi[(size_t)i * n + e]) * ph;
+        W[(size_t)i * n + c] = w.real();
+        W[(size_t)i * n + c + 1] = w.imag();
+      }
+      lam[c] = lam[c + 1] = re[e];
+      kind[c] = 1;
+      kind[c + 1] = 2;
+      c += 2;
+    }
+  }
+  if (c != n) return -1;
   std::vector<double> A2W((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) {

@@ -35,6 +35,17 @@ int hess_eigvals(int n, const double* H, double* re, double* im);
 int decompose(int n, const double* A1, const double* A2, bool descending,
               double* Wbar, double* W, double* lam);
 
+// Like decompose(), descending, for pencils that may have complex-conjugate eigenvalue pairs:
+// a pair contributes two real columns, the real and imaginary parts of the eigenvector of the
+// member with positive imaginary part, phased so that its coefficient 'top' is real positive
+// (kind = 1 and 2; real eigenvalues kind = 0; lam = real parts).  W-bar = (A2 W)^{-1}, so
+// W-bar A2 W = I and W-bar A1 W is block diagonal with 2x2 blocks for the pairs.
+int decompose_pairs(int n, const double* A1, const double* A2, int top, double* Wbar, double* W, double* lam,
+                    int* kind);
+
+// All eigenvalues and unit eigenvectors (real and imaginary parts) of a general real matrix.
+int eig_general2(int n, const double* A, double* re, double* im, double* Vr, double* Vi);
+
 // Banded LU with partial pivoting (the row-swap form of LAPACK's gbtrf).  The matrix is
 // given as a row-major band: row i holds columns i-kl .. i+ku+kl in B[i*(2kl+ku+1) + (j-i+kl)]
 // (the last kl columns receive fill-in).  On return U(i, i+d) = B[i*w + kl + d] (d = 0..kl+ku),

@@ -158,6 +158,8 @@ int setup_shift(fm_ctx* c, double Estar);                            // banded y
 int launch_apply(fm_ctx* c, double E, const double* x, double* y, bool only_S);
 int launch_precond(fm_ctx* c, const double* x, double* y);
 int dot_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, double* h_host);
+int dot_many_x(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_host);
+int axpy_many_norm(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double* nrm2_out);
 int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double sign);
 int scale_copy(fm_ctx* c, const double* x, double a, double* y);   // y = a x
 int axpby(fm_ctx* c, double a, const double* x, double b, double* y);  // y = a x + b y

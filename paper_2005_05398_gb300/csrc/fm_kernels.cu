@@ -533,16 +533,18 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// partial[j][block] = sum over this block's slice of V[j] . w
+// partial[j][block] = sum over this block's slice of V[j] . w  (j < nv), and for j = nv, when
+// 'extra' is given, extra . w
 __global__ void __launch_bounds__(kRedThreads) k_dot_many(const double* __restrict__ V, int64_t ldv, int nv,
                                                          const double* __restrict__ w, int64_t n,
-                                                         double* __restrict__ partial) {
+                                                         double* __restrict__ partial, const double* __restrict__ extra) {
   __shared__ double sh[32];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * chunk;
   const int64_t hi = min(n, lo + chunk);
-  for (int j = 0; j < nv; ++j) {
-    const double* v = V + (int64_t)j * ldv;
+  const int nt = nv + (extra ? 1 : 0);
+  for (int j = 0; j < nt; ++j) {
+    const double* v = (j < nv) ? V + (int64_t)j * ldv : extra;
     double s = 0.0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s = fma(v[i], w[i], s);
     s = block_sum(s, sh);
@@ -556,6 +558,27 @@ __global__ void k_dot_finish(const double* __restrict__ partial, int nb, int nv,
   double s = 0.0;
   for (int b = 0; b < nb; ++b) s += partial[(int64_t)j * nb + b];
   h[j] = s;
+}
+
+// w += sign * sum_j h[j] V[j], and partial[block] = sum over the block's slice of the new w^2
+__global__ void __launch_bounds__(kRedThreads) k_axpy_many_norm(const double* __restrict__ V, int64_t ldv, int nv,
+                                                               const double* __restrict__ h, double sign,
+                                                               double* __restrict__ w, int64_t n,
+                                                               double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  double acc = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < nv; ++j) s = fma(h[j], V[(int64_t)j * ldv + i], s);
+    const double v = fma(sign, s, w[i]);
+    w[i] = v;
+    acc = fma(v, v, acc);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
 // w += sign * sum_j h[j] V[j]
@@ -855,19 +878,24 @@ int launch_precond(fm_ctx* c, const double* x, double* y) {
 }
 
 int dot_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, double* h_host) {
+  return dot_many_x(c, V, ldv, nv, w, nullptr, h_host);
+}
+
+int dot_many_x(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_host) {
   const int nb = c->red_blocks;
+  const int nt = nv + (extra ? 1 : 0);
   {
     const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_many<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red);
-    prof_end(c, tk_, 2.0 * nv * (double)c->N, (nv + 1.0) * 8.0 * (double)c->N);
+    k_dot_many<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra);
+    prof_end(c, tk_, 2.0 * nt * (double)c->N, (nt + 1.0) * 8.0 * (double)c->N);
   }
   {
     const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_finish<<<(nv + 63) / 64, 64, 0, c->stream>>>(c->red, nb, nv, c->red + (int64_t)nb * 256);
+    k_dot_finish<<<(nt + 63) / 64, 64, 0, c->stream>>>(c->red, nb, nt, c->red + (int64_t)nb * 256);
     prof_end(c, tk_, 0.0, 0.0);
   }
   c->launches += 2;
-  FM_CUDA(cudaMemcpyAsync(h_host, c->red + (int64_t)nb * 256, nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaMemcpyAsync(h_host, c->red + (int64_t)nb * 256, nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   FM_CUDA(cudaStreamSynchronize(c->stream));
   return prof_harvest(c);
 }
@@ -883,6 +911,28 @@ int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_h
   c->launches++;
   FM_CUDA(cudaGetLastError());
   return FM_OK;
+}
+
+// w -= V h (h on the host), returns ||w||^2 after the update
+int axpy_many_norm(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double* nrm2_out) {
+  double* hd = c->red + (int64_t)c->red_blocks * 256 + 512;
+  FM_CUDA(cudaMemcpyAsync(hd, h_host, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  const int nb = c->red_blocks;
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+    k_axpy_many_norm<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, hd, -1.0, w, c->N, c->red);
+    prof_end(c, tk_, (2.0 * nv + 2.0) * (double)c->N, (nv + 2.0) * 8.0 * (double)c->N);
+  }
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+    k_dot_finish<<<1, 64, 0, c->stream>>>(c->red, nb, 1, c->red + (int64_t)nb * 256);
+    prof_end(c, tk_, 0.0, 0.0);
+  }
+  c->launches += 2;
+  FM_CUDA(cudaGetLastError());
+  FM_CUDA(cudaMemcpyAsync(nrm2_out, c->red + (int64_t)nb * 256, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  return prof_harvest(c);
 }
 
 int scale_copy(fm_ctx* c, const double* x, double a, double* y) {

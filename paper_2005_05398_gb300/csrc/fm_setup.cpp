@@ -443,14 +443,23 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       }
       double* Wb = &Wzb[(size_t)iM * nz * nz];
       double* Wr = &Wz[(size_t)iM * nz * nz];
-      const int e = fmh::decompose(nz, A1.data(), Szd.data(), true, Wb, Wr, &cp.Lz[(size_t)iM * nz]);
+      const int top = 2 * cp.az.nint;  // value function of the node z = 1
+      std::vector<int> kind(nz, 0);
+      const int e = fmh::decompose_pairs(nz, A1.data(), Szd.data(), top, Wb, Wr, &cp.Lz[(size_t)iM * nz], kind.data());
       if (e == -1) return FM_ERR_COMPLEX_SPECTRUM;
       if (e != 0) return FM_ERR_NUMERIC;
-      const int top = 2 * cp.az.nint;  // value function of the node z = 1
+      bool has_pairs = false;
+      for (int kd : kind) has_pairs = has_pairs || kd != 0;
+      if (has_pairs && c->opts.z_eigs == 1) return FM_ERR_COMPLEX_SPECTRUM;
+      // columns scaled so their spline equals g_l^{M'}(1); the imaginary-part column of a
+      // complex pair takes the scale of its real-part column
+      double sc = 1.0;
       for (int l = 0; l < nz; ++l) {
-        const double f1 = Wr[(size_t)top * nz + l];
-        if (f1 == 0.0) return FM_ERR_NUMERIC;
-        const double sc = g_at_one(Mp + l, Mp) / f1;
+        if (kind[l] != 2) {
+          const double f1 = Wr[(size_t)top * nz + l];
+          if (f1 == 0.0) return FM_ERR_NUMERIC;
+          sc = g_at_one(Mp + l, Mp) / f1;
+        }
         for (int q = 0; q < nz; ++q) Wr[(size_t)q * nz + l] *= sc;
         for (int q = 0; q < nz; ++q) Wb[(size_t)l * nz + q] /= sc;
       }

@@ -38,6 +38,8 @@ CASES = {
     "he_l2_odd": dict(J=2, tau=-1, nint=(5, 6, 4), R=(15.0, 17.0)),
     "psm_l2": dict(J=2, nint=(6, 5, 4), R=(30.0, 27.0), mass=(1.0, 1.0, 1.0), charge=(-1.0, -1.0, 1.0), shift=-0.27),
     "he_l1_percomp": dict(J=1, nint=(6, 6, 4), R=(20.0, 20.0), grids={3: {"nint": (4, 3, 3), "R": (9.0, 6.0)}}),
+    "psm_l3_pairs": dict(J=3, nint=(4, 4, 8), R=(20.0, 18.0), mass=(1.0, 1.0, 1.0), charge=(-1.0, -1.0, 1.0),
+                         shift=-0.27),
     "distinct_l1": dict(J=1, nint=(5, 5, 3), R=(12.0, 11.0), identical_pair=0, mass=(1.0, 3.0, 7.0),
                         charge=(-1.0, 2.0, -1.0)),
 }
@@ -70,7 +72,7 @@ def test_apply_matches_oracle(pkg, name):
     ctx.close()
 
 
-@pytest.mark.parametrize("name", ["he_l0_merkuriev", "he_l1", "he_l2_odd", "psm_l2", "he_l1_percomp"])
+@pytest.mark.parametrize("name", ["he_l0_merkuriev", "he_l1", "he_l2_odd", "psm_l2", "he_l1_percomp", "psm_l3_pairs"])
 def test_precond_fp64_matches_paper_form(pkg, name):
     """The GPU preconditioner (z/x mode products + banded y solves) equals the
     paper's Eq. prec-2 with y eigen-transforms and tridiagonal M' chains."""
@@ -167,7 +169,8 @@ def test_solve_matches_sparse_lu(pkg, precision):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8
 
 
-@pytest.mark.parametrize("name,k", [("he_l0_merkuriev", 1), ("he_l0_merkuriev", 3), ("he_l1", 2), ("psm_l2", 2)])
+@pytest.mark.parametrize("name,k", [("he_l0_merkuriev", 1), ("he_l0_merkuriev", 3), ("he_l1", 2), ("psm_l2", 2),
+                                    ("psm_l3_pairs", 2)])
 def test_eigs_match_oracle(pkg, name, k):
     from oracle.system import FMSystem
     from oracle import solvers

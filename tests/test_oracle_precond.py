@@ -113,3 +113,39 @@ def test_oracle_fgmres_matches_sparse_lu():
     assert info["resid"] < 1e-12
     assert np.linalg.norm(x - ref) < 1e-9 * np.linalg.norm(ref)
     assert info["iters"] < 100  # the preconditioner is effective (unpreconditioned GMRES stalls)
+
+
+def test_complex_pairs_real_basis():
+    """M' = 3 z pencil on 8 sin-mapped intervals has complex pairs: the real basis keeps
+    W-bar A2 W = I, W-bar A1 W block diagonal with the pairs' 2x2 rotation-scaling blocks,
+    and the low (cubic-representable) modes exact."""
+    from oracle.precond import decompose_pairs
+    wl = workload("he_l0_24x24x8", J=3, nint=(2, 2, 8), R=(8.0, 8.0))
+    s = FMSystem(wl)
+    g = s.g[1]
+    z = g.az.pts
+    Sz, D1z, D2z = g.az.mat(0), g.az.mat(1), g.az.mat(2)
+    Mp = 3
+    Dz = (1 - z * z)[:, None] * D2z - (2 * (Mp + 1) * z)[:, None] * D1z - Mp * (Mp + 1) * Sz
+    Wb, W, lr, kinds = decompose_pairs(Dz, Sz, 2 * g.az.basis.N)
+    assert kinds.count(1) == kinds.count(2) >= 1
+    assert np.allclose(Wb @ Sz @ W, np.eye(g.nz), atol=1e-10)
+    T = Wb @ Dz @ W
+    for l, kd in enumerate(kinds):
+        if kd == 0:
+            assert abs(T[l, l] - lr[l]) < 1e-8 * abs(lr).max()
+        elif kd == 1:
+            blk = T[l:l + 2, l:l + 2]
+            assert abs(blk[0, 0] - blk[1, 1]) < 1e-8 * abs(lr).max() and abs(blk[0, 1] + blk[1, 0]) < 1e-8 * abs(lr).max()
+    off = T - np.diag(np.diag(T))
+    for l, kd in enumerate(kinds):
+        if kd == 1:
+            off[l, l + 1] = off[l + 1, l] = 0
+    assert np.abs(off).max() < 1e-8 * abs(lr).max()
+    assert np.allclose(lr[:4], [-(Mp + l) * (Mp + l + 1) for l in range(4)], atol=1e-9)
+    P = Preconditioner(s, -0.3)  # builds with the pairs and still inverts its own operator
+    L = P.dense_L(1)
+    v = np.random.default_rng(15).standard_normal(g.csize)
+    full = np.zeros(s.N)
+    full[:g.csize] = L @ v
+    assert np.linalg.norm(P.apply(full)[:g.csize] - v) < 1e-11 * np.linalg.norm(v)
