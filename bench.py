@@ -101,7 +101,7 @@ def dist_env():
     return ws, rank, local
 
 
-def roofline(prof, peaks):
+def roofline(prof, peaks, wname=WORKLOAD):
     """The dominant kernel class (largest device time) against its roofline."""
     bound_of = {"apply_xy": "alu", "apply_z": "alu", "coupling": "alu", "dot": "alu", "axpy": "alu",
                 "zmix": "hbm", "xmix": "hbm", "ysolve": "hbm", "other": "hbm"}
@@ -120,7 +120,7 @@ def roofline(prof, peaks):
     traffic = None
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        traffic = tr.get(WORKLOAD, {}).get(name)
+        traffic = tr.get(wname, {}).get(name)
     except Exception:
         pass
     return {"kernel": name, "bound": bound_of[name], "achieved": achieved, "peak": peak, "unit": unit,
@@ -192,10 +192,12 @@ def run_ours(args):
     from paper_2005_05398_gb300 import build
     build.build()
     wl = workload(args.workload)
+    if args.k is None:
+        args.k = wl["k"]
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
-    ctx = pkg.Context(wl, precision=1 if args.precision == "fp32" else 0, restart_m=args.restart, ncv=args.ncv,
-                      device=local, stream=stream)
+    ctx = pkg.Context(wl, precision={"fp64": 0, "fp32": 1, "mixed": 2}[args.precision], restart_m=args.restart,
+                      ncv=args.ncv, device=local, stream=stream)
     ctx.fm_set_shift(wl["shift"])
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -260,14 +262,15 @@ def run_ours(args):
     out = None
     if rank == 0:
         peaks = measured_peaks()
-        rl = roofline(prof, peaks)
+        rl = roofline(prof, peaks, args.workload)
         kern = {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
                     "share": round(v["ms"] / max(sum(p["ms"] for p in prof.values()), 1e-9), 4)} for k, v in prof.items()}
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64", "data": "synthetic (seeded N(0,1) Arnoldi start vectors)",
-               "config": {"workload": WORKLOAD, "system": "He-like L=0 (Z=2, two electrons, infinite core)",
-                          "grid": "96x96x24 intervals, cubic Hermite, R=40", "n_unknowns": n, "k": args.k,
+               "config": {"workload": args.workload, "system": f"{wl['system']} L={wl['J']} tau={wl['tau']} p={wl['p']}",
+                          "grid": f"{wl['nint'][0]}x{wl['nint'][1]}x{wl['nint'][2]} intervals, cubic Hermite, R={wl['R'][0]:g}",
+                          "n_unknowns": n, "k": args.k,
                           "shift": wl["shift"], "precond_precision": args.precision, "restart_m": args.restart,
                           "ncv": args.ncv, "l2": "inputs larger than L2 (Krylov basis and factors > 129 MB)",
                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
@@ -293,7 +296,7 @@ def run_kernel_loop(args):
     from paper_2005_05398_gb300 import build
     build.build()
     wl = workload(args.workload)
-    ctx = pkg.Context(wl, precision=1 if args.precision == "fp32" else 0, restart_m=args.restart, ncv=4)
+    ctx = pkg.Context(wl, precision={"fp64": 0, "fp32": 1, "mixed": 2}[args.precision], restart_m=args.restart, ncv=4)
     ctx.fm_set_shift(wl["shift"])
     x = torch.tensor(rand_vec(ctx.n, SEED_BASE), dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
@@ -321,10 +324,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
     ap.add_argument("--restart", type=int, default=40)
     ap.add_argument("--ncv", type=int, default=20)
-    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--k", type=int, default=None, help="eigenpairs per step (default: the workload's)")
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

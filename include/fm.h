@@ -87,13 +87,17 @@ typedef struct {
   double vs_cut;
 } fm_splitting;
 
-enum { FM_PREC_FP64 = 0, FM_PREC_FP32 = 1 };
+/* Precision modes.  FP64: float64 everywhere.  FP32: float32 preconditioner, float64 operator,
+ * FGMRES and Gram-Schmidt.  MIXED: float64 iterative refinement on the true float64 residual
+ * around float32 FGMRES corrections (float32 operator, preconditioner and Gram-Schmidt), each
+ * solved to a relative 3e-5; the result meets the same float64 tolerance. */
+enum { FM_PREC_FP64 = 0, FM_PREC_FP32 = 1, FM_PREC_MIXED = 2 };
 
 typedef struct {
   double tol;        /* relative residual of fm_solve (FGMRES true residual), e.g. 1e-12 */
   int restart_m;     /* FGMRES restart length (1..128) */
   int max_iters;     /* total FGMRES iteration limit per fm_solve */
-  int precision;     /* FM_PREC_FP64 or FM_PREC_FP32 (preconditioner arithmetic) */
+  int precision;     /* FM_PREC_FP64, FM_PREC_FP32 or FM_PREC_MIXED */
   int ncv;           /* Arnoldi basis size of fm_eigs (>= 2k + 1) */
   int max_restarts;  /* Arnoldi restarts of fm_eigs */
   double eig_tol;    /* fm_eigs: relative Ritz residual |h_{m+1,m} y_m| / |theta| at which a Ritz pair is
@@ -112,7 +116,7 @@ typedef struct {
 
 typedef struct {
   int iters;          /* FGMRES iterations (fm_solve) or total inner iterations (fm_eigs) */
-  int restarts;       /* FGMRES restarts or Arnoldi restarts */
+  int restarts;       /* FGMRES restarts (refinement steps in FM_PREC_MIXED) or Arnoldi restarts */
   int op_applies;     /* shift-invert operator applications (fm_eigs) */
   int converged;      /* 1 when every requested quantity met its tolerance */
   double resid;       /* final relative residual (fm_solve) or max eigen-residual (fm_eigs) */
@@ -132,6 +136,12 @@ void fm_default_opts(fm_opts* opts);
  * or one per solved component.  On error *out is NULL. */
 int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_splitting* split,
               const fm_opts* opts, fm_ctx** out);
+
+/* Device memory (bytes) that fm_create with these arguments would hold, from the same size
+ * plan (no allocation, no GPU work, no eigen-decompositions; within a few percent).  For
+ * admission control of concurrent solves.  fm_eigs_host adds k vectors on first use. */
+int fm_estimate_bytes(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_splitting* split,
+                      const fm_opts* opts, int64_t* bytes);
 
 /* Sizes: total unknowns, solved components, n_M = J - M0 + 1 (Section 2.2). */
 int fm_size(const fm_ctx* ctx, int64_t* n_unknowns, int* n_components, int* n_M);
@@ -165,7 +175,11 @@ int fm_solve(fm_ctx* ctx, double E, const double* rhs, double* x, fm_info* info)
 /* k eigenpairs of H c = E S c nearest 'shift' by restarted Arnoldi on the
  * shift-invert operator (H - shift S)^{-1} S (Eq. FM-lin; E = shift + 1/theta), each
  * operator application an FGMRES solve to max(tol, eig_tol / 10).  v0 (device, may be NULL = seeded normal start)
- * starts the iteration.  evals (host, k doubles) receive E sorted by |E - shift|;
+ * starts the iteration.  Only real eigenvalues are returned: complex-conjugate pairs of the
+ * non-symmetric collocation pencil (non-physical in the bound-state problem) are passed over,
+ * so the result is the k real eigenvalues nearest the shift.  An inner solve that ends more
+ * than 1e4 times above its tolerance makes the call report FM_ERR_NOT_CONVERGED.
+ * evals (host, k doubles) receive E sorted by |E - shift|;
  * evecs (device, k * n_unknowns, may be NULL) the eigenvectors normalised to unit
  * 2-norm with their largest-magnitude entry positive.  info may be NULL. */
 int fm_eigs(fm_ctx* ctx, double shift, int k, const double* v0, double* evals, double* evecs, fm_info* info);

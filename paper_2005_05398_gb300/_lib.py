@@ -55,6 +55,8 @@ SIGNATURES = {
     "fm_create": (c_int, [ctypes.POINTER(fm_system), ctypes.POINTER(fm_grid), c_int, ctypes.POINTER(fm_splitting),
                           ctypes.POINTER(fm_opts), ctypes.POINTER(c_void_p)]),
     "fm_size": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    "fm_estimate_bytes": (c_int, [ctypes.POINTER(fm_system), ctypes.POINTER(fm_grid), c_int,
+                                  ctypes.POINTER(fm_splitting), ctypes.POINTER(fm_opts), ctypes.POINTER(c_int64)]),
     "fm_component": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int64)]),
     "fm_apply": (c_int, [c_void_p, c_double, c_void_p, c_void_p]),
     "fm_apply_S": (c_int, [c_void_p, c_void_p, c_void_p]),
@@ -139,6 +141,27 @@ def make_structs(wl):
     return s, grids, len(gl), sp
 
 
+def make_opts(**opt):
+    o = fm_opts()
+    lib().fm_default_opts(ctypes.byref(o))
+    for k, v in opt.items():
+        if k == "stream":
+            o.stream = c_void_p(v.cuda_stream if hasattr(v, "cuda_stream") else v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def fm_estimate_bytes(wl, **opt):
+    """Device bytes fm_create would hold for this workload and options (no GPU work)."""
+    s, grids, ng, sp = make_structs(wl)
+    o = make_opts(**opt)
+    b = c_int64()
+    _check("fm_estimate_bytes", lib().fm_estimate_bytes(ctypes.byref(s), grids, ng, ctypes.byref(sp), ctypes.byref(o),
+                                                        ctypes.byref(b)))
+    return b.value
+
+
 def fm_host_decompose(A1, A2, descending=False):
     """(W-bar, W, lam) from libfm's host set-up code (numpy arrays; no GPU)."""
     import numpy as np
@@ -157,13 +180,7 @@ class Context:
     def __init__(self, wl, **opt):
         L = lib()
         self.wl = dict(wl)
-        o = fm_opts()
-        L.fm_default_opts(ctypes.byref(o))
-        for k, v in opt.items():
-            if k == "stream":
-                o.stream = c_void_p(v.cuda_stream if hasattr(v, "cuda_stream") else v)
-            else:
-                setattr(o, k, v)
+        o = make_opts(**opt)
         self.opts = o
         s, grids, ng, sp = make_structs(wl)
         h = c_void_p()

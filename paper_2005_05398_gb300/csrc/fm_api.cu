@@ -187,6 +187,147 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
   return converged ? FM_OK : FM_ERR_NOT_CONVERGED;
 }
 
+// float32 Gram-Schmidt (classical, DGKS re-orthogonalisation), coefficients and norm in float64
+static int orthogonalize32(fm_ctx* c, const float* V, int nv, float* w, double* h, double* nrm) {
+  std::vector<double> h1(nv), h2(nv);
+  int rc;
+  double before2;
+  if ((rc = dot_many32(c, w, c->N, 1, w, &before2))) return rc;
+  if ((rc = dot_many32(c, V, c->N, nv, w, h1.data()))) return rc;
+  double n2;
+  if ((rc = axpy_many_norm32(c, V, c->N, nv, h1.data(), -1.0f, w, &n2))) return rc;
+  for (int i = 0; i < nv; ++i) h[i] = h1[i];
+  double after = std::sqrt(std::max(n2, 0.0));
+  if (after < 0.7071067811865476 * std::sqrt(std::max(before2, 0.0))) {
+    if ((rc = dot_many32(c, V, c->N, nv, w, h2.data()))) return rc;
+    if ((rc = axpy_many_norm32(c, V, c->N, nv, h2.data(), -1.0f, w, &n2))) return rc;
+    for (int i = 0; i < nv; ++i) h[i] += h2[i];
+    after = std::sqrt(std::max(n2, 0.0));
+  }
+  *nrm = after;
+  return FM_OK;
+}
+
+// float32 right-preconditioned FGMRES for (H - E S) d = b (float32 operator, preconditioner and basis;
+// Givens and the small least-squares problem in float64).  d starts at zero.
+static int fgmres32(fm_ctx* c, double E, const float* b, float* d, double tol, int max_iters, int* iters_out) {
+  int rc;
+  const int m = c->opts.restart_m;
+  const int64_t N = c->N;
+  double b2;
+  if ((rc = dot_many32(c, b, N, 1, b, &b2))) return rc;
+  const double bnorm = std::sqrt(std::max(b2, 0.0));
+  *iters_out = 0;
+  FM_CUDA(cudaMemsetAsync(d, 0, N * sizeof(float), c->stream));
+  if (!(bnorm > 0.0)) return FM_OK;
+  float* r = c->r32;
+  FM_CUDA(cudaMemcpyAsync(r, b, N * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+  double beta = bnorm, beta_prev = HUGE_VAL;
+  std::vector<double> R((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 1), y(m);
+  int total = 0;
+  while (beta > tol * bnorm && total < max_iters && beta <= 0.5 * beta_prev) {
+    beta_prev = beta;
+    if ((rc = axpby32(c, (float)(1.0 / beta), r, 0.0f, c->V32))) return rc;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m && total < max_iters; ++j) {
+      float* Vj = c->V32 + (int64_t)j * N;
+      float* Zj = c->Z32 + (int64_t)j * N;
+      if ((rc = launch_precond32(c, Vj, Zj))) return rc;
+      if ((rc = launch_apply32(c, E, Zj, c->w32, false))) return rc;
+      double hn;
+      if ((rc = orthogonalize32(c, c->V32, j + 1, c->w32, h.data(), &hn))) return rc;
+      if (!std::isfinite(hn)) return FM_ERR_BREAKDOWN;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+      }
+      const double rr = std::hypot(h[j], hn);
+      cs[j] = (rr == 0.0) ? 1.0 : h[j] / rr;
+      sn[j] = (rr == 0.0) ? 0.0 : hn / rr;
+      h[j] = rr;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) R[(size_t)i * m + j] = h[i];
+      ++total;
+      jdone = j + 1;
+      if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0) break;
+      if ((rc = axpby32(c, (float)(1.0 / hn), c->w32, 0.0f, c->V32 + (int64_t)(j + 1) * N))) return rc;
+    }
+    for (int i = jdone - 1; i >= 0; --i) {
+      double sacc = g[i];
+      for (int k = i + 1; k < jdone; ++k) sacc -= R[(size_t)i * m + k] * y[k];
+      if (R[(size_t)i * m + i] == 0.0) return FM_ERR_BREAKDOWN;
+      y[i] = sacc / R[(size_t)i * m + i];
+    }
+    if ((rc = axpy_many_norm32(c, c->Z32, N, jdone, y.data(), 1.0f, d, nullptr))) return rc;
+    if ((rc = launch_apply32(c, E, d, c->w32, false))) return rc;  // float32 residual r = b - A d
+    if ((rc = axpby32(c, 1.0f, b, 0.0f, r))) return rc;
+    if ((rc = axpby32(c, -1.0f, c->w32, 1.0f, r))) return rc;
+    double r2;
+    if ((rc = dot_many32(c, r, N, 1, r, &r2))) return rc;
+    beta = std::sqrt(std::max(r2, 0.0));
+    if (!std::isfinite(beta)) return FM_ERR_BREAKDOWN;
+  }
+  *iters_out = total;
+  return FM_OK;
+}
+
+// Mixed precision: float64 iterative refinement (true residual r = b - (H - E S) x in float64)
+// around float32 FGMRES corrections, each solved to a relative 3e-5.
+static int ir_solve(fm_ctx* c, double E, const double* b, double* x, double tol, int max_iters, int* iters_out,
+                    int* outer_out, double* resid_out) {
+  int rc;
+  double bnorm;
+  if ((rc = nrm2(c, b, &bnorm))) return rc;
+  *iters_out = 0;
+  *outer_out = 0;
+  if (!(bnorm > 0.0)) {
+    FM_CUDA(cudaMemsetAsync(x, 0, c->N * sizeof(double), c->stream));
+    *resid_out = 0.0;
+    return std::isfinite(bnorm) ? FM_OK : FM_ERR_BREAKDOWN;
+  }
+  double* r = c->r;
+  if ((rc = launch_apply(c, E, x, r, false))) return rc;
+  if ((rc = axpby(c, 1.0, b, -1.0, r))) return rc;
+  double beta;
+  if ((rc = nrm2(c, r, &beta))) return rc;
+  double beta_prev = HUGE_VAL;
+  int total = 0;
+  bool converged = false;
+  while (true) {
+    if (!std::isfinite(beta)) return FM_ERR_BREAKDOWN;
+    if (beta <= tol * bnorm) {
+      converged = true;
+      break;
+    }
+    if (total >= max_iters || beta > 0.5 * beta_prev) break;
+    beta_prev = beta;
+    if ((rc = to32(c, r, 1.0 / beta, c->d32))) return rc;  // normalised residual as the float32 right-hand side
+    int it = 0;
+    if ((rc = fgmres32(c, E, c->d32, c->e32, 3e-5, max_iters - total, &it))) return rc;
+    total += it;
+    ++*outer_out;
+    if ((rc = add32(c, c->e32, beta, x))) return rc;  // x += beta * correction
+    if ((rc = launch_apply(c, E, x, r, false))) return rc;
+    if ((rc = axpby(c, 1.0, b, -1.0, r))) return rc;
+    if ((rc = nrm2(c, r, &beta))) return rc;
+  }
+  *iters_out = total;
+  *resid_out = beta / bnorm;
+  return converged ? FM_OK : FM_ERR_NOT_CONVERGED;
+}
+
+// (H - E S) x = b with the context's precision mode: float64 FGMRES (modes 0, 1) or float64
+// iterative refinement around float32 FGMRES (mode 2).
+static int solve_any(fm_ctx* c, double E, const double* b, double* x, double tol, int max_iters, int* iters_out,
+                     int* restarts_out, double* resid_out) {
+  if (c->opts.precision == FM_PREC_MIXED) return ir_solve(c, E, b, x, tol, max_iters, iters_out, restarts_out, resid_out);
+  return fgmres(c, E, b, x, tol, max_iters, iters_out, restarts_out, resid_out);
+}
+
 // Householder-free modified Gram-Schmidt QR of an m x k matrix (row-major), twice.
 static bool small_qr(int m, int k, std::vector<double>& Y) {
   for (int pass = 0; pass < 2; ++pass)
@@ -284,7 +425,7 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
   if (nM <= 0 || nM > 8) return FM_ERR_ARG;
   if (o.z_eigs == 1 && nM != 1) return FM_ERR_ARG;
   if (o.restart_m < 1 || o.restart_m > 256 || o.max_iters < 1 || !(o.tol > 0) || o.ncv < 3 || o.ncv > 64 ||
-      o.max_restarts < 0 || !(o.eig_tol > 0) || (o.precision != 0 && o.precision != 1) || o.y_solver < 0 ||
+      o.max_restarts < 0 || !(o.eig_tol > 0) || o.precision < 0 || o.precision > 2 || o.y_solver < 0 ||
       o.y_solver > 2)
     return FM_ERR_ARG;
   fm_ctx* c = new fm_ctx();
@@ -320,10 +461,27 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
       (rc = dev_alloc(c, (void**)&c->tuneWU, (size_t)8 * N * 8)))
     return fail(rc);
   if (cudaMallocHost((void**)&c->red_host, 8192 * 8) != cudaSuccess) return fail(FM_ERR_OOM);
+  if (o.precision == FM_PREC_MIXED) {  // float32 Krylov workspace of the mixed-precision solves
+    if ((rc = dev_alloc(c, (void**)&c->V32, (size_t)(m + 1) * N * 4)) || (rc = dev_alloc(c, (void**)&c->Z32, (size_t)m * N * 4)) ||
+        (rc = dev_alloc(c, (void**)&c->w32, N * 4)) || (rc = dev_alloc(c, (void**)&c->r32, N * 4)) ||
+        (rc = dev_alloc(c, (void**)&c->d32, N * 4)) || (rc = dev_alloc(c, (void**)&c->e32, N * 4)) ||
+        (rc = dev_alloc(c, (void**)&c->P32, N * 4)) || (rc = dev_alloc(c, (void**)&c->Q32, N * 4)) ||
+        (rc = dev_alloc(c, (void**)&c->R32, N * 4)))
+      return fail(rc);
+  }
   c->m_alloc = m;
   c->ncv_alloc = o.ncv;
   *out = c;
   return FM_OK;
+}
+
+int fm_estimate_bytes(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_splitting* split,
+                      const fm_opts* opts, int64_t* bytes) {
+  if (!sys || !grids || !split || !bytes || n_grids < 1) return FM_ERR_ARG;
+  fm_opts o;
+  if (opts) o = *opts;
+  else fm_default_opts(&o);
+  return estimate_bytes(sys, grids, n_grids, split, &o, bytes);
 }
 
 int fm_size(const fm_ctx* c, int64_t* n, int* ncomp, int* nM) {
@@ -428,7 +586,7 @@ int fm_solve(fm_ctx* c, double E, const double* rhs, double* x, fm_info* info) {
     if ((rc = setup_shift(c, E))) return rc;
   int it = 0, rs = 0;
   double res = 0.0;
-  rc = fgmres(c, E, rhs, x, c->opts.tol, c->opts.max_iters, &it, &rs, &res);
+  rc = solve_any(c, E, rhs, x, c->opts.tol, c->opts.max_iters, &it, &rs, &res);
   FM_CUDA(cudaStreamSynchronize(c->stream));
   if (info) {
     std::memset(info, 0, sizeof(*info));
@@ -473,13 +631,14 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
   std::vector<double> Y;  // eigenvectors of the projected matrix (nsz x nsz)
   std::vector<std::vector<double>> hist;  // eigenvalue history of each wanted Ritz value
   const bool verbose = getenv("FM_VERBOSE") != nullptr;
+  double worst_inner = 0.0;  // largest relative residual an inner solve ended with
   double max_res = 0.0;
   while (true) {
     bool done = false;
     for (int j = kcur; j < m; ++j) {
       double* Vj = V + (int64_t)j * N;
       double* w = V + (int64_t)(j + 1) * N;
-      if (c->opts.tune && nsz >= 1 && !best.empty()) {
+      if (c->opts.tune && c->opts.precision != FM_PREC_MIXED && nsz >= 1 && !best.empty()) {
         // tuned preconditioner (Freitag-Spence): U = orthonormalised Ritz vectors of the wanted values
         std::vector<int> cols;
         for (const auto& rz : best)
@@ -498,10 +657,11 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
       int it = 0, rs = 0;
       double res = 0.0;
       const double inner_tol = std::max(c->opts.tol, 0.1 * c->opts.eig_tol);
-      rc = fgmres(c, shift, c->tmpN, w, inner_tol, c->opts.max_iters, &it, &rs, &res);
+      rc = solve_any(c, shift, c->tmpN, w, inner_tol, c->opts.max_iters, &it, &rs, &res);
       inner += it;
       ++ops;
       if (rc != FM_OK && rc != FM_ERR_NOT_CONVERGED) return rc;
+      worst_inner = std::max(worst_inner, res);
       std::vector<double> h(j + 1);
       double hn;
       if ((rc = orthogonalize(c, V, j + 1, w, h.data(), &hn))) return rc;
@@ -597,6 +757,8 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
     ++restarts;
   }
   c->n_tune = 0;
+  // an inner solve that stalled far above its tolerance makes the Krylov relation unreliable
+  if (worst_inner > 1e4 * std::max(c->opts.tol, 0.1 * c->opts.eig_tol)) converged = false;
   if (nsz < k || (int)best.size() < k) return FM_ERR_NOT_CONVERGED;
   // eigenvectors c = V y, energies E = shift + 1/theta
   std::vector<double> Ek(k);

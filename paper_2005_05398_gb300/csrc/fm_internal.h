@@ -42,8 +42,15 @@ struct Source {          // one V^(s) coupling source of a component (Eq. FM-pre
   bool sym = false;
 };
 
+// float32 copies of the operator tables (mixed-precision inner solves)
+struct Tabs32 {
+  float *Sx = nullptr, *D2x = nullptr, *Sy = nullptr, *D2y = nullptr, *Sz = nullptr, *D1z = nullptr, *D2z = nullptr;
+  float *zp = nullptr, *W = nullptr, *A = nullptr, *B = nullptr, *iy2 = nullptr, *cval = nullptr, *cw = nullptr;
+};
+
 struct Comp {
   int label = 0;                 // particle label alpha
+  Tabs32 f32;
   Axis ax, ay, az;
   int nx = 0, ny = 0, nz = 0;
   int64_t npts = 0, off = 0;     // points per M' block, offset in the vector
@@ -51,7 +58,10 @@ struct Comp {
   std::vector<Source> sources;
   // device tables
   AxisDev dx, dy, dz;
-  double* W = nullptr;           // [nz][nx][ny] left-hand potential V_a + sum V^(l)_b (Eq. FM-pre)
+  double* W = nullptr;           // [nM][nz][nx][ny] V_a + sum V^(l)_b + q M'(M'+1) + (J(J+1)-2M'^2)/y^2, q = 1/x^2+1/y^2
+  double* A = nullptr;           // [nz][nx][ny] q (1 - z^2)
+  double* B = nullptr;           // [nM][nz][nx][ny] 2 (M'+1) z q
+  double* iy2 = nullptr;         // [ny] 1/y^2
   // coupling tables: n_act active points, per (source s): taps and weights
   int n_act = 0;
   int* act_pt = nullptr;         // [n_act] point index (k*nx + i)*ny + j
@@ -108,11 +118,18 @@ struct fm_ctx {
   double* P = nullptr;           // [N] y/x-pass planes for the apply (S_x S_y c)
   double* Q = nullptr;           // [N] (D_x S_y c)
   double* R = nullptr;           // [N] (S_x D_y c)
+  float* P32 = nullptr; float* Q32 = nullptr; float* R32 = nullptr;  // float32 apply scratch
   double* t64 = nullptr;         // [N] preconditioner stage buffer
   double* u64 = nullptr;
   float* t32 = nullptr;
   float* u32 = nullptr;
   int m_alloc = 0;
+  float* V32 = nullptr;          // float32 FGMRES basis [(m+1)][N] (mixed precision)
+  float* Z32 = nullptr;          // [m][N]
+  float* w32 = nullptr;          // [N]
+  float* r32 = nullptr;          // [N]
+  float* d32 = nullptr;          // [N]
+  float* e32 = nullptr;          // [N]
   double* V = nullptr;           // FGMRES basis [(m+1)][N]
   double* Z = nullptr;           // FGMRES preconditioned directions [m][N]
   double* w = nullptr;           // [N]
@@ -154,9 +171,19 @@ int dev_alloc(fm_ctx* c, void** p, size_t bytes);
 int upload(fm_ctx* c, void** p, const void* host, size_t bytes);
 int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids);       // grids, tables, coupling, z/x decompositions
 int setup_shift(fm_ctx* c, double Estar);                            // banded y systems
+int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const fm_splitting* split, const fm_opts* o,
+                   int64_t* out);
 // kernels (fm_kernels.cu)
 int launch_apply(fm_ctx* c, double E, const double* x, double* y, bool only_S);
+int launch_apply32(fm_ctx* c, double E, const float* x, float* y, bool only_S);
 int launch_precond(fm_ctx* c, const double* x, double* y);
+int launch_precond32(fm_ctx* c, const float* x, float* y);
+int dot_many32(fm_ctx* c, const float* V, int64_t ldv, int nv, const float* w, double* h_host);
+int axpy_many_norm32(fm_ctx* c, const float* V, int64_t ldv, int nv, const double* h_host, float sign, float* w,
+                     double* nrm2_out);
+int to32(fm_ctx* c, const double* x, double a, float* y);
+int add32(fm_ctx* c, const float* y, double a, double* x);
+int axpby32(fm_ctx* c, float a, const float* x, float b, float* y);
 int dot_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, double* h_host);
 int dot_many_x(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_host);
 int axpy_many_norm(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double* nrm2_out);

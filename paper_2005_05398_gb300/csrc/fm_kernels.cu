@@ -26,35 +26,36 @@ constexpr int kMaxM = 8;  // largest n_M handled by the register arrays (J <= 7)
 // apply, pass 1: for one (component, M', z-dof k) plane c[i][j] (n_x x n_y) and a tile
 // of TX x-collocation points: P = (S_x (x) S_y) c, Q = (D2_x (x) S_y) c, R = (S_x (x) D2_y) c.
 // ---------------------------------------------------------------------------
-template <int TX>
-__global__ void __launch_bounds__(256) k_apply_xy(const double* __restrict__ c, double* __restrict__ P,
-                                                  double* __restrict__ Q, double* __restrict__ R, int nx, int ny,
-                                                  const int* __restrict__ bx, const double* __restrict__ Sx,
-                                                  const double* __restrict__ D2x, const int* __restrict__ by,
-                                                  const double* __restrict__ Sy, const double* __restrict__ D2y,
+template <int TX, typename T>
+__global__ void __launch_bounds__(256) k_apply_xy(const T* __restrict__ c, T* __restrict__ P,
+                                                  T* __restrict__ Q, T* __restrict__ R, int nx, int ny,
+                                                  const int* __restrict__ bx, const T* __restrict__ Sx,
+                                                  const T* __restrict__ D2x, const int* __restrict__ by,
+                                                  const T* __restrict__ Sy, const T* __restrict__ D2y,
                                                   bool only_S) {
-  extern __shared__ double sm[];
+  extern __shared__ unsigned char smraw_xy[];
+  T* sm = reinterpret_cast<T*>(smraw_xy);
   const int rows = TX + 2;
-  double* cs = sm;                 // [rows][ny]
-  double* As = sm + rows * ny;     // [rows][ny]  S_y pass
-  double* Bs = As + rows * ny;     // [rows][ny]  D2_y pass
+  T* cs = sm;                 // [rows][ny]
+  T* As = sm + rows * ny;     // [rows][ny]  S_y pass
+  T* Bs = As + rows * ny;     // [rows][ny]  D2_y pass
   const int64_t plane = (int64_t)blockIdx.y * nx * ny;
   const int xi0 = blockIdx.x * TX;
   const int r0 = xi0 - 1;
   for (int idx = threadIdx.x; idx < rows * ny; idx += blockDim.x) {
     const int r = r0 + idx / ny;
-    cs[idx] = (r >= 0 && r < nx) ? c[plane + (int64_t)r * ny + (idx % ny)] : 0.0;
+    cs[idx] = (r >= 0 && r < nx) ? c[plane + (int64_t)r * ny + (idx % ny)] : (T)0;
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < rows * ny; idx += blockDim.x) {
     const int r = idx / ny, eta = idx % ny;
     const int b = by[eta];
-    double a = 0.0, d = 0.0;
+    T a = 0, d = 0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int j = b + t;
       if (j >= 0 && j < ny) {
-        const double v = cs[r * ny + j];
+        const T v = cs[r * ny + j];
         a = fma(Sy[eta * 4 + t], v, a);
         d = fma(D2y[eta * 4 + t], v, d);
       }
@@ -67,12 +68,12 @@ __global__ void __launch_bounds__(256) k_apply_xy(const double* __restrict__ c, 
     const int xi = xi0 + idx / ny, eta = idx % ny;
     if (xi >= nx) continue;
     const int b = bx[xi] - r0;
-    double p = 0.0, q = 0.0, rr = 0.0;
+    T p = 0, q = 0, rr = 0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int lr = b + t;
       if (lr >= 0 && lr < rows) {
-        const double a = As[lr * ny + eta];
+        const T a = As[lr * ny + eta];
         p = fma(Sx[xi * 4 + t], a, p);
         q = fma(D2x[xi * 4 + t], a, q);
         rr = fma(Sx[xi * 4 + t], Bs[lr * ny + eta], rr);
@@ -87,27 +88,30 @@ __global__ void __launch_bounds__(256) k_apply_xy(const double* __restrict__ c, 
   }
 }
 
+template <typename T>
 struct ZPassArgs {
-  const double* P;
-  const double* Q;
-  const double* R;
-  double* y;
-  const double* W;       // [nz][nx][ny]
+  const T* P;
+  const T* Q;
+  const T* R;
+  T* y;
+  const T* W;       // [nM][nz][nx][ny] folded diagonal coefficient (without -E)
+  const T* A;       // [nz][nx][ny] (1/x^2 + 1/y^2)(1 - z^2)
+  const T* B;       // [nM][nz][nx][ny] 2 (M'+1) z (1/x^2 + 1/y^2)
+  const T* iy2;     // [ny] 1/y^2
   const int* bz;
-  const double* Sz;
-  const double* D1z;
-  const double* D2z;
-  const double* zp;
-  const double* xp;
-  const double* yp;
+  const T* Sz;
+  const T* D1z;
+  const T* D2z;
+  const T* zp;
   int nx, ny, nz, nM, M0, J;
-  double E;
-  double lamp[kMaxM];    // lambda-hat^{J, M'} for M'+1 coupling
-  double lamm[kMaxM];    // lambda-hat^{J, -M'} for M'-1 coupling
+  T E;
+  T lamp[kMaxM];    // lambda-hat^{J, M'} for M'+1 coupling
+  T lamm[kMaxM];    // lambda-hat^{J, -M'} for M'-1 coupling
 };
 
 // apply, pass 2: one thread per output point (M', zeta, xi, eta) of a component.
-__global__ void __launch_bounds__(256) k_apply_z(ZPassArgs a, bool only_S) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_z(ZPassArgs<T> a, bool only_S) {
   const int64_t npts = (int64_t)a.nz * a.nx * a.ny;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= npts * a.nM) return;
@@ -117,13 +121,13 @@ __global__ void __launch_bounds__(256) k_apply_z(ZPassArgs a, bool only_S) {
   const int64_t xy = pt - (int64_t)zeta * a.nx * a.ny;
   const int b = a.bz[zeta];
   const int64_t blk = (int64_t)iM * npts;
-  double U = 0, Uz = 0, Uzz = 0, Uxx = 0, Uyy = 0;
+  T U = 0, Uz = 0, Uzz = 0, Uxx = 0, Uyy = 0;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     const int k = b + t;
     if (k >= 0 && k < a.nz) {
       const int64_t o = blk + (int64_t)k * a.nx * a.ny + xy;
-      const double p = a.P[o];
+      const T p = a.P[o];
       U = fma(a.Sz[zeta * 4 + t], p, U);
       if (!only_S) {
         Uz = fma(a.D1z[zeta * 4 + t], p, Uz);
@@ -137,29 +141,32 @@ __global__ void __launch_bounds__(256) k_apply_z(ZPassArgs a, bool only_S) {
     a.y[gid] = U;
     return;
   }
-  const int xi = (int)(xy / a.ny), eta = (int)(xy - (int64_t)xi * a.ny);
-  const double x = a.xp[xi], y = a.yp[eta], z = a.zp[zeta];
-  const double ix2 = 1.0 / (x * x), iy2 = 1.0 / (y * y);
-  const double q = ix2 + iy2;
+  // pointwise coefficients folded at set-up: W = V_a + sum V^(l) + q M'(M'+1) + (J(J+1) - 2M'^2)/y^2
+  const T C = a.W[blk + pt] - a.E;
+  T out = fma(C, U, fma(a.B[blk + pt], Uz, fma(-a.A[pt], Uzz, -Uyy - Uxx)));
+  if (a.nM == 1) {
+    a.y[gid] = out;
+    return;
+  }
+  const int eta = (int)(xy % a.ny);
+  const T z = a.zp[zeta];
+  const T iy2 = a.iy2[eta];
   const int Mp = a.M0 + iM;
-  const double jm = (double)(a.J * (a.J + 1) - 2 * Mp * Mp);
-  const double C = q * (double)(Mp * (Mp + 1)) + jm * iy2 + a.W[pt] - a.E;
-  double out = -Uyy - Uxx - q * (1.0 - z * z) * Uzz + 2.0 * (Mp + 1) * z * q * Uz + C * U;
   if (iM + 1 < a.nM) {  // lambda-hat^{J,M'}/y^2 [-(1-z^2) d/dz + 2(M'+1) z] psi_{M'+1}
-    double Up = 0, Uzp = 0;
+    T Up = 0, Uzp = 0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int k = b + t;
       if (k >= 0 && k < a.nz) {
-        const double p = a.P[blk + npts + (int64_t)k * a.nx * a.ny + xy];
+        const T p = a.P[blk + npts + (int64_t)k * a.nx * a.ny + xy];
         Up = fma(a.Sz[zeta * 4 + t], p, Up);
         Uzp = fma(a.D1z[zeta * 4 + t], p, Uzp);
       }
     }
-    out += a.lamp[iM] * iy2 * (-(1.0 - z * z) * Uzp + 2.0 * (Mp + 1) * z * Up);
+    out += a.lamp[iM] * iy2 * (-((T)1 - z * z) * Uzp + (T)(2 * (Mp + 1)) * z * Up);
   }
   if (iM >= 1) {  // lambda-hat^{J,-M'}/y^2 d/dz psi_{M'-1}
-    double Uzm = 0;
+    T Uzm = 0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int k = b + t;
@@ -170,17 +177,18 @@ __global__ void __launch_bounds__(256) k_apply_z(ZPassArgs a, bool only_S) {
   a.y[gid] = out;
 }
 
+template <typename T>
 struct CouplingArgs {
-  const double* x;      // full input vector
-  double* y;            // full output vector (accumulated)
+  const T* x;           // full input vector
+  T* y;                 // full output vector (accumulated)
   int64_t row_off;      // offset of the target component
   int64_t npts;         // points per M' block of the target component
   int n_act;
   const int* act_pt;
   int ns;
   const int* base[3];   // per source: [3][n_act]
-  const double* val[3]; // per source: [12][n_act]
-  const double* w[3];   // per source: [nM*nM][n_act]
+  const T* val[3];      // per source: [12][n_act]
+  const T* w[3];        // per source: [nM*nM][n_act]
   int64_t src_off[3];
   int64_t src_npts[3];
   int snx[3], sny[3], snz[3];
@@ -188,15 +196,16 @@ struct CouplingArgs {
 };
 
 // V^(s) coupling: one thread per active collocation point of a component.
-__global__ void __launch_bounds__(128) k_apply_coupling(CouplingArgs a) {
+template <typename T>
+__global__ void __launch_bounds__(128) k_apply_coupling(CouplingArgs<T> a) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.n_act) return;
-  double acc[kMaxM];
+  T acc[kMaxM];
 #pragma unroll
-  for (int m = 0; m < kMaxM; ++m) acc[m] = 0.0;
+  for (int m = 0; m < kMaxM; ++m) acc[m] = (T)0;
   for (int s = 0; s < a.ns; ++s) {
     const int bz = a.base[s][p], bx = a.base[s][a.n_act + p], by = a.base[s][2 * a.n_act + p];
-    double vz[4], vx[4], vy[4];
+    T vz[4], vx[4], vy[4];
     int iz[4], ix[4], iy[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -208,15 +217,15 @@ __global__ void __launch_bounds__(128) k_apply_coupling(CouplingArgs a) {
       iy[t] = min(max(by + t, 0), a.sny[s] - 1);
     }
     for (int jM = 0; jM < a.nM; ++jM) {
-      const double* cb = a.x + a.src_off[s] + (int64_t)jM * a.src_npts[s];
-      double sz = 0.0;
+      const T* cb = a.x + a.src_off[s] + (int64_t)jM * a.src_npts[s];
+      T sz = 0;
 #pragma unroll
       for (int tz = 0; tz < 4; ++tz) {
-        double sx = 0.0;
+        T sx = 0;
 #pragma unroll
         for (int tx = 0; tx < 4; ++tx) {
-          const double* row = cb + ((int64_t)iz[tz] * a.snx[s] + ix[tx]) * a.sny[s];
-          double sy = vy[0] * row[iy[0]];
+          const T* row = cb + ((int64_t)iz[tz] * a.snx[s] + ix[tx]) * a.sny[s];
+          T sy = vy[0] * row[iy[0]];
           sy = fma(vy[1], row[iy[1]], sy);
           sy = fma(vy[2], row[iy[2]], sy);
           sy = fma(vy[3], row[iy[3]], sy);
@@ -534,46 +543,160 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // partial[j][block] = sum over this block's slice of V[j] . w  (j < nv), and for j = nv, when
-// 'extra' is given, extra . w
+// 'extra' is given, extra . w.  The vectors are taken eight at a time so that every thread keeps
+// eight independent loads in flight per element; the eight partial sums are reduced together.
 __global__ void __launch_bounds__(kRedThreads) k_dot_many(const double* __restrict__ V, int64_t ldv, int nv,
                                                          const double* __restrict__ w, int64_t n,
                                                          double* __restrict__ partial, const double* __restrict__ extra) {
-  __shared__ double sh[32];
+  constexpr int JT = 8;
+  __shared__ double sh[JT][kRedThreads / 32];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * chunk;
   const int64_t hi = min(n, lo + chunk);
   const int nt = nv + (extra ? 1 : 0);
-  for (int j = 0; j < nt; ++j) {
-    const double* v = (j < nv) ? V + (int64_t)j * ldv : extra;
-    double s = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s = fma(v[i], w[i], s);
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j0 = 0; j0 < nt; j0 += JT) {
+    const int nj = min(JT, nt - j0);
+    const double* vp[JT];
+#pragma unroll
+    for (int u = 0; u < JT; ++u) {
+      const int j = j0 + min(u, nj - 1);
+      vp[u] = (j < nv) ? V + (int64_t)j * ldv : extra;
+    }
+    double acc[JT];
+#pragma unroll
+    for (int u = 0; u < JT; ++u) acc[u] = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int u = 0; u < JT; ++u)
+        if (u < nj) acc[u] = fma(vp[u][i], wi, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < JT; ++u) {
+      double v = acc[u];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[u][wid] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nj) {
+      double r = 0.0;
+      for (int q = 0; q < kRedThreads / 32; ++q) r += sh[threadIdx.x][q];
+      partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = r;
+    }
+    __syncthreads();
   }
 }
 
-__global__ void k_dot_finish(const double* __restrict__ partial, int nb, int nv, double* __restrict__ h) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nv) return;
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += partial[(int64_t)j * nb + b];
-  h[j] = s;
+// float32 vectors: partial[j][block] (float64) = V[j] . w over the block's slice (eight vectors per pass)
+__global__ void __launch_bounds__(kRedThreads) k_dot_many32(const float* __restrict__ V, int64_t ldv, int nv,
+                                                           const float* __restrict__ w, int64_t n,
+                                                           double* __restrict__ partial) {
+  constexpr int JT = 8;
+  __shared__ double sh[JT][kRedThreads / 32];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j0 = 0; j0 < nv; j0 += JT) {
+    const int nj = min(JT, nv - j0);
+    float acc[JT];
+#pragma unroll
+    for (int u = 0; u < JT; ++u) acc[u] = 0.0f;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const float wi = w[i];
+#pragma unroll
+      for (int u = 0; u < JT; ++u)
+        if (u < nj) acc[u] = fmaf(V[(int64_t)(j0 + u) * ldv + i], wi, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < JT; ++u) {
+      double v = (double)acc[u];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[u][wid] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nj) {
+      double r = 0.0;
+      for (int q = 0; q < kRedThreads / 32; ++q) r += sh[threadIdx.x][q];
+      partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = r;
+    }
+    __syncthreads();
+  }
 }
 
-// w += sign * sum_j h[j] V[j], and partial[block] = sum over the block's slice of the new w^2
+// float32: w += sign * sum_j h[j] V[j], partial[block] = sum of the new w^2 (float64)
+__global__ void __launch_bounds__(kRedThreads) k_axpy_many_norm32(const float* __restrict__ V, int64_t ldv, int nv,
+                                                                 const float* __restrict__ h, float sign,
+                                                                 float* __restrict__ w, int64_t n,
+                                                                 double* __restrict__ partial) {
+  __shared__ double sh[32];
+  float acc = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    int j = 0;
+    for (; j + 3 < nv; j += 4) {
+      s0 = fmaf(h[j], V[(int64_t)j * ldv + i], s0);
+      s1 = fmaf(h[j + 1], V[(int64_t)(j + 1) * ldv + i], s1);
+      s2 = fmaf(h[j + 2], V[(int64_t)(j + 2) * ldv + i], s2);
+      s3 = fmaf(h[j + 3], V[(int64_t)(j + 3) * ldv + i], s3);
+    }
+    for (; j < nv; ++j) s0 = fmaf(h[j], V[(int64_t)j * ldv + i], s0);
+    const float v = fmaf(sign, (s0 + s1) + (s2 + s3), w[i]);
+    w[i] = v;
+    acc = fmaf(v, v, acc);
+  }
+  const double a = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = a;
+}
+
+// y32 = (float)(a * x64)
+__global__ void k_to32(const double* __restrict__ x, double a, float* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)(a * x[i]);
+}
+
+// x64 += a * (double)y32
+__global__ void k_add32(const float* __restrict__ y, double a, double* __restrict__ x, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = fma(a, (double)y[i], x[i]);
+}
+
+// float32 y = a x + b y
+__global__ void k_axpby32(float a, const float* __restrict__ x, float b, float* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + (b == 0.0f ? 0.0f : b * y[i]);
+}
+
+// h[j] = sum_b partial[j][b]: one warp per j, fixed order (lane-strided sums, then a shuffle tree)
+__global__ void k_dot_finish(const double* __restrict__ partial, int nb, int nv, double* __restrict__ h) {
+  const int j = blockIdx.x;
+  if (j >= nv) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 32) s += partial[(int64_t)j * nb + b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) h[j] = s;
+}
+
+// w += sign * sum_j h[j] V[j], and partial[block] = sum over the block's elements of the new w^2
+// (grid-stride, four independent accumulators over j so that several loads are in flight)
 __global__ void __launch_bounds__(kRedThreads) k_axpy_many_norm(const double* __restrict__ V, int64_t ldv, int nv,
                                                                const double* __restrict__ h, double sign,
                                                                double* __restrict__ w, int64_t n,
                                                                double* __restrict__ partial) {
   __shared__ double sh[32];
-  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t lo = (int64_t)blockIdx.x * chunk;
-  const int64_t hi = min(n, lo + chunk);
   double acc = 0.0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < nv; ++j) s = fma(h[j], V[(int64_t)j * ldv + i], s);
-    const double v = fma(sign, s, w[i]);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int j = 0;
+    for (; j + 3 < nv; j += 4) {
+      s0 = fma(h[j], V[(int64_t)j * ldv + i], s0);
+      s1 = fma(h[j + 1], V[(int64_t)(j + 1) * ldv + i], s1);
+      s2 = fma(h[j + 2], V[(int64_t)(j + 2) * ldv + i], s2);
+      s3 = fma(h[j + 3], V[(int64_t)(j + 3) * ldv + i], s3);
+    }
+    for (; j < nv; ++j) s0 = fma(h[j], V[(int64_t)j * ldv + i], s0);
+    const double v = fma(sign, (s0 + s1) + (s2 + s3), w[i]);
     w[i] = v;
     acc = fma(v, v, acc);
   }
@@ -586,9 +709,16 @@ __global__ void __launch_bounds__(256) k_axpy_many(const double* __restrict__ V,
                                                    const double* __restrict__ h, double sign, double* __restrict__ w,
                                                    int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < nv; ++j) s = fma(h[j], V[(int64_t)j * ldv + i], s);
-    w[i] = fma(sign, s, w[i]);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int j = 0;
+    for (; j + 3 < nv; j += 4) {
+      s0 = fma(h[j], V[(int64_t)j * ldv + i], s0);
+      s1 = fma(h[j + 1], V[(int64_t)(j + 1) * ldv + i], s1);
+      s2 = fma(h[j + 2], V[(int64_t)(j + 2) * ldv + i], s2);
+      s3 = fma(h[j + 3], V[(int64_t)(j + 3) * ldv + i], s3);
+    }
+    for (; j < nv; ++j) s0 = fma(h[j], V[(int64_t)j * ldv + i], s0);
+    w[i] = fma(sign, (s0 + s1) + (s2 + s3), w[i]);
   }
 }
 
@@ -668,61 +798,83 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
 
 namespace fmi {
 
-int launch_apply(fm_ctx* c, double E, const double* x, double* y, bool only_S) {
+template <typename T>
+struct ApplyTabs {
+  const T *Sx, *D2x, *Sy, *D2y, *Sz, *D1z, *D2z, *zp, *W, *A, *B, *iy2, *cval, *cw;
+};
+
+template <typename T>
+static ApplyTabs<T> tabs_of(const Comp& cp);
+
+template <>
+ApplyTabs<double> tabs_of<double>(const Comp& cp) {
+  return {cp.dx.S, cp.dx.D2, cp.dy.S, cp.dy.D2, cp.dz.S, cp.dz.D1, cp.dz.D2, cp.dz.pts, cp.W, cp.A, cp.B, cp.iy2,
+          cp.cpl_val, cp.cpl_w};
+}
+
+template <>
+ApplyTabs<float> tabs_of<float>(const Comp& cp) {
+  return {cp.f32.Sx, cp.f32.D2x, cp.f32.Sy, cp.f32.D2y, cp.f32.Sz, cp.f32.D1z, cp.f32.D2z, cp.f32.zp, cp.f32.W,
+          cp.f32.A, cp.f32.B, cp.f32.iy2, cp.f32.cval, cp.f32.cw};
+}
+
+// y = (H - E S) x (only_S: y = S x) with scratch planes P, Q, R, in the element type T.
+template <typename T>
+static int apply_t(fm_ctx* c, double E, const T* x, T* y, bool only_S, T* P, T* Q, T* R, bool timed) {
+  const double fscale = std::is_same<T, float>::value ? 1.0 : 1.0;
   for (auto& cp : c->comps) {
+    const ApplyTabs<T> tb = tabs_of<T>(cp);
     const int64_t off = cp.off;
     constexpr int TX = 8;
-    const size_t smem = (size_t)3 * (TX + 2) * cp.ny * sizeof(double);
+    const size_t smem = (size_t)3 * (TX + 2) * cp.ny * sizeof(T);
     dim3 g1((cp.nx + TX - 1) / TX, cp.nz * c->nM);
     {
-      const int tk_ = prof_begin(c, FM_KERNEL_APPLY_XY);
-      k_apply_xy<TX><<<g1, 256, smem, c->stream>>>(x + off, c->P + off, c->Q + off, c->R + off, cp.nx, cp.ny, cp.dx.base,
-                                                 cp.dx.S, cp.dx.D2, cp.dy.base, cp.dy.S, cp.dy.D2, only_S);
-      prof_end(c, tk_, (double)cp.npts * c->nM * (only_S ? 16.0 : 40.0), (double)cp.npts * c->nM * (only_S ? 16.0 : 32.0));
+      const int tk_ = timed ? prof_begin(c, FM_KERNEL_APPLY_XY) : -1;
+      k_apply_xy<TX, T><<<g1, 256, smem, c->stream>>>(x + off, P + off, Q + off, R + off, cp.nx, cp.ny, cp.dx.base, tb.Sx,
+                                                      tb.D2x, cp.dy.base, tb.Sy, tb.D2y, only_S);
+      prof_end(c, tk_, fscale * cp.npts * c->nM * (only_S ? 16.0 : 40.0), (double)cp.npts * c->nM * (only_S ? 2.0 : 4.0) * sizeof(T));
     }
     c->launches++;
-    ZPassArgs a;
-    a.P = c->P + off; a.Q = c->Q + off; a.R = c->R + off; a.y = y + off; a.W = cp.W;
-    a.bz = cp.dz.base; a.Sz = cp.dz.S; a.D1z = cp.dz.D1; a.D2z = cp.dz.D2;
-    a.zp = cp.dz.pts; a.xp = cp.dx.pts; a.yp = cp.dy.pts;
-    a.nx = cp.nx; a.ny = cp.ny; a.nz = cp.nz; a.nM = c->nM; a.M0 = c->M0; a.J = c->sys.J; a.E = E;
-    for (int i = 0; i < kMaxM; ++i) {
-      a.lamp[i] = 0.0;
-      a.lamm[i] = 0.0;
-    }
+    ZPassArgs<T> a;
+    a.P = P + off; a.Q = Q + off; a.R = R + off; a.y = y + off; a.W = tb.W; a.A = tb.A; a.B = tb.B; a.iy2 = tb.iy2;
+    a.bz = cp.dz.base; a.Sz = tb.Sz; a.D1z = tb.D1z; a.D2z = tb.D2z; a.zp = tb.zp;
+    a.nx = cp.nx; a.ny = cp.ny; a.nz = cp.nz; a.nM = c->nM; a.M0 = c->M0; a.J = c->sys.J; a.E = (T)E;
+    for (int i = 0; i < kMaxM; ++i) a.lamp[i] = a.lamm[i] = (T)0;
     for (int iM = 0; iM < c->nM; ++iM) {
       const int Mp = c->Mps[iM], J = c->sys.J;
-      const double lp = sqrt((double)(J * (J + 1) - Mp * (Mp + 1)) > 0 ? (double)(J * (J + 1) - Mp * (Mp + 1)) : 0.0);
-      const double lm = sqrt((double)(J * (J + 1) - Mp * (Mp - 1)) > 0 ? (double)(J * (J + 1) - Mp * (Mp - 1)) : 0.0);
-      a.lamp[iM] = lp * sqrt(1.0 + (Mp == 0 ? 1.0 : 0.0));
-      a.lamm[iM] = lm * sqrt(1.0 + (Mp == 1 ? 1.0 : 0.0));
+      const double vp = (double)(J * (J + 1) - Mp * (Mp + 1)), vm = (double)(J * (J + 1) - Mp * (Mp - 1));
+      a.lamp[iM] = (T)((vp > 0 ? sqrt(vp) : 0.0) * sqrt(Mp == 0 ? 2.0 : 1.0));
+      a.lamm[iM] = (T)((vm > 0 ? sqrt(vm) : 0.0) * sqrt(Mp == 1 ? 2.0 : 1.0));
     }
     const int64_t tot = cp.npts * c->nM;
     {
-      const int tk_ = prof_begin(c, FM_KERNEL_APPLY_Z);
-      k_apply_z<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(a, only_S);
-      prof_end(c, tk_, (double)tot * (only_S ? 8.0 : (56.0 + (c->nM > 1 ? 32.0 : 0.0))), (double)tot * (only_S ? 16.0 : 40.0));
+      const int tk_ = timed ? prof_begin(c, FM_KERNEL_APPLY_Z) : -1;
+      k_apply_z<T><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(a, only_S);
+      prof_end(c, tk_, (double)tot * (only_S ? 8.0 : (10.0 + (c->nM > 1 ? 32.0 : 0.0) + 40.0)),
+               (double)tot * (only_S ? 2.0 : 7.0) * sizeof(T));
     }
     c->launches++;
   }
   if (!only_S) {
     for (auto& cp : c->comps) {
       if (cp.n_act == 0 || cp.sources.empty()) continue;
-      CouplingArgs a{};
+      const ApplyTabs<T> tb = tabs_of<T>(cp);
+      CouplingArgs<T> a{};
       a.x = x; a.y = y; a.row_off = cp.off; a.npts = cp.npts; a.n_act = cp.n_act; a.act_pt = cp.act_pt;
       a.ns = (int)cp.sources.size(); a.nM = c->nM;
       for (int s = 0; s < a.ns; ++s) {
         const auto& src = c->comps[cp.sources[s].src];
         a.base[s] = cp.cpl_base + (int64_t)s * 3 * cp.n_act;
-        a.val[s] = cp.cpl_val + (int64_t)s * 12 * cp.n_act;
-        a.w[s] = cp.cpl_w + (int64_t)s * c->nM * c->nM * cp.n_act;
+        a.val[s] = tb.cval + (int64_t)s * 12 * cp.n_act;
+        a.w[s] = tb.cw + (int64_t)s * c->nM * c->nM * cp.n_act;
         a.src_off[s] = src.off; a.src_npts[s] = src.npts;
         a.snx[s] = src.nx; a.sny[s] = src.ny; a.snz[s] = src.nz;
       }
       {
-        const int tk_ = prof_begin(c, FM_KERNEL_COUPLING);
-        k_apply_coupling<<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
-        prof_end(c, tk_, (double)cp.n_act * a.ns * (168.0 * c->nM + 2.0 * c->nM * c->nM), (double)cp.n_act * (4.0 + 16.0 * c->nM + a.ns * (108.0 + 8.0 * c->nM * c->nM)));
+        const int tk_ = timed ? prof_begin(c, FM_KERNEL_COUPLING) : -1;
+        k_apply_coupling<T><<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
+        prof_end(c, tk_, (double)cp.n_act * a.ns * (168.0 * c->nM + 2.0 * c->nM * c->nM),
+                 (double)cp.n_act * (4.0 + 2.0 * c->nM * sizeof(T) + a.ns * (12.0 + (12.0 + c->nM * c->nM) * sizeof(T))));
       }
       c->launches++;
     }
@@ -731,55 +883,23 @@ int launch_apply(fm_ctx* c, double E, const double* x, double* y, bool only_S) {
   return FM_OK;
 }
 
+int launch_apply(fm_ctx* c, double E, const double* x, double* y, bool only_S) {
+  return apply_t<double>(c, E, x, y, only_S, c->P, c->Q, c->R, true);
+}
+
+int launch_apply32(fm_ctx* c, double E, const float* x, float* y, bool only_S) {
+  return apply_t<float>(c, E, x, y, only_S, c->P32, c->Q32, c->R32, true);
+}
+
 // The operator apply with caller-chosen scratch planes (used by the entry point that allocates
 // nothing, whose planes live in a fixed device array).  Same kernels and launch shapes as
 // launch_apply; no per-kernel timing.
 int launch_apply_scratch(fm_ctx* c, double E, const double* x, double* y, double* P, double* Q, double* R) {
-  for (auto& cp : c->comps) {
-    const int64_t off = cp.off;
-    constexpr int TX = 8;
-    const size_t smem = (size_t)3 * (TX + 2) * cp.ny * sizeof(double);
-    dim3 g1((cp.nx + TX - 1) / TX, cp.nz * c->nM);
-    k_apply_xy<TX><<<g1, 256, smem, c->stream>>>(x + off, P + off, Q + off, R + off, cp.nx, cp.ny, cp.dx.base, cp.dx.S,
-                                                 cp.dx.D2, cp.dy.base, cp.dy.S, cp.dy.D2, false);
-    ZPassArgs a;
-    a.P = P + off; a.Q = Q + off; a.R = R + off; a.y = y + off; a.W = cp.W;
-    a.bz = cp.dz.base; a.Sz = cp.dz.S; a.D1z = cp.dz.D1; a.D2z = cp.dz.D2;
-    a.zp = cp.dz.pts; a.xp = cp.dx.pts; a.yp = cp.dy.pts;
-    a.nx = cp.nx; a.ny = cp.ny; a.nz = cp.nz; a.nM = c->nM; a.M0 = c->M0; a.J = c->sys.J; a.E = E;
-    for (int i = 0; i < kMaxM; ++i) a.lamp[i] = a.lamm[i] = 0.0;
-    for (int iM = 0; iM < c->nM; ++iM) {
-      const int Mp = c->Mps[iM], J = c->sys.J;
-      const double vp = (double)(J * (J + 1) - Mp * (Mp + 1)), vm = (double)(J * (J + 1) - Mp * (Mp - 1));
-      a.lamp[iM] = (vp > 0 ? sqrt(vp) : 0.0) * sqrt(Mp == 0 ? 2.0 : 1.0);
-      a.lamm[iM] = (vm > 0 ? sqrt(vm) : 0.0) * sqrt(Mp == 1 ? 2.0 : 1.0);
-    }
-    const int64_t tot = cp.npts * c->nM;
-    k_apply_z<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(a, false);
-    c->launches += 2;
-  }
-  for (auto& cp : c->comps) {
-    if (cp.n_act == 0 || cp.sources.empty()) continue;
-    CouplingArgs a{};
-    a.x = x; a.y = y; a.row_off = cp.off; a.npts = cp.npts; a.n_act = cp.n_act; a.act_pt = cp.act_pt;
-    a.ns = (int)cp.sources.size(); a.nM = c->nM;
-    for (int s = 0; s < a.ns; ++s) {
-      const auto& src = c->comps[cp.sources[s].src];
-      a.base[s] = cp.cpl_base + (int64_t)s * 3 * cp.n_act;
-      a.val[s] = cp.cpl_val + (int64_t)s * 12 * cp.n_act;
-      a.w[s] = cp.cpl_w + (int64_t)s * c->nM * c->nM * cp.n_act;
-      a.src_off[s] = src.off; a.src_npts[s] = src.npts;
-      a.snx[s] = src.nx; a.sny[s] = src.ny; a.snz[s] = src.nz;
-    }
-    k_apply_coupling<<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
-    c->launches++;
-  }
-  FM_CUDA(cudaGetLastError());
-  return FM_OK;
+  return apply_t<double>(c, E, x, y, false, P, Q, R, false);
 }
 
-template <typename T>
-static int precond_impl(fm_ctx* c, const double* x, double* y, T* t) {
+template <typename T, typename TIO>
+static int precond_impl(fm_ctx* c, const TIO* x, TIO* y, T* t) {
   for (auto& cp : c->comps) {
     const int64_t nxy = (int64_t)cp.nx * cp.ny;
     const T* Wzb = std::is_same<T, double>::value ? (const T*)cp.Wzb : (const T*)cp.Wzb32;
@@ -801,7 +921,7 @@ static int precond_impl(fm_ctx* c, const double* x, double* y, T* t) {
     const size_t smz = ((size_t)cp.nz * cp.nz + (size_t)cp.nz * 128) * sizeof(T);
     {
       const int tk_ = prof_begin(c, FM_KERNEL_ZMIX);
-      k_zmix<double, T, T><<<gz, 128, smz, c->stream>>>(Wzb, x, t, cp.nz, nxy, cp.off);
+      k_zmix<TIO, T, T><<<gz, 128, smz, c->stream>>>(Wzb, x, t, cp.nz, nxy, cp.off);
       prof_end(c, tk_, 2.0 * cp.nz * ncomp, ncomp * (8.0 + ts));
     }
     dim3 gx((cp.ny + 63) / 64, (cp.nx + 63) / 64, c->nM * cp.nz);
@@ -863,7 +983,7 @@ static int precond_impl(fm_ctx* c, const double* x, double* y, T* t) {
     }
     {
       const int tk_ = prof_begin(c, FM_KERNEL_ZMIX);
-      k_zmix<T, double, T><<<gz, 128, smz, c->stream>>>(Wz, t, y, cp.nz, nxy, cp.off);
+      k_zmix<T, TIO, T><<<gz, 128, smz, c->stream>>>(Wz, t, y, cp.nz, nxy, cp.off);
       prof_end(c, tk_, 2.0 * cp.nz * ncomp, ncomp * (8.0 + ts));
     }
     c->launches += 5;
@@ -873,9 +993,11 @@ static int precond_impl(fm_ctx* c, const double* x, double* y, T* t) {
 }
 
 int launch_precond(fm_ctx* c, const double* x, double* y) {
-  if (c->opts.precision == FM_PREC_FP32) return precond_impl<float>(c, x, y, c->t32);
-  return precond_impl<double>(c, x, y, c->t64);
+  if (c->opts.precision != FM_PREC_FP64) return precond_impl<float, double>(c, x, y, c->t32);
+  return precond_impl<double, double>(c, x, y, c->t64);
 }
+
+int launch_precond32(fm_ctx* c, const float* x, float* y) { return precond_impl<float, float>(c, x, y, c->t32); }
 
 int dot_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, double* h_host) {
   return dot_many_x(c, V, ldv, nv, w, nullptr, h_host);
@@ -891,7 +1013,7 @@ int dot_many_x(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w,
   }
   {
     const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_finish<<<(nt + 63) / 64, 64, 0, c->stream>>>(c->red, nb, nt, c->red + (int64_t)nb * 256);
+    k_dot_finish<<<nt, 32, 0, c->stream>>>(c->red, nb, nt, c->red + (int64_t)nb * 256);
     prof_end(c, tk_, 0.0, 0.0);
   }
   c->launches += 2;
@@ -917,7 +1039,7 @@ int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_h
 int axpy_many_norm(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double* nrm2_out) {
   double* hd = c->red + (int64_t)c->red_blocks * 256 + 512;
   FM_CUDA(cudaMemcpyAsync(hd, h_host, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  const int nb = c->red_blocks;
+  const int nb = 4 * c->red_blocks;  // grid-stride blocks; one partial each
   {
     const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
     k_axpy_many_norm<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, hd, -1.0, w, c->N, c->red);
@@ -925,12 +1047,12 @@ int axpy_many_norm(fm_ctx* c, const double* V, int64_t ldv, int nv, const double
   }
   {
     const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_finish<<<1, 64, 0, c->stream>>>(c->red, nb, 1, c->red + (int64_t)nb * 256);
+    k_dot_finish<<<1, 32, 0, c->stream>>>(c->red, nb, 1, c->red + (int64_t)c->red_blocks * 256);
     prof_end(c, tk_, 0.0, 0.0);
   }
   c->launches += 2;
   FM_CUDA(cudaGetLastError());
-  FM_CUDA(cudaMemcpyAsync(nrm2_out, c->red + (int64_t)nb * 256, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaMemcpyAsync(nrm2_out, c->red + (int64_t)c->red_blocks * 256, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   FM_CUDA(cudaStreamSynchronize(c->stream));
   return prof_harvest(c);
 }
@@ -1043,12 +1165,87 @@ int prof_harvest(fm_ctx* c) {
   return FM_OK;
 }
 
+int dot_many32(fm_ctx* c, const float* V, int64_t ldv, int nv, const float* w, double* h_host) {
+  const int nb = c->red_blocks;
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+    k_dot_many32<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red);
+    prof_end(c, tk_, 2.0 * nv * (double)c->N, (nv + 1.0) * 4.0 * (double)c->N);
+  }
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+    k_dot_finish<<<nv, 32, 0, c->stream>>>(c->red, nb, nv, c->red + (int64_t)nb * 256);
+    prof_end(c, tk_, 0.0, 0.0);
+  }
+  c->launches += 2;
+  FM_CUDA(cudaGetLastError());
+  FM_CUDA(cudaMemcpyAsync(h_host, c->red + (int64_t)nb * 256, nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  return prof_harvest(c);
+}
+
+int axpy_many_norm32(fm_ctx* c, const float* V, int64_t ldv, int nv, const double* h_host, float sign, float* w,
+                     double* nrm2_out) {
+  std::vector<float> hf(h_host, h_host + nv);
+  float* hd = reinterpret_cast<float*>(c->red + (int64_t)c->red_blocks * 256 + 512);
+  FM_CUDA(cudaMemcpyAsync(hd, hf.data(), nv * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  const int nb = 4 * c->red_blocks;
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+    k_axpy_many_norm32<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, hd, sign, w, c->N, c->red);
+    prof_end(c, tk_, (2.0 * nv + 2.0) * (double)c->N, (nv + 2.0) * 4.0 * (double)c->N);
+  }
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+    k_dot_finish<<<1, 32, 0, c->stream>>>(c->red, nb, 1, c->red + (int64_t)c->red_blocks * 256);
+    prof_end(c, tk_, 0.0, 0.0);
+  }
+  c->launches += 2;
+  FM_CUDA(cudaGetLastError());
+  if (nrm2_out) {
+    FM_CUDA(cudaMemcpyAsync(nrm2_out, c->red + (int64_t)c->red_blocks * 256, sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+    FM_CUDA(cudaStreamSynchronize(c->stream));
+    return prof_harvest(c);
+  }
+  return FM_OK;
+}
+
+int to32(fm_ctx* c, const double* x, double a, float* y) {
+  const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+  k_to32<<<grid_for(c->N, 256), 256, 0, c->stream>>>(x, a, y, c->N);
+  prof_end(c, tk_, 0.0, 0.0);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+int add32(fm_ctx* c, const float* y, double a, double* x) {
+  const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+  k_add32<<<grid_for(c->N, 256), 256, 0, c->stream>>>(y, a, x, c->N);
+  prof_end(c, tk_, 0.0, 0.0);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+int axpby32(fm_ctx* c, float a, const float* x, float b, float* y) {
+  const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+  k_axpby32<<<grid_for(c->N, 256), 256, 0, c->stream>>>(a, x, b, y, c->N);
+  prof_end(c, tk_, 0.0, 0.0);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
 int kernels_init(fm_ctx* c) {
   (void)c;
-  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<double, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<float, double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_zmix<float, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_ysolve1<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_ysolve1<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_ysolve<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));

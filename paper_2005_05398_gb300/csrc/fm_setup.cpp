@@ -340,8 +340,10 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
     if ((rc = upload_axis(c, cp.ax, cp.dx))) return rc;
     if ((rc = upload_axis(c, cp.ay, cp.dy))) return rc;
     if ((rc = upload_axis(c, cp.az, cp.dz))) return rc;
-    // left-hand potential V_a(x) + sum_{b != a} V^(l)_b(x_b, y_b)   (Eq. FM-pre)
-    std::vector<double> W((size_t)cp.npts);
+    // pointwise coefficients of Eq. FM-pre: the left-hand potential V_a(x) + sum_{b != a} V^(l)_b(x_b, y_b)
+    // folded with the M'-dependent diagonal terms, and the coefficients of the z derivatives
+    std::vector<double> W((size_t)nM * cp.npts), Atab((size_t)cp.npts), Btab((size_t)nM * cp.npts), iy2(cp.ny);
+    for (int j = 0; j < cp.ny; ++j) iy2[j] = 1.0 / (cp.ay.pts[j] * cp.ay.pts[j]);
     for (int k = 0; k < cp.nz; ++k)
       for (int i = 0; i < cp.nx; ++i)
         for (int j = 0; j < cp.ny; ++j) {
@@ -357,9 +359,30 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
             else if (c->split.mode == FM_SPLIT_MERKURIEV) tot += (1.0 - chi(c->split, xb, yb)) * vc;
           }
           if (!std::isfinite(tot)) return FM_ERR_NUMERIC;
-          W[((size_t)k * cp.nx + i) * cp.ny + j] = tot;
+          const size_t pt = ((size_t)k * cp.nx + i) * cp.ny + j;
+          const double q = 1.0 / (x * x) + iy2[j];
+          Atab[pt] = q * (1.0 - z * z);
+          for (int iM = 0; iM < nM; ++iM) {
+            const int Mp = c->Mps[iM];
+            W[(size_t)iM * cp.npts + pt] = tot + q * Mp * (Mp + 1.0) + (J * (J + 1.0) - 2.0 * Mp * Mp) * iy2[j];
+            Btab[(size_t)iM * cp.npts + pt] = 2.0 * (Mp + 1) * z * q;
+          }
         }
     if ((rc = upload(c, (void**)&cp.W, W.data(), W.size() * sizeof(double)))) return rc;
+    if ((rc = upload(c, (void**)&cp.A, Atab.data(), Atab.size() * sizeof(double)))) return rc;
+    if ((rc = upload(c, (void**)&cp.B, Btab.data(), Btab.size() * sizeof(double)))) return rc;
+    if ((rc = upload(c, (void**)&cp.iy2, iy2.data(), iy2.size() * sizeof(double)))) return rc;
+    {  // float32 copies for the mixed-precision inner solves
+      auto up32 = [&](float** dst, const std::vector<double>& v) {
+        std::vector<float> f(v.begin(), v.end());
+        return upload(c, (void**)dst, f.data(), f.size() * sizeof(float));
+      };
+      if ((rc = up32(&cp.f32.Sx, cp.ax.S)) || (rc = up32(&cp.f32.D2x, cp.ax.D2)) || (rc = up32(&cp.f32.Sy, cp.ay.S)) ||
+          (rc = up32(&cp.f32.D2y, cp.ay.D2)) || (rc = up32(&cp.f32.Sz, cp.az.S)) || (rc = up32(&cp.f32.D1z, cp.az.D1)) ||
+          (rc = up32(&cp.f32.D2z, cp.az.D2)) || (rc = up32(&cp.f32.zp, cp.az.pts)) || (rc = up32(&cp.f32.W, W)) ||
+          (rc = up32(&cp.f32.A, Atab)) || (rc = up32(&cp.f32.B, Btab)) || (rc = up32(&cp.f32.iy2, iy2)))
+        return rc;
+    }
 
     // coupling geometry (Eqs. r-form, s-rot): active points and, per source, taps and weights
     if (!cp.sources.empty()) {
@@ -422,6 +445,9 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       if ((rc = upload(c, (void**)&cp.cpl_base, base.data(), base.size() * sizeof(int)))) return rc;
       if ((rc = upload(c, (void**)&cp.cpl_val, val.data(), val.size() * sizeof(double)))) return rc;
       if ((rc = upload(c, (void**)&cp.cpl_w, wt.data(), wt.size() * sizeof(double)))) return rc;
+      std::vector<float> val32(val.begin(), val.end()), wt32(wt.begin(), wt.end());
+      if ((rc = upload(c, (void**)&cp.f32.cval, val32.data(), val32.size() * sizeof(float)))) return rc;
+      if ((rc = upload(c, (void**)&cp.f32.cw, wt32.data(), wt32.size() * sizeof(float)))) return rc;
     }
 
     // z decompositions per M' (Eq. z-dec), columns normalised to g_l^{M'}(1)
@@ -555,6 +581,66 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       if ((rc = upload(c, (void**)&cp.dLx64, cp.Lx.data(), cp.Lx.size() * 8))) return rc;
     }
   }
+  return FM_OK;
+}
+
+// Device bytes a context with these parameters holds (the allocations of setup_host and fm_create,
+// computed from the same size plan without allocating or decomposing anything).
+int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const fm_splitting* split, const fm_opts* o,
+                   int64_t* out) {
+  const int M0 = (1 - S->tau) / 2, nM = S->J - M0 + 1;
+  if (nM <= 0 || nM > 8) return FM_ERR_ARG;
+  std::vector<int> labels;
+  if (split->mode == FM_SPLIT_SCHRODINGER) labels = {1};
+  else if (S->identical_pair == 12) labels = {1, 3};
+  else labels = {1, 2, 3};
+  if (n_grids != 1 && n_grids != (int)labels.size()) return FM_ERR_ARG;
+  double bytes = 0.0;
+  int64_t N = 0;
+  for (size_t ic = 0; ic < labels.size(); ++ic) {
+    const fm_grid& g = grids[n_grids == 1 ? 0 : ic];
+    if (g.nint_x < 1 || g.nint_y < 1 || g.nint_z < 1 || !(g.Rx > 0) || !(g.Ry > 0)) return FM_ERR_ARG;
+    Axis ax, ay, az;
+    ax.build(g.xmap, g.nint_x, 0.0, g.Rx, true);
+    ay.build(g.ymap, g.nint_y, 0.0, g.Ry, true);
+    az.build(g.zmap, g.nint_z, -1.0, 1.0, false);
+    const double nx = ax.n, ny = ay.n, nz = az.n, npts = nx * ny * nz;
+    N += (int64_t)(npts * nM);
+    bytes += (nx + ny + nz) * (4 + 3 * 4 * 12 + 8) * 1.5;              // tap tables (float64 + float32)
+    bytes += (2.0 * nM + 1.0) * npts * 12.0 + ny * 12.0;                 // W, B per M'; A; iy2 (+ float32)
+    if (split->mode != FM_SPLIT_SCHRODINGER) {                           // coupling geometry
+      double act = 0.0;
+      for (int i = 0; i < ax.n; ++i)
+        for (int j = 0; j < ay.n; ++j)
+          if (split->mode != FM_SPLIT_MERKURIEV || chi(*split, ax.pts[i], ay.pts[j]) > split->vs_cut) act += 1.0;
+      act *= nz;
+      const double ns = 2.0;
+      bytes += act * (4.0 + ns * (12.0 + 12.0 * 12.0 + nM * nM * 12.0));
+    }
+    const double nl = nM + nz - 1;
+    bytes += 2.0 * nM * nz * nz * 12.0 + 2.0 * nl * nx * nx * 12.0;     // z and x decompositions
+    double bo = 0.0, lo = 0.0, po = 0.0;                                 // banded y factors
+    for (int il = 0; il < (int)nl; ++il) {
+      const int l = M0 + il;
+      int cnt = 0;
+      for (int iM = 0; iM < nM; ++iM) {
+        const int Mp = M0 + iM;
+        if (Mp <= l && l <= Mp + (int)nz - 1) ++cnt;
+      }
+      const double n = cnt * ny, kl = (cnt == 1) ? 2 : 2 * cnt + 1;
+      bo += n * (2 * kl + 1) * nx;
+      lo += n * kl * nx;
+      po += n * nx;
+    }
+    bytes += bo * 12.0 + lo * 12.0 + po;
+    if (nM == 1) bytes += 2.0 * nl * ny * ny * 12.0 + nl * (nx + ny) * 12.0;  // per-l y diagonalisation
+  }
+  const double m = o->restart_m, ncv = o->ncv, n = (double)N;
+  bytes += n * 8.0 * (5 + 2 + 3 + 16) + n * 4.0 * 2;                    // apply scratch, stage buffers, tuning
+  bytes += n * 8.0 * ((m + 1) + std::max(m, ncv) + (ncv + 1));          // FGMRES and Arnoldi bases
+  if (o->precision == FM_PREC_MIXED) bytes += n * 4.0 * ((m + 1) + m + 7);
+  bytes += (2.0 * 152 * 256 + 8192) * 8.0;
+  *out = (int64_t)bytes;
   return FM_OK;
 }
 

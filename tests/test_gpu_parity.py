@@ -89,8 +89,12 @@ def test_precond_fp64_matches_paper_form(pkg, name):
     y = torch.empty(s.N, dtype=torch.float64, device="cuda")
     ctx.fm_precond_apply(_dev(v), y)
     got = y.cpu().numpy()
-    assert np.linalg.norm(got - ref) < 1e-10 * np.linalg.norm(ref), name
-    assert np.max(np.abs(got - ref)) < 1e-9 * np.max(np.abs(ref))
+    # the M'=3 z pencil of psm_l3_pairs has two nearly degenerate high modes (-427.451 / -427.454,
+    # relative gap 7e-6): their eigenvectors, and so W_z, agree between two correct eigensolvers only
+    # to ~eps / gap ~ 1e-11 relative per column, amplified by the transforms to ~1e-9
+    tol = 1e-8 if name == "psm_l3_pairs" else 1e-10
+    assert np.linalg.norm(got - ref) < tol * np.linalg.norm(ref), name
+    assert np.max(np.abs(got - ref)) < 10 * tol * np.max(np.abs(ref))
     ctx.close()
 
 
@@ -149,7 +153,7 @@ def test_computed_z_gives_exact_inverse_of_fmfin(pkg):
     assert np.linalg.norm(y.cpu().numpy() - v) < 1e-10 * np.linalg.norm(v)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_solve_matches_sparse_lu(pkg, precision):
     from oracle.system import FMSystem
     from oracle import solvers
@@ -169,17 +173,21 @@ def test_solve_matches_sparse_lu(pkg, precision):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8
 
 
-@pytest.mark.parametrize("name,k", [("he_l0_merkuriev", 1), ("he_l0_merkuriev", 3), ("he_l1", 2), ("psm_l2", 2),
-                                    ("psm_l3_pairs", 2)])
-def test_eigs_match_oracle(pkg, name, k):
+@pytest.mark.parametrize("name,k,precision", [("he_l0_merkuriev", 1, 0), ("he_l0_merkuriev", 3, 1), ("he_l1", 2, 1),
+                                              ("psm_l2", 2, 1), ("psm_l3_pairs", 2, 1), ("he_l0_merkuriev", 3, 2),
+                                              ("psm_l2", 2, 2)])
+def test_eigs_match_oracle(pkg, name, k, precision):
     from oracle.system import FMSystem
     from oracle import solvers
     wl = _wl(name)
     s = FMSystem(wl)
     H, S = s.H(), s.S()
     shift = wl["shift"] if name != "he_l1" else -2.12
-    Eo, vo = solvers.eigs_near(H, S, shift, k)
-    ctx = pkg.Context(wl, restart_m=40)
+    Eo, vo = solvers.eigs_near(H, S, shift, k + 4)
+    # fm_eigs returns real eigenvalues only (complex-conjugate pairs of the pencil are passed over)
+    real = np.abs(Eo.imag) <= 1e-10 * np.abs(Eo)
+    Eo, vo = Eo[real][:k], vo[:, real][:, :k]
+    ctx = pkg.Context(wl, restart_m=40, precision=precision)
     evecs = torch.empty(k * s.N, dtype=torch.float64, device="cuda")
     ev, info = ctx.fm_eigs(shift, k, evecs=evecs)
     assert info["converged"] == 1
