@@ -44,7 +44,8 @@ typedef enum {
   FM_ERR_COMPLEX_SPECTRUM = -6, /* a 1D generalized eigenproblem has complex eigenvalues */
   FM_ERR_NO_SHIFT = -7,         /* preconditioner used before fm_set_shift */
   FM_ERR_NUMERIC = -8,          /* singular 1D or banded factor, non-finite setup value */
-  FM_ERR_SCRATCH_LIMIT = -9     /* problem larger than the fixed scratch of fm_apply_noalloc */
+  FM_ERR_SCRATCH_LIMIT = -9,    /* problem larger than the fixed scratch of fm_apply_noalloc */
+  FM_ERR_TIMEOUT = -10          /* a bounded wait inside a device kernel expired (results invalid) */
 } fm_status;
 
 /* Three particles (Section 2.1).  Masses in electron masses ("infinite" core: 1e15,
@@ -93,6 +94,12 @@ typedef struct {
  * solved to a relative 3e-5; the result meets the same float64 tolerance. */
 enum { FM_PREC_FP64 = 0, FM_PREC_FP32 = 1, FM_PREC_MIXED = 2 };
 
+/* Mode products of the float32 preconditioner (FP32 and MIXED precision).  AUTO: the x and y
+ * stages run as TF32 tensor-core GEMMs (float32 accumulation) on every component whose n_x and
+ * n_y are multiples of 4 in [16, 256], on float32 CUDA cores otherwise.  SIMT: float32 CUDA cores
+ * always.  TF32: tensor cores, FM_ERR_ARG from fm_create when a component is not eligible. */
+enum { FM_MMA_AUTO = 0, FM_MMA_SIMT = 1, FM_MMA_TF32 = 2 };
+
 typedef struct {
   double tol;        /* relative residual of fm_solve (FGMRES true residual), e.g. 1e-12 */
   int restart_m;     /* FGMRES restart length (1..128) */
@@ -110,6 +117,7 @@ typedef struct {
                         diagonalisation of (A_l, S_y) when n_M = 1 (both invert the same matrix) */
   int tune;          /* fm_eigs: 1 = tune the preconditioner to the current Ritz vectors U (rank-k update
                         P + (A U - P U) U^T, Freitag & Spence), 0 = plain preconditioner */
+  int mma;           /* FM_MMA_AUTO, FM_MMA_SIMT or FM_MMA_TF32 */
   int device;        /* CUDA device ordinal */
   void* stream;      /* cudaStream_t, NULL = legacy default stream */
 } fm_opts;

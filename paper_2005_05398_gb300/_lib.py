@@ -34,7 +34,7 @@ class fm_splitting(ctypes.Structure):
 class fm_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("restart_m", c_int), ("max_iters", c_int), ("precision", c_int),
                 ("ncv", c_int), ("max_restarts", c_int), ("eig_tol", c_double), ("z_eigs", c_int),
-                ("y_solver", c_int), ("tune", c_int), ("device", c_int), ("stream", c_void_p)]
+                ("y_solver", c_int), ("tune", c_int), ("mma", c_int), ("device", c_int), ("stream", c_void_p)]
 
 
 class fm_info(ctypes.Structure):
@@ -45,7 +45,8 @@ class fm_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-FM_OK, FM_ERR_NOT_CONVERGED, FM_ERR_SCRATCH_LIMIT = 0, -4, -9
+FM_OK, FM_ERR_NOT_CONVERGED, FM_ERR_SCRATCH_LIMIT, FM_ERR_TIMEOUT = 0, -4, -9, -10
+FM_MMA_AUTO, FM_MMA_SIMT, FM_MMA_TF32 = 0, 1, 2
 KERNEL_CLASSES = ["apply_xy", "apply_z", "coupling", "zmix", "xmix", "ysolve", "dot", "axpy", "other"]
 
 _LIB = None

@@ -371,6 +371,7 @@ void fm_default_opts(fm_opts* o) {
   o->z_eigs = 0;
   o->tune = 1;
   o->y_solver = 0;
+  o->mma = FM_MMA_AUTO;
   o->device = 0;
   o->stream = nullptr;
 }
@@ -387,6 +388,7 @@ const char* fm_strerror(int s) {
     case FM_ERR_NO_SHIFT: return "preconditioner used before fm_set_shift";
     case FM_ERR_NUMERIC: return "singular or non-finite set-up quantity";
     case FM_ERR_SCRATCH_LIMIT: return "problem larger than the fixed scratch of fm_apply_noalloc (FM_NOALLOC_MAX_UNKNOWNS)";
+    case FM_ERR_TIMEOUT: return "a bounded wait inside a device kernel expired";
     default: return "unknown status";
   }
 }
@@ -426,7 +428,7 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
   if (o.z_eigs == 1 && nM != 1) return FM_ERR_ARG;
   if (o.restart_m < 1 || o.restart_m > 256 || o.max_iters < 1 || !(o.tol > 0) || o.ncv < 3 || o.ncv > 64 ||
       o.max_restarts < 0 || !(o.eig_tol > 0) || o.precision < 0 || o.precision > 2 || o.y_solver < 0 ||
-      o.y_solver > 2)
+      o.y_solver > 2 || o.mma < 0 || o.mma > 2)
     return FM_ERR_ARG;
   fm_ctx* c = new fm_ctx();
   c->sys = *sys;
@@ -469,6 +471,7 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
         (rc = dev_alloc(c, (void**)&c->R32, N * 4)))
       return fail(rc);
   }
+  if ((rc = tc_setup(c))) return fail(rc);
   c->m_alloc = m;
   c->ncv_alloc = o.ncv;
   *out = c;
@@ -574,7 +577,8 @@ int fm_precond_apply(fm_ctx* c, const double* x, double* y) {
   if (!c || !x || !y || x == y) return FM_ERR_ARG;
   if (!c->have_shift) return FM_ERR_NO_SHIFT;
   FM_CUDA(cudaSetDevice(c->device));
-  return launch_precond(c, x, y);
+  int rc = launch_precond(c, x, y);
+  return rc ? rc : tc_check(c);
 }
 
 int fm_solve(fm_ctx* c, double E, const double* rhs, double* x, fm_info* info) {
@@ -588,6 +592,10 @@ int fm_solve(fm_ctx* c, double E, const double* rhs, double* x, fm_info* info) {
   double res = 0.0;
   rc = solve_any(c, E, rhs, x, c->opts.tol, c->opts.max_iters, &it, &rs, &res);
   FM_CUDA(cudaStreamSynchronize(c->stream));
+  if (rc == FM_OK || rc == FM_ERR_NOT_CONVERGED) {
+    const int tc = tc_check(c);
+    if (tc) rc = tc;
+  }
   if (info) {
     std::memset(info, 0, sizeof(*info));
     info->iters = it;
@@ -602,8 +610,14 @@ int fm_solve(fm_ctx* c, double E, const double* rhs, double* x, fm_info* info) {
 static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* evals, double* evecs, fm_info* info);
 
 int fm_eigs(fm_ctx* c, double shift, int k, const double* v0, double* evals, double* evecs, fm_info* info) {
-  const int rc = eigs_impl(c, shift, k, v0, evals, evecs, info);
-  if (c) c->n_tune = 0;
+  int rc = eigs_impl(c, shift, k, v0, evals, evecs, info);
+  if (c) {
+    c->n_tune = 0;
+    if (rc == FM_OK || rc == FM_ERR_NOT_CONVERGED) {
+      const int tc = tc_check(c);
+      if (tc) rc = tc;
+    }
+  }
   return rc;
 }
 

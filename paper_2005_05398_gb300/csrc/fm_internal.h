@@ -1,5 +1,6 @@
 // Internal structures of libfm (not part of the C ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -96,6 +97,11 @@ struct Comp {
   float* dLy32 = nullptr;                          // [nl][ny]
   float* dLx32 = nullptr;                          // [nl][nx]
   double* Wy64 = nullptr; double* Wyb64 = nullptr; double* dLy64 = nullptr; double* dLx64 = nullptr;
+  float2* dLx2 = nullptr;                          // [nl][nx] lambda_x as (hi, lo) float pairs
+  float2* dLy2 = nullptr;                          // [nl][ny] lambda_y as (hi, lo) float pairs
+  // tensor-core chain: TMA maps of the stage buffers and of the float32 W matrices
+  // 0 t[slab][j][i], 1 u[slab][j][i], 2 W-bar_x, 3 W_x, 4 u[slab][i][j], 5 t[slab][i][j], 6 W-bar_y, 7 W_y
+  CUtensorMap tm[8];
 };
 
 }  // namespace fmi
@@ -151,6 +157,8 @@ struct fm_ctx {
   double* tuneU = nullptr;       // [8][N]
   double* tuneWU = nullptr;      // [8][N]  W - U
   std::vector<double> tuneGinv;  // (U^T W)^{-1}, n_tune x n_tune, row-major
+  bool tc_active = false;        // float32 preconditioner x / y stages on the tensor cores
+  int* tc_err = nullptr;         // device flag: a bounded wait of a tensor-core kernel expired
   int64_t launches = 0;
   int64_t device_bytes = 0;
   // per-kernel timing (fm_profile)
@@ -199,6 +207,13 @@ int launch_apply_scratch(fm_ctx* c, double E, const double* x, double* y, double
 int prof_begin(fm_ctx* c, int cls);
 void prof_end(fm_ctx* c, int token, double flops, double bytes);
 int prof_harvest(fm_ctx* c);   // after a stream synchronisation: fold finished records
+// tensor-core preconditioner stages (fm_tc.cu)
+bool tc_component_ok(const Comp& cp);
+int tc_setup(fm_ctx* c);       // after the stage buffers exist: encode the TMA maps
+int tc_kernels_init();
+int tc_check(fm_ctx* c);       // FM_ERR_TIMEOUT when a tensor-core kernel gave up a wait
+template <typename TIO>
+int precond_tc(fm_ctx* c, Comp& cp, const TIO* x, TIO* y, bool ydiag, int (*ysolve)(fm_ctx*, Comp&));
 }  // namespace fmi
 
 #define FM_CUDA(call)                                   \

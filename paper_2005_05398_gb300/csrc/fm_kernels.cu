@@ -898,25 +898,67 @@ int launch_apply_scratch(fm_ctx* c, double E, const double* x, double* y, double
   return apply_t<double>(c, E, x, y, false, P, Q, R, false);
 }
 
+// Banded y solves of one component (Eq. prec-2 y stage with the M' chain), in place on
+// u[slab][j][i].
+template <typename T>
+static int ysolve_banded(fm_ctx* c, fmi::Comp& cp, T* u) {
+  const T* U = std::is_same<T, double>::value ? (const T*)cp.yU : (const T*)cp.yU32;
+  const T* L = std::is_same<T, double>::value ? (const T*)cp.yL : (const T*)cp.yL32;
+  const double ts = (double)sizeof(T);
+  double yfl = 0.0, yby = 0.0;  // per line 2n(2kl+ku) + n flops; factors + vector bytes
+  for (int il = 0; il < cp.nl; ++il) {
+    const int nc = cp.chain_n[il], n = nc * cp.ny, kl = (nc == 1) ? 2 : 2 * nc + 1;
+    yfl += (double)cp.nx * (2.0 * n * (3.0 * kl) + n);
+    yby += (double)cp.nx * ((double)n * (3.0 * kl + 1.0) * ts + n + 2.0 * n * ts);
+  }
+  YArgs ya;
+  ya.nx = cp.nx; ya.ny = cp.ny; ya.nz = cp.nz; ya.M0 = c->M0; ya.nl = cp.nl; ya.comp_off = cp.off;
+  ya.chain_lo = (const int*)cp.d_chain_lo; ya.chain_n = (const int*)cp.d_chain_n;
+  ya.band_off = cp.d_band_off; ya.lmul_off = cp.d_lmul_off; ya.piv_off = cp.d_piv_off;
+  int maxnc = 1;
+  for (int v : cp.chain_n) maxnc = std::max(maxnc, v);
+  const size_t line_bytes = (size_t)maxnc * cp.ny * sizeof(T);
+  const int tk_ = prof_begin(c, FM_KERNEL_YSOLVE);
+  if (maxnc == 1 && line_bytes * 32 <= 200 * 1024) {
+    dim3 gy((cp.nx + 31) / 32, cp.nl);
+    k_ysolve1<T, 32><<<gy, 32, line_bytes * 32, c->stream>>>(ya, U, L, cp.yP, u);
+  } else if (line_bytes * 64 <= 200 * 1024) {
+    dim3 gy((cp.nx + 63) / 64, cp.nl);
+    k_ysolve<T, 64><<<gy, 64, line_bytes * 64, c->stream>>>(ya, U, L, cp.yP, u);
+  } else if (line_bytes * 32 <= 200 * 1024) {
+    dim3 gy((cp.nx + 31) / 32, cp.nl);
+    k_ysolve<T, 32><<<gy, 32, line_bytes * 32, c->stream>>>(ya, U, L, cp.yP, u);
+  } else {
+    if (line_bytes * 8 > 200 * 1024) return FM_ERR_ARG;  // M' chains too long for one line in shared memory
+    dim3 gy((cp.nx + 7) / 8, cp.nl);
+    k_ysolve<T, 8><<<gy, 8, line_bytes * 8, c->stream>>>(ya, U, L, cp.yP, u);
+  }
+  prof_end(c, tk_, yfl, yby);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+static int ysolve32_cb(fm_ctx* c, fmi::Comp& cp) { return ysolve_banded<float>(c, cp, c->u32); }
+
 template <typename T, typename TIO>
 static int precond_impl(fm_ctx* c, const TIO* x, TIO* y, T* t) {
+  const bool is32 = std::is_same<T, float>::value;
   for (auto& cp : c->comps) {
+    const bool ymda = cp.ydiag_ok && (c->opts.y_solver == 2 || (c->opts.y_solver == 0 && is32));
+    if (is32 && c->tc_active) {  // x and y stages on the tensor cores
+      const int rc = fmi::precond_tc<TIO>(c, cp, x, y, ymda, ysolve32_cb);
+      if (rc) return rc;
+      continue;
+    }
     const int64_t nxy = (int64_t)cp.nx * cp.ny;
     const T* Wzb = std::is_same<T, double>::value ? (const T*)cp.Wzb : (const T*)cp.Wzb32;
     const T* Wz = std::is_same<T, double>::value ? (const T*)cp.Wz : (const T*)cp.Wz32;
     const T* Wxb = std::is_same<T, double>::value ? (const T*)cp.Wxb : (const T*)cp.Wxb32;
     const T* Wx = std::is_same<T, double>::value ? (const T*)cp.Wx : (const T*)cp.Wx32;
-    const T* U = std::is_same<T, double>::value ? (const T*)cp.yU : (const T*)cp.yU32;
-    const T* L = std::is_same<T, double>::value ? (const T*)cp.yL : (const T*)cp.yL32;
     T* u = std::is_same<T, double>::value ? (T*)c->u64 : (T*)c->u32;
     const double ncomp = (double)nxy * cp.nz * c->nM;  // unknowns of this component
     const double ts = (double)sizeof(T);
-    double yfl = 0.0, yby = 0.0;  // banded y solves: per line 2n(2kl+ku) + n flops; factors + vector bytes
-    for (int il = 0; il < cp.nl; ++il) {
-      const int nc = cp.chain_n[il], n = nc * cp.ny, kl = (nc == 1) ? 2 : 2 * nc + 1;
-      yfl += (double)cp.nx * (2.0 * n * (3.0 * kl) + n);
-      yby += (double)cp.nx * ((double)n * (3.0 * kl + 1.0) * ts + n + 2.0 * n * ts);
-    }
     dim3 gz((unsigned)((nxy + 127) / 128), c->nM);
     const size_t smz = ((size_t)cp.nz * cp.nz + (size_t)cp.nz * 128) * sizeof(T);
     {
@@ -930,8 +972,6 @@ static int precond_impl(fm_ctx* c, const TIO* x, TIO* y, T* t) {
       k_mix<T, false, true, false><<<gx, 256, 0, c->stream>>>(Wxb, t, u, cp.nx, cp.ny, cp.nz, cp.off, c->M0, nullptr, nullptr);
       prof_end(c, tk_, 2.0 * cp.nx * ncomp, 2.0 * ncomp * ts);
     }
-    const bool is32 = std::is_same<T, float>::value;
-    const bool ymda = cp.ydiag_ok && (c->opts.y_solver == 2 || (c->opts.y_solver == 0 && is32));
     if (ymda) {
       // n_M = 1: per-l diagonalisation of (A_l, S_y): W_y (Lambda_y + lambda_x)^{-1} W-bar_y on transposed slabs
       const T* Wyb = is32 ? (const T*)cp.Wyb32 : (const T*)cp.Wyb64;
@@ -949,32 +989,10 @@ static int precond_impl(fm_ctx* c, const TIO* x, TIO* y, T* t) {
         k_mix<T, false, false, false><<<gyy, 256, 0, c->stream>>>(Wy, t, u, cp.ny, cp.nx, cp.nz, cp.off, c->M0, nullptr, nullptr);
         prof_end(c, tk_, 2.0 * cp.ny * ncomp, 2.0 * ncomp * ts);
       }
+      c->launches += 2;
     } else {
-    YArgs ya;
-    ya.nx = cp.nx; ya.ny = cp.ny; ya.nz = cp.nz; ya.M0 = c->M0; ya.nl = cp.nl; ya.comp_off = cp.off;
-    ya.chain_lo = (const int*)cp.d_chain_lo; ya.chain_n = (const int*)cp.d_chain_n;
-    ya.band_off = cp.d_band_off; ya.lmul_off = cp.d_lmul_off; ya.piv_off = cp.d_piv_off;
-    int maxnc = 1;
-    for (int v : cp.chain_n) maxnc = std::max(maxnc, v);
-    const size_t line_bytes = (size_t)maxnc * cp.ny * sizeof(T);
-    {
-      const int tk_ = prof_begin(c, FM_KERNEL_YSOLVE);
-      if (maxnc == 1 && line_bytes * 32 <= 200 * 1024) {
-        dim3 gy((cp.nx + 31) / 32, cp.nl);
-        k_ysolve1<T, 32><<<gy, 32, line_bytes * 32, c->stream>>>(ya, U, L, cp.yP, u);
-      } else if (line_bytes * 64 <= 200 * 1024) {
-        dim3 gy((cp.nx + 63) / 64, cp.nl);
-        k_ysolve<T, 64><<<gy, 64, line_bytes * 64, c->stream>>>(ya, U, L, cp.yP, u);
-      } else if (line_bytes * 32 <= 200 * 1024) {
-        dim3 gy((cp.nx + 31) / 32, cp.nl);
-        k_ysolve<T, 32><<<gy, 32, line_bytes * 32, c->stream>>>(ya, U, L, cp.yP, u);
-      } else {
-        if (line_bytes * 8 > 200 * 1024) return FM_ERR_ARG;  // M' chains too long for one line in shared memory
-        dim3 gy((cp.nx + 7) / 8, cp.nl);
-        k_ysolve<T, 8><<<gy, 8, line_bytes * 8, c->stream>>>(ya, U, L, cp.yP, u);
-      }
-      prof_end(c, tk_, yfl, yby);
-    }
+      const int rc = ysolve_banded<T>(c, cp, u);
+      if (rc) return rc;
     }
     {
       const int tk_ = prof_begin(c, FM_KERNEL_XMIX);
@@ -986,7 +1004,7 @@ static int precond_impl(fm_ctx* c, const TIO* x, TIO* y, T* t) {
       k_zmix<T, TIO, T><<<gz, 128, smz, c->stream>>>(Wz, t, y, cp.nz, nxy, cp.off);
       prof_end(c, tk_, 2.0 * cp.nz * ncomp, ncomp * (8.0 + ts));
     }
-    c->launches += 5;
+    c->launches += 4;
   }
   FM_CUDA(cudaGetLastError());
   return FM_OK;
@@ -1254,7 +1272,7 @@ int kernels_init(fm_ctx* c) {
   FM_CUDA(cudaFuncSetAttribute(k_ysolve<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_ysolve<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_ysolve<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  return FM_OK;
+  return tc_kernels_init();
 }
 
 int fill_normal(fm_ctx* c, double* x, uint64_t seed) {

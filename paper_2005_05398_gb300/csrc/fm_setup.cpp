@@ -181,6 +181,12 @@ static double vhat(const fm_ctx* c, int a, double y, double Ry) {
 // the symmetries d_{M M'} = (-1)^{M-M'} d_{M' M} = d_{-M', -M} for the other indices.
 // d_over_sin returns d / sin(w)^k (k <= min(|M-M'|, |M+M'|)).
 // ---------------------------------------------------------------------------
+// a float64 value as an unevaluated sum of two floats (hi, lo)
+static float2 split2(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
 static double lfact(int n) { return std::lgamma(n + 1.0); }
 
 static double binom(int n, int k) {
@@ -579,6 +585,10 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       if ((rc = dev_alloc(c, (void**)&cp.Wyb64, (size_t)nl * ny * ny * 8))) return rc;
       if ((rc = dev_alloc(c, (void**)&cp.dLy64, (size_t)nl * ny * 8))) return rc;
       if ((rc = upload(c, (void**)&cp.dLx64, cp.Lx.data(), cp.Lx.size() * 8))) return rc;
+      std::vector<float2> lx2(cp.Lx.size());
+      for (size_t q = 0; q < lx2.size(); ++q) lx2[q] = split2(cp.Lx[q]);
+      if ((rc = upload(c, (void**)&cp.dLx2, lx2.data(), lx2.size() * sizeof(float2)))) return rc;
+      if ((rc = dev_alloc(c, (void**)&cp.dLy2, (size_t)nl * ny * sizeof(float2)))) return rc;
     }
   }
   return FM_OK;
@@ -633,7 +643,7 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
       po += n * nx;
     }
     bytes += bo * 12.0 + lo * 12.0 + po;
-    if (nM == 1) bytes += 2.0 * nl * ny * ny * 12.0 + nl * (nx + ny) * 12.0;  // per-l y diagonalisation
+    if (nM == 1) bytes += 2.0 * nl * ny * ny * 12.0 + nl * (nx + ny) * 20.0;  // per-l y diagonalisation
   }
   const double m = o->restart_m, ncv = o->ncv, n = (double)N;
   bytes += n * 8.0 * (5 + 2 + 3 + 16) + n * 4.0 * 2;                    // apply scratch, stage buffers, tuning
@@ -742,6 +752,9 @@ int setup_shift(fm_ctx* c, double Estar) {
         FM_CUDA(cudaMemcpyAsync(cp.Wy64, Wy.data(), Wy.size() * 8, cudaMemcpyHostToDevice, c->stream));
         FM_CUDA(cudaMemcpyAsync(cp.Wyb64, Wyb.data(), Wyb.size() * 8, cudaMemcpyHostToDevice, c->stream));
         FM_CUDA(cudaMemcpyAsync(cp.dLy64, Ly.data(), Ly.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        std::vector<float2> ly2(Ly.size());
+        for (size_t q = 0; q < ly2.size(); ++q) ly2[q] = split2(Ly[q]);
+        FM_CUDA(cudaMemcpyAsync(cp.dLy2, ly2.data(), ly2.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
         FM_CUDA(cudaStreamSynchronize(c->stream));
         cp.ydiag_ok = true;
       }

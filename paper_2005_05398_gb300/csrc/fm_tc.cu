@@ -1,0 +1,572 @@
+// Tensor-core mode products of the float32 preconditioner (Eq. prec-2, Section 3.3).
+//
+// The inverse of the tensor-trick preconditioner is a chain of mode products: W-bar_z, W-bar_x,
+// the y stage, W_x, W_z.  The x and y stages are, per (component, M', z-mode) slab, dense
+// n x n matrix products with the slab (n = 2 nint <= 256).  Here they run as batched GEMMs on the
+// 5th-generation tensor cores: tcgen05.mma kind::tf32 with float32 accumulation in tensor memory,
+// both operands staged into shared memory by TMA (128-byte swizzle, K-major), one CTA per 128
+// slab rows, a 4-deep mbarrier pipeline between the TMA producer thread and the MMA thread, and
+// a 4-warp epilogue that reads the accumulator with tcgen05.ld.
+//
+// Every operand is K-major (the contracted index contiguous in memory).  The chain keeps that
+// true by choosing the layout each stage writes:
+//   z forward   x[M'][k][i][j]           -> t[slab][j][i]     (SIMT, transposed store)
+//   x forward   A = t (rows j, K = i)    -> u[slab][i][j]     (ydiag)  or u[slab][j][i] (banded y)
+//   y forward   A = u (rows i, K = j)    -> t[slab][i][j] / (lambda_x + lambda_y)
+//   y inverse   A = t (rows i, K = j)    -> u[slab][j][i]
+//   (banded y solves work in place on u[slab][j][i])
+//   x inverse   A = u (rows j, K = i)    -> t[slab][i][j]
+//   z inverse   t[slab][i][j]            -> y[M'][k][i][j]    (SIMT)
+// The diagonal 1/(lambda_x + lambda_y) of the y stage (lambda_y holds lambda_z - E*) is summed
+// from float64 values split into (hi, lo) float pairs, so that the near-singular sum keeps its
+// float64 accuracy before the float32 reciprocal.
+//
+// Every mbarrier wait is bounded (about one second of global time); a wait that expires sets an
+// error flag that the host reads, and the kernel still releases its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+#include <type_traits>
+
+#include "fm_internal.h"
+
+namespace fmi {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the completion of the phase with the given parity, for at most about one second.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255u) == 255u && global_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte swizzled layout
+// (rows of 128 bytes, 8-row atoms 1024 bytes apart).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading-dimension offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride between 8-row atoms
+  d |= (uint64_t)1 << 46;             // descriptor version of sm_100 family
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::tf32, D float32, A and B tf32, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t tf32_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive accumulator columns of this warp's 32 lanes (one row per thread)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 1 / (a + b) for a = ah + al, b = bh + bl given as float pairs: the sum is formed with an
+// error-free two-sum of the high parts, so cancellation between a and b costs no accuracy.
+__device__ __forceinline__ float inv_sum2(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  const float e = (a.x - (s - bb)) + (b.x - bb);
+  return 1.0f / (s + (e + (a.y + b.y)));
+}
+
+}  // namespace
+
+struct TcArgs {
+  int rows;            // A rows per slab (the vector index that is not contracted)
+  int K;               // contraction length
+  int N;               // outputs per row (rows of W)
+  int nb;              // N rounded up to 16: MMA N and the B box height
+  int nkb;             // K blocks of 32 elements
+  int stages;          // pipeline depth
+  int ncols;           // tensor-memory columns allocated (power of two >= nb)
+  int nz;              // slabs per M' (slab = iM * nz + k, l - M0 = iM + k)
+  int trans_out;       // 1: out[slab][n][row]; 0: out[slab][row][n]
+  int64_t slab_stride;
+  int ldo;             // stride between out rows of the chosen layout
+  float* out;
+  const float2* dRow;  // optional diagonal terms (hi, lo): [nl][rows]
+  const float2* dCol;  //                                    [nl][N]
+  int* err;            // set to 1 when a bounded wait expired
+};
+
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTileA = 128 * 128;  // 128 rows x 32 tf32
+
+// out = W^l . slab (see the chain above), one CTA per (128-row tile, slab)
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_mix(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+  extern __shared__ unsigned char tc_smem[];
+  const uint32_t raw = smem_u32(tc_smem);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = tc_smem + (base - raw);
+  const uint32_t tileB = (uint32_t)a.nb * 128u;
+  const uint32_t stage_bytes = kTileA + tileB;
+  const uint32_t bars = base + (uint32_t)a.stages * stage_bytes;  // full[8], empty[8], done
+  const uint32_t full0 = bars, empty0 = bars + 64, done = bars + 128, slot = bars + 136;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bars - base) + 140);
+  volatile int* n_issued = reinterpret_cast<volatile int*>(gbase + (bars - base) + 144);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slab = blockIdx.y, row0 = blockIdx.x * 128;
+  const int il = slab / a.nz + slab % a.nz;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    *n_issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(a.ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + (slot - base));
+
+  if (warp == 0 && lane == 0) {  // TMA producer
+    for (int kb = 0; kb < a.nkb; ++kb) {
+      const int s = kb % a.stages;
+      const uint32_t ph = (uint32_t)(kb / a.stages) & 1u;
+      if (kb >= a.stages && !mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const uint32_t sa = base + (uint32_t)s * stage_bytes;
+      mbar_expect_tx(full0 + 8 * s, stage_bytes);
+      tma_load_3d(sa, &tmA, kb * 32, row0, slab, full0 + 8 * s);
+      tma_load_3d(sa + kTileA, &tmB, kb * 32, 0, il, full0 + 8 * s);
+      *n_issued = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    const uint32_t idesc = tf32_idesc(a.nb);
+    bool ok = true;
+    for (int kb = 0; kb < a.nkb && ok; ++kb) {
+      const int s = kb % a.stages;
+      const uint32_t ph = (uint32_t)(kb / a.stages) & 1u;
+      if (!mbar_wait(full0 + 8 * s, ph) || *abort_flag) {
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = base + (uint32_t)s * stage_bytes;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        if (kb * 32 + kk * 8 >= a.K) break;  // zero-filled tail of the last block
+        mma_tf32(tmem, sw128_desc(sa + 32u * kk), sw128_desc(sa + kTileA + 32u * kk), idesc, (kb | kk) ? 1u : 0u);
+      }
+      mma_commit(empty0 + 8 * s);
+    }
+    mma_commit(done);  // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // epilogue: all four warps, warp w owns accumulator lanes (rows) 32w .. 32w + 31
+  const bool ready = mbar_wait(done, 0);
+  tc_fence_after();
+  if (!ready) *abort_flag = 1;
+  if (__all_sync(0xffffffffu, ready && !*abort_flag)) {
+    const int r = row0 + warp * 32 + lane;
+    const bool rok = r < a.rows;
+    float* outs = a.out + (int64_t)slab * a.slab_stride;
+    float2 drow = make_float2(0.f, 0.f);
+    if (a.dRow && rok) drow = a.dRow[(int64_t)il * a.rows + r];
+    float* stg = reinterpret_cast<float*>(gbase) + warp * (32 * 33);  // stage 0 is free now
+    for (int c0 = 0; c0 < a.nb; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (a.dRow) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = c0 + j;
+          if (n < a.N) v[j] *= inv_sum2(drow, a.dCol[(int64_t)il * a.N + n]);
+        }
+      }
+      if (a.trans_out) {  // out[n][r]: lanes hold consecutive rows, 128-byte stores per column
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = c0 + j;
+          if (rok && n < a.N) outs[(int64_t)n * a.ldo + r] = v[j];
+        }
+      } else {  // out[r][n]: transpose the warp's 32 x 32 block through shared memory
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
+        __syncwarp();
+        const int n = c0 + lane;
+        for (int q = 0; q < 32; ++q) {
+          const int rq = row0 + warp * 32 + q;
+          if (rq < a.rows && n < a.N) outs[(int64_t)rq * a.ldo + n] = stg[q * 33 + lane];
+        }
+        __syncwarp();
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    // a wait expired: let the loads still in flight (at most one per stage) land before exit
+    const int n = *n_issued;
+    for (int kb = max(0, n - a.stages); kb < n; ++kb)
+      (void)mbar_wait(full0 + 8 * (kb % a.stages), (uint32_t)(kb / a.stages) & 1u);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.ncols) : "memory");
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// z mode products, register-blocked: out[l][p] = sum_k W[l][k] in[k][p] for one (component, M')
+// and a tile of 128 points p = (i, j).  Warp w computes the outputs l = lc + w + 4u (u < 16) of
+// four points per lane; W is kept in shared memory permuted as Wp[k][w][u] so that a thread reads
+// its 16 weights of one k with four 16-byte loads.
+//   TRANS = false: the tile is 128 consecutive points of the [i][j] plane; out[l][i][j].
+//   TRANS = true:  the tile is 8 (i) x 16 (j) points; out[l][j][i] (x contiguous).
+// ---------------------------------------------------------------------------
+template <typename TI, typename TO, bool TRANS>
+__global__ void __launch_bounds__(128) k_zmix_rb(const float* __restrict__ Wall, const TI* __restrict__ in,
+                                                 TO* __restrict__ out, int nz, int nx, int ny, int64_t comp_off) {
+  extern __shared__ __align__(16) float zsm[];
+  float* Vs = zsm;                    // [nz][128]
+  float* Wp = zsm + (size_t)nz * 128;  // [nz][4][16]
+  const int iM = blockIdx.y;
+  const int64_t nxy = (int64_t)nx * ny;
+  const float* W = Wall + (int64_t)iM * nz * nz;
+  const int64_t base = comp_off + (int64_t)iM * nz * nxy;
+  int i0 = 0, j0 = 0;
+  int64_t p0 = 0;
+  if (TRANS) {
+    const int tj = (ny + 15) / 16;
+    i0 = (blockIdx.x / tj) * 8;
+    j0 = (blockIdx.x % tj) * 16;
+  } else {
+    p0 = (int64_t)blockIdx.x * 128;
+  }
+  // input tile: Vs[k][q], q = jl * 8 + il (TRANS) or q = p - p0
+  for (int e = threadIdx.x; e < nz * 128; e += 128) {
+    const int k = e / 128, t = e % 128;
+    float v = 0.f;
+    int q = t;
+    if (TRANS) {
+      const int il = t / 16, jl = t % 16;  // consecutive threads walk j: coalesced reads
+      const int i = i0 + il, j = j0 + jl;
+      q = jl * 8 + il;
+      if (i < nx && j < ny) v = (float)in[base + (int64_t)k * nxy + (int64_t)i * ny + j];
+    } else {
+      if (p0 + t < nxy) v = (float)in[base + (int64_t)k * nxy + p0 + t];
+    }
+    Vs[k * 128 + q] = v;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int lc = 0; lc < nz; lc += 64) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < nz * 64; e += 128) {  // Wp[k][w][u] = W[lc + w + 4u][k]
+      const int k = e / 64, wu = e % 64, w = wu / 16, u = wu % 16;
+      const int l = lc + w + 4 * u;
+      Wp[e] = (l < nz) ? W[(int64_t)l * nz + k] : 0.f;
+    }
+    __syncthreads();
+    float acc[16][4];
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[u][q] = 0.f;
+    for (int k = 0; k < nz; ++k) {
+      const float4 v = *reinterpret_cast<const float4*>(&Vs[k * 128 + 4 * lane]);
+      const float4* wp = reinterpret_cast<const float4*>(&Wp[(k * 4 + warp) * 16]);
+#pragma unroll
+      for (int u4 = 0; u4 < 4; ++u4) {
+        const float4 w = wp[u4];
+        const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          acc[4 * u4 + t][0] = fmaf(ww[t], v.x, acc[4 * u4 + t][0]);
+          acc[4 * u4 + t][1] = fmaf(ww[t], v.y, acc[4 * u4 + t][1]);
+          acc[4 * u4 + t][2] = fmaf(ww[t], v.z, acc[4 * u4 + t][2]);
+          acc[4 * u4 + t][3] = fmaf(ww[t], v.w, acc[4 * u4 + t][3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int l = lc + warp + 4 * u;
+      if (l >= nz) break;
+      TO* ol = out + base + (int64_t)l * nxy;
+      if (TRANS) {
+        const int jl = lane / 2, il = 4 * (lane % 2);  // q = 4 lane .. 4 lane + 3
+        const int j = j0 + jl, i = i0 + il;
+        if (j < ny) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (i + q < nx) ol[(int64_t)j * nx + i + q] = (TO)acc[u][q];
+        }
+      } else {
+        const int64_t p = p0 + 4 * lane;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (p + q < nxy) ol[p + q] = (TO)acc[u][q];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 3D float32 map [d2][d1][d0] (d0 contiguous), box 32 x box1 x 1, 128-byte swizzle, zero fill
+bool encode3(CUtensorMap* m, const float* ptr, int d0, int d1, int d2, int box1) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15u) != 0 || (d0 * 4) % 16 != 0 || box1 < 1 || box1 > 256) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+  const cuuint64_t strides[2] = {(cuuint64_t)d0 * 4, (cuuint64_t)d0 * d1 * 4};
+  const cuuint32_t box[3] = {32, (cuuint32_t)box1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int round16(int n) { return (n + 15) / 16 * 16; }
+
+int tmem_cols(int nb) {
+  int c = 32;
+  while (c < nb) c *= 2;
+  return c;
+}
+
+size_t tc_smem_bytes(int nb, int stages, int ncols) {
+  size_t b = 1024 + (size_t)stages * (kTileA + (size_t)nb * 128) + 256;
+  // at most 512 / ncols CTAs may share an SM's tensor memory: ask for enough shared memory that
+  // no more fit (228 KB per SM, 1 KB reserved per CTA)
+  const int max_ctas = 512 / ncols;
+  if (max_ctas < 16) b = std::max(b, (size_t)(233472 / (max_ctas + 1)) + 1);
+  return b;
+}
+
+}  // namespace
+
+bool tc_component_ok(const Comp& cp) {
+  return cp.nx % 4 == 0 && cp.ny % 4 == 0 && cp.nx <= 256 && cp.ny <= 256 && cp.nx >= 16 && cp.ny >= 16;
+}
+
+int tc_setup(fm_ctx* c) {
+  c->tc_active = false;
+  if (c->opts.precision == FM_PREC_FP64 || c->opts.mma == FM_MMA_SIMT) return FM_OK;
+  bool all = true;
+  for (auto& cp : c->comps) all = all && tc_component_ok(cp);
+  if (!all) return c->opts.mma == FM_MMA_TF32 ? FM_ERR_ARG : FM_OK;
+  if (!encode_fn()) return c->opts.mma == FM_MMA_TF32 ? FM_ERR_CUDA : FM_OK;
+  if (!c->tc_err) {
+    int rc = dev_alloc(c, (void**)&c->tc_err, 256);
+    if (rc) return rc;
+    FM_CUDA(cudaMemsetAsync(c->tc_err, 0, 256, c->stream));
+  }
+  for (auto& cp : c->comps) {
+    const int nx = cp.nx, ny = cp.ny, ns = c->nM * cp.nz, nl = cp.nl;
+    float* t = c->t32 + cp.off;
+    float* u = c->u32 + cp.off;
+    bool ok = encode3(&cp.tm[0], t, nx, ny, ns, 128)       // x forward: t[slab][j][i]
+              && encode3(&cp.tm[1], u, nx, ny, ns, 128)     // x inverse: u[slab][j][i]
+              && encode3(&cp.tm[2], cp.Wxb32, nx, nx, nl, round16(nx)) && encode3(&cp.tm[3], cp.Wx32, nx, nx, nl, round16(nx));
+    if (ok && cp.Wy32) {
+      ok = encode3(&cp.tm[4], u, ny, nx, ns, 128)           // y forward: u[slab][i][j]
+           && encode3(&cp.tm[5], t, ny, nx, ns, 128)        // y inverse: t[slab][i][j]
+           && encode3(&cp.tm[6], cp.Wyb32, ny, ny, nl, round16(ny)) && encode3(&cp.tm[7], cp.Wy32, ny, ny, nl, round16(ny));
+    }
+    if (!ok) return FM_ERR_CUDA;
+  }
+  c->tc_active = true;
+  return FM_OK;
+}
+
+int tc_kernels_init() {
+  FM_CUDA(cudaFuncSetAttribute(k_tc_mix, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_zmix_rb<double, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_zmix_rb<float, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_zmix_rb<float, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_zmix_rb<float, float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+  return FM_OK;
+}
+
+namespace {
+
+// one tensor-core stage: out = W^l . slab for every slab of component cp
+int tc_stage(fm_ctx* c, const Comp& cp, const CUtensorMap& mA, const CUtensorMap& mB, int rows, int K, int N,
+             bool trans_out, float* out, const float2* dRow, const float2* dCol, int cls) {
+  TcArgs a;
+  a.rows = rows;
+  a.K = K;
+  a.N = N;
+  a.nb = round16(N);
+  a.nkb = (K + 31) / 32;
+  a.stages = std::min(4, a.nkb);
+  a.ncols = tmem_cols(a.nb);
+  a.nz = cp.nz;
+  a.trans_out = trans_out ? 1 : 0;
+  a.slab_stride = (int64_t)rows * N;
+  a.ldo = trans_out ? rows : N;
+  a.out = out;
+  a.dRow = dRow;
+  a.dCol = dCol;
+  a.err = c->tc_err;
+  const int ns = c->nM * cp.nz;
+  dim3 grid((unsigned)((rows + 127) / 128), (unsigned)ns);
+  const size_t smem = tc_smem_bytes(a.nb, a.stages, a.ncols);
+  const double nun = (double)rows * N * ns;
+  const int tk_ = prof_begin(c, cls);
+  k_tc_mix<<<grid, kTcThreads, smem, c->stream>>>(mA, mB, a);
+  prof_end(c, tk_, 2.0 * K * nun, 8.0 * nun);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+template <typename TI, typename TO, bool TRANS>
+int zstage(fm_ctx* c, const Comp& cp, const float* W, const TI* in, TO* out) {
+  const int nz = cp.nz;
+  const int64_t nxy = (int64_t)cp.nx * cp.ny;
+  const unsigned tiles = TRANS ? (unsigned)(((cp.nx + 7) / 8) * ((cp.ny + 15) / 16)) : (unsigned)((nxy + 127) / 128);
+  dim3 grid(tiles, c->nM);
+  const size_t smem = ((size_t)nz * 128 + (size_t)nz * 64) * sizeof(float);
+  if (smem > 100 * 1024) return FM_ERR_ARG;
+  const double ncomp = (double)nxy * nz * c->nM;
+  const int tk_ = prof_begin(c, FM_KERNEL_ZMIX);
+  k_zmix_rb<TI, TO, TRANS><<<grid, 128, smem, c->stream>>>(W, in, out, nz, cp.nx, cp.ny, cp.off);
+  prof_end(c, tk_, 2.0 * nz * ncomp, ncomp * (double)(sizeof(TI) + sizeof(TO)));
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+}  // namespace
+
+// y = P^{-1} x through the tensor-core chain (float32 stage buffers t32 / u32).  The banded y
+// solves (n_M > 1, or when chosen) run on u[slab][j][i] through the given callback.
+template <typename TIO>
+int precond_tc(fm_ctx* c, Comp& cp, const TIO* x, TIO* y, bool ydiag, int (*ysolve)(fm_ctx*, Comp&)) {
+  int rc;
+  float* t = c->t32 + cp.off;
+  float* u = c->u32 + cp.off;
+  const int nx = cp.nx, ny = cp.ny;
+  if ((rc = zstage<TIO, float, true>(c, cp, cp.Wzb32, x, c->t32))) return rc;  // t[slab][j][i]
+  // x forward: rows j, K = i -> u[slab][i][j] (ydiag) or u[slab][j][i] (banded y)
+  if ((rc = tc_stage(c, cp, cp.tm[0], cp.tm[2], ny, nx, nx, ydiag, u, nullptr, nullptr, FM_KERNEL_XMIX))) return rc;
+  if (ydiag) {
+    // y forward with the diagonal: rows i, K = j -> t[slab][i][j] / (lambda_x,i + lambda_y,j)
+    if ((rc = tc_stage(c, cp, cp.tm[4], cp.tm[6], nx, ny, ny, false, t, cp.dLx2, cp.dLy2, FM_KERNEL_YSOLVE))) return rc;
+    // y inverse: rows i, K = j -> u[slab][j][i]
+    if ((rc = tc_stage(c, cp, cp.tm[5], cp.tm[7], nx, ny, ny, true, u, nullptr, nullptr, FM_KERNEL_YSOLVE))) return rc;
+  } else {
+    if ((rc = ysolve(c, cp))) return rc;
+  }
+  // x inverse: rows j, K = i -> t[slab][i][j]
+  if ((rc = tc_stage(c, cp, cp.tm[1], cp.tm[3], ny, nx, nx, true, t, nullptr, nullptr, FM_KERNEL_XMIX))) return rc;
+  return zstage<float, TIO, false>(c, cp, cp.Wz32, c->t32, y);
+}
+
+template int precond_tc<double>(fm_ctx*, Comp&, const double*, double*, bool, int (*)(fm_ctx*, Comp&));
+template int precond_tc<float>(fm_ctx*, Comp&, const float*, float*, bool, int (*)(fm_ctx*, Comp&));
+
+int tc_check(fm_ctx* c) {
+  if (!c->tc_active || !c->tc_err) return FM_OK;
+  int h = 0;
+  FM_CUDA(cudaMemcpyAsync(&h, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  return h ? FM_ERR_TIMEOUT : FM_OK;
+}
+
+}  // namespace fmi

@@ -1,0 +1,137 @@
+"""GPU: the float32 preconditioner with its x and y stages on the tensor cores (TF32 mode
+products, float32 accumulation).  The grids span several 128-row tiles, K blocks with ragged
+tails and both y-stage forms (per-l diagonalisation for n_M = 1, banded M'-chain solves)."""
+import numpy as np
+import pytest
+
+from fm_inputs import workload, rand_vec
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# TF32 keeps 10 mantissa bits (unit roundoff 2^-11); four chained products of length <= 132 with
+# the conditioning of the 1D eigenvector bases stay well inside this bound (a layout or index
+# error gives O(1)).
+TF32_REL = 1e-2
+
+CASES = {
+    "he_l0_rows132": dict(nint=(66, 34, 3), R=(20.0, 17.0)),      # y stage: 2 row tiles (128 + 4)
+    "he_l0_rows132y": dict(nint=(34, 66, 3), R=(20.0, 17.0)),     # x stage: 2 row tiles
+    "he_l1_banded": dict(J=1, nint=(10, 12, 4), R=(20.0, 17.0)),  # n_M = 2: banded y solves between
+    "psm_l2": dict(J=2, nint=(8, 10, 4), R=(30.0, 27.0), mass=(1.0, 1.0, 1.0), charge=(-1.0, -1.0, 1.0),
+                   shift=-0.27),
+}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2005_05398_gb300 as p
+    from paper_2005_05398_gb300 import build
+    build.build()
+    p.lib()
+    return p
+
+
+def _dev(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+def _wl(name):
+    return workload("he_l0_24x24x8", **CASES[name])
+
+
+def test_tc_eligibility(pkg):
+    from paper_2005_05398_gb300._lib import FMError
+    ctx = pkg.Context(_wl("he_l1_banded"), precision=1, mma=2)
+    ctx.close()
+    with pytest.raises(FMError) as e:  # n_x = 14, n_y = 18: not multiples of 4
+        pkg.Context(workload("he_l0_24x24x8", nint=(7, 9, 5)), precision=1, mma=2)
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("y_solver", [0, 1])
+def test_tc_precond_close_to_fp64(pkg, name, y_solver):
+    wl = _wl(name)
+    E = wl["shift"] + 0.011
+    ref_ctx = pkg.Context(wl, precision=0, y_solver=y_solver)
+    tc = pkg.Context(wl, precision=1, mma=2, y_solver=y_solver)
+    simt = pkg.Context(wl, precision=1, mma=1, y_solver=y_solver)
+    v = _dev(rand_vec(ref_ctx.n, 21))
+    out = {}
+    for key, c in (("ref", ref_ctx), ("tc", tc), ("simt", simt)):
+        c.fm_set_shift(E)
+        y = torch.empty_like(v)
+        c.fm_precond_apply(v, y)
+        out[key] = y
+        c.close()
+    nref = torch.linalg.norm(out["ref"]).item()
+    e_simt = torch.linalg.norm(out["simt"] - out["ref"]).item() / nref
+    e_tc = torch.linalg.norm(out["tc"] - out["ref"]).item() / nref
+    print(name, y_solver, "float32 SIMT", e_simt, "TF32 tensor cores", e_tc)
+    assert e_simt < 1e-4
+    assert e_tc < TF32_REL, name
+
+
+def test_tc_computed_z_inverts_fmfin(pkg):
+    """n_M = 1, computed z eigenvalues: the preconditioner is the exact inverse of Eq. FM-fin's left
+    operator, so P^{-1} L v returns v to TF32 accuracy through the tensor-core chain."""
+    from oracle.system import FMSystem
+    from oracle.precond import Preconditioner
+    wl = workload("he_l0_24x24x8", nint=(10, 8, 3), R=(10.0, 12.0))
+    s = FMSystem(wl)
+    E = -2.7
+    P = Preconditioner(s, E, z_eigs="computed")
+    ctx = pkg.Context(wl, z_eigs=1, precision=1, mma=2)
+    ctx.fm_set_shift(E)
+    v = rand_vec(s.N, 22)
+    Lv = np.zeros(s.N)
+    for a in s.comps:
+        g = s.g[a]
+        Lv[s.off[a]:s.off[a] + g.csize] = P.dense_L_fmfin(a) @ v[s.off[a]:s.off[a] + g.csize]
+    y = torch.empty(s.N, dtype=torch.float64, device="cuda")
+    ctx.fm_precond_apply(_dev(Lv), y)
+    # L v is dominated by its high-frequency part, which the inverse cancels: the TF32 truncation
+    # of the stages (2^-10 relative) is amplified by ||L^{-1}|| ||L v|| / ||v|| and by the condition of
+    # the 1D eigenvector bases, to about 1.4e-2 on this grid; an index or layout error gives O(1)
+    err = np.linalg.norm(y.cpu().numpy() - v) / np.linalg.norm(v)
+    print("computed-z TF32 identity error", err)
+    assert err < 5e-2
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_tc_solve_matches_sparse_lu(pkg, precision):
+    from oracle.system import FMSystem
+    from oracle import solvers
+    wl = workload("he_l0_24x24x8", nint=(10, 12, 4), R=(20.0, 17.0))
+    s = FMSystem(wl)
+    H, S = s.H(), s.S()
+    E = -2.5
+    b = rand_vec(s.N, 23)
+    ref = solvers.solve(H, S, E, b)
+    ctx = pkg.Context(wl, precision=precision, mma=2, restart_m=40)
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    info = ctx.fm_solve(E, _dev(b), x)
+    got = x.cpu().numpy()
+    assert info["converged"] == 1 and info["resid"] <= 1e-12
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8
+
+
+@pytest.mark.parametrize("name,k,precision", [("he_l1_banded", 2, 1), ("psm_l2", 2, 2), ("he_l1_banded", 2, 2)])
+def test_tc_eigs_match_oracle(pkg, name, k, precision):
+    from oracle.system import FMSystem
+    from oracle import solvers
+    wl = _wl(name)
+    s = FMSystem(wl)
+    H, S = s.H(), s.S()
+    shift = wl["shift"] if name != "he_l1_banded" else -2.12
+    Eo, _ = solvers.eigs_near(H, S, shift, k + 4)
+    real = np.abs(Eo.imag) <= 1e-10 * np.abs(Eo)
+    Eo = Eo[real][:k].real
+    ctx = pkg.Context(wl, restart_m=40, precision=precision, mma=2)
+    ev, info = ctx.fm_eigs(shift, k)
+    assert info["converged"] == 1
+    for i in range(k):
+        assert abs(ev[i] - Eo[i]) <= 1e-9 * abs(Eo[i]), (ev, Eo)
