@@ -85,9 +85,8 @@ struct Comp {
   std::vector<int64_t> band_off;        // per l: offset (in elements) of its group in yU / yL
   std::vector<int64_t> piv_off;
   int64_t band_total = 0, lmul_total = 0, piv_total = 0;
-  double* yU = nullptr;          // per l: [n][kl+ku+1][nx]
-  double* yL = nullptr;          // per l: [n][kl][nx]
-  unsigned char* yP = nullptr;   // per l: [n][nx] pivot offsets
+  double* yU = nullptr;          // per l: [n][kl+ku+1][nx], reciprocal pivot first
+  double* yL = nullptr;          // per l: [n][kl+1][nx], slot 0 the pivot offset, then the multipliers
   float* yU32 = nullptr; float* yL32 = nullptr;
   std::vector<int64_t> lmul_off;
   // n_M = 1: per-l diagonalisation of (A_l, S_y), A_l = -D_y + (c_l Y_r2 + V^ - E*) S_y, used by the
@@ -213,7 +212,9 @@ int tc_setup(fm_ctx* c);       // after the stage buffers exist: encode the TMA 
 int tc_kernels_init();
 int tc_check(fm_ctx* c);       // FM_ERR_TIMEOUT when a tensor-core kernel gave up a wait
 template <typename TIO>
-int precond_tc(fm_ctx* c, Comp& cp, const TIO* x, TIO* y, bool ydiag, int (*ysolve)(fm_ctx*, Comp&));
+int precond_tc_front(fm_ctx* c, Comp& cp, const TIO* x, bool ydiag);   // z, x forward (+ diagonalised y)
+template <typename TIO>
+int precond_tc_back(fm_ctx* c, Comp& cp, TIO* y);                       // x, z inverse
 }  // namespace fmi
 
 #define FM_CUDA(call)                                   \

@@ -370,159 +370,195 @@ __global__ void __launch_bounds__(256) k_mix(const T* __restrict__ Wall, const T
 // banded y solves: one thread per (l, i_x) line of a component; the right-hand side is
 // the M'-chain of y-vectors t[iM][l - M'][i_x][:] interleaved as r = j * nc + c.
 struct YArgs {
-  int nx, ny, nz, M0, nl;
+  int nx, ny, nz, M0, nl, maxn;
   int64_t comp_off;
   const int* chain_lo;   // [nl]
   const int* chain_n;    // [nl]
   const int64_t* band_off;  // [nl] offset into U
   const int64_t* lmul_off;  // [nl] offset into L
-  const int64_t* piv_off;   // [nl] offset into P
 };
 
 // Transposed slabs [j][i_x]: element (iM, k, j, i_x) of a component lives at
-// comp_off + ((iM * nz + k) * ny + j) * nx + i_x.  A CTA stages LPB consecutive lines of one l
-// (rows r = j * nc + c) in shared memory with coalesced loads, each thread eliminates its
-// line there (factors streamed from global memory, coalesced across the lines), and the
-// CTA writes the lines back.
-template <typename T, int LPB>
-__global__ void __launch_bounds__(LPB) k_ysolve(YArgs a, const T* __restrict__ U, const T* __restrict__ L,
-                                                const unsigned char* __restrict__ Pv, T* __restrict__ t) {
-  extern __shared__ unsigned char smraw[];
-  T* xs = reinterpret_cast<T*>(smraw);  // [n][LPB]
-  const int il = blockIdx.y;
-  const int ix0 = blockIdx.x * LPB;
-  const int tid = threadIdx.x;
-  const int ix = ix0 + tid;
-  const int nc = a.chain_n[il], lo = a.chain_lo[il];
-  const int n = nc * a.ny;
-  const int kl = (nc == 1) ? 2 : 2 * nc + 1;
-  const int w = 2 * kl + 1;
-  const int l = a.M0 + il;
-  const bool live = ix < a.nx;
-  for (int r = 0; r < n; ++r) {
-    const int j = r / nc, c = r - j * nc;
-    const int iM = lo + c, k = l - a.M0 - iM;
-    const int64_t row = a.comp_off + (((int64_t)iM * a.nz + k) * a.ny + j) * a.nx;
-    xs[r * LPB + tid] = live ? t[row + ix] : (T)0;
-  }
-  __syncthreads();
-  if (live) {
-    const T* Ub = U + a.band_off[il] + ix;
-    const T* Lb = L + a.lmul_off[il] + ix;
-    const unsigned char* Pb = Pv + a.piv_off[il] + ix;
-    const int64_t nx = a.nx;
-    for (int r = 0; r < n; ++r) {
-      const int pr = r + Pb[(int64_t)r * nx];
-      T xr = xs[pr * LPB + tid];
-      if (pr != r) {
-        xs[pr * LPB + tid] = xs[r * LPB + tid];
+// comp_off + ((iM * nz + k) * ny + j) * nx + i_x.  One thread per line (l, i_x), LPB consecutive
+// lines of one l per CTA, the unknowns of a line ordered r = j * n_c + c.  A factor "segment" is
+// one (row, slot) entry for the CTA's LPB lines: contiguous in memory, and contiguous in the
+// shared-memory ring.  The CTA copies segments with cooperative cp.async pieces of PB bytes (a
+// thread copies pieces of other threads' lines), so every wait is followed by a CTA barrier:
+//   [copy chunk ch+1] [wait chunk ch] [barrier] [eliminate the R rows of chunk ch] [barrier]
+// The line itself is staged in shared memory the same way.
+__device__ __forceinline__ void cp_async_pb(void* dst, const void* src, int pb) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if (pb == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Copy nseg segments: segment s goes from src(s) (LPB elements, contiguous) to dst(s); only the
+// first 'valid' lines are copied (valid is a multiple of the piece length).  Thread t copies piece
+// t % pps of segments t / pps, t / pps + LPB / pps, ...
+template <typename T, int LPB, typename SrcF, typename DstF>
+__device__ __forceinline__ void copy_segments(int nseg, int valid, int pb, SrcF src, DstF dst) {
+  const int ep = pb / (int)sizeof(T);  // elements per piece
+  const int pps = (valid + ep - 1) / ep;
+  const int spr = LPB / pps;           // segments per round
+  const int t = threadIdx.x;
+  if (t >= spr * pps) return;
+  const int k = t % pps;
+  for (int sg = t / pps; sg < nseg; sg += spr) cp_async_pb(dst(sg) + k * ep, src(sg) + k * ep, pb);
+}
+
+// One line through the banded LU factors.  The forward sweep keeps x[r .. r+KL] in a register
+// window (the pivot swap is a select over the window), the backward sweep keeps the KL+KU solved
+// values x[r+1 ..] in registers and adds the newest one last, so the row-to-row dependency is a
+// couple of FMAs instead of a shared-memory round trip.
+template <typename T, int LPB, int KL>
+__device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* __restrict__ Ub, int64_t nx, int n,
+                                            int R, T* xs, T* ring, int Wring, int tid, bool live, int valid,
+                                            int pb) {
+  constexpr int W = 2 * KL + 1;
+  const int nch = (n + R - 1) / R;
+  const size_t half = (size_t)R * Wring * LPB;
+  // forward: L z = P b, row r uses L[r][0] (pivot offset) and L[r][1..KL]
+  auto issue_f = [&](int ch) {
+    T* buf = ring + (ch & 1) * half;
+    const int r0 = ch * R, rows = min(R, n - r0);
+    copy_segments<T, LPB>(
+        rows * (KL + 1), valid, pb,
+        [&](int sg) { return Lb + ((int64_t)(r0 + sg / (KL + 1)) * (KL + 1) + sg % (KL + 1)) * nx; },
+        [&](int sg) { return buf + ((size_t)(sg / (KL + 1)) * Wring + sg % (KL + 1)) * LPB; });
+    cp_commit();
+  };
+  T w[KL + 1];
+#pragma unroll
+  for (int i = 0; i <= KL; ++i) w[i] = (live && i < n) ? xs[i * LPB + tid] : (T)0;
+  issue_f(0);
+  for (int ch = 0; ch < nch; ++ch) {
+    if (ch + 1 < nch) {
+      issue_f(ch + 1);
+      cp_wait_all_but_one();
+    } else {
+      cp_wait_all();
+    }
+    __syncthreads();
+    if (live) {
+      const T* buf = ring + (ch & 1) * half;
+      const int r0 = ch * R, rows = min(R, n - r0);
+      for (int q = 0; q < rows; ++q) {
+        const int r = r0 + q;
+        const T* f = buf + (size_t)q * Wring * LPB + tid;
+        const int p = (int)f[0];
+        T xr = w[0];
+#pragma unroll
+        for (int i = 1; i <= KL; ++i) xr = (p == i) ? w[i] : xr;
+#pragma unroll
+        for (int i = 1; i <= KL; ++i)
+          if (p == i) w[i] = w[0];
+#pragma unroll
+        for (int d = 1; d <= KL; ++d) w[d] -= f[d * LPB] * xr;
         xs[r * LPB + tid] = xr;
+#pragma unroll
+        for (int i = 0; i < KL; ++i) w[i] = w[i + 1];
+        w[KL] = (r + KL + 1 < n) ? xs[(r + KL + 1) * LPB + tid] : (T)0;
       }
-      const int dmax = min(kl, n - 1 - r);
-      for (int d = 1; d <= dmax; ++d) xs[(r + d) * LPB + tid] -= Lb[((int64_t)r * kl + (d - 1)) * nx] * xr;
     }
-    for (int r = n - 1; r >= 0; --r) {
-      T s = xs[r * LPB + tid];
-      const int dmax = min(w - 1, n - 1 - r);
-      for (int d = 1; d <= dmax; ++d) s -= Ub[((int64_t)r * w + d) * nx] * xs[(r + d) * LPB + tid];
-      xs[r * LPB + tid] = s / Ub[((int64_t)r * w) * nx];
-    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int r = 0; r < n; ++r) {
-    const int j = r / nc, c = r - j * nc;
-    const int iM = lo + c, k = l - a.M0 - iM;
-    const int64_t row = a.comp_off + (((int64_t)iM * a.nz + k) * a.ny + j) * a.nx;
-    if (live) t[row + ix] = xs[r * LPB + tid];
+  // backward: U x = z, rows descending, U[r][0] the reciprocal of the pivot, U[r][d] the coefficient
+  // of x[r + d]; v[i] = x[r + 1 + i] (0 beyond the line, where the band entries are 0)
+  auto issue_b = [&](int ch) {
+    T* buf = ring + (ch & 1) * half;
+    const int rtop = n - 1 - ch * R, rows = min(R, rtop + 1);
+    copy_segments<T, LPB>(
+        rows * W, valid, pb, [&](int sg) { return Ub + ((int64_t)(rtop - sg / W) * W + sg % W) * nx; },
+        [&](int sg) { return buf + ((size_t)(sg / W) * Wring + sg % W) * LPB; });
+    cp_commit();
+  };
+  T v[W - 1];
+#pragma unroll
+  for (int i = 0; i < W - 1; ++i) v[i] = (T)0;
+  issue_b(0);
+  for (int ch = 0; ch < nch; ++ch) {
+    if (ch + 1 < nch) {
+      issue_b(ch + 1);
+      cp_wait_all_but_one();
+    } else {
+      cp_wait_all();
+    }
+    __syncthreads();
+    if (live) {
+      const T* buf = ring + (ch & 1) * half;
+      const int rows = min(R, n - ch * R);
+      for (int q = 0; q < rows; ++q) {
+        const int r = n - 1 - (ch * R + q);
+        const T* f = buf + (size_t)q * Wring * LPB + tid;
+        T s0 = xs[r * LPB + tid], s1 = 0;
+#pragma unroll
+        for (int d = 2; d < W; d += 2) s0 -= f[d * LPB] * v[d - 1];
+#pragma unroll
+        for (int d = 3; d < W; d += 2) s1 -= f[d * LPB] * v[d - 1];
+        const T x = ((s0 + s1) - f[LPB] * v[0]) * f[0];
+        xs[r * LPB + tid] = x;
+#pragma unroll
+        for (int i = W - 2; i > 0; --i) v[i] = v[i - 1];
+        v[0] = x;
+      }
+    }
+    __syncthreads();
   }
 }
 
-// Single-M' chains (n_M = 1): kl = ku = 2, U rows of width 5.  Same staging as k_ysolve; the
-// factors of the next D rows are kept in flight in a register ring so that the elimination of
-// row r never waits on the load latency of its own factors.
+// the components of one launch (blockIdx.z selects one)
+template <typename T>
+struct YBatch {
+  YArgs a[3];
+  const T* U[3];
+  const T* L[3];
+};
+
 template <typename T, int LPB>
-__global__ void __launch_bounds__(LPB) k_ysolve1(YArgs a, const T* __restrict__ U, const T* __restrict__ L,
-                                                 const unsigned char* __restrict__ Pv, T* __restrict__ t) {
-  constexpr int KL = 2, W = 5, D = 8;
-  extern __shared__ unsigned char smraw[];
-  T* xs = reinterpret_cast<T*>(smraw);  // [n][LPB]
+__global__ void __launch_bounds__(LPB) k_ysolve(const YBatch<T> yb, int R, int Wring, int maxn, T* __restrict__ t) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const YArgs& a = yb.a[blockIdx.z];
+  const T* __restrict__ U = yb.U[blockIdx.z];
+  const T* __restrict__ L = yb.L[blockIdx.z];
   const int il = blockIdx.y;
+  const int ix0 = blockIdx.x * LPB;
+  if (il >= a.nl || ix0 >= a.nx) return;  // grid sized for the largest component (uniform per CTA)
+  const int nc = a.chain_n[il], lo = a.chain_lo[il];
+  const int n = nc * a.ny;
+  T* xs = reinterpret_cast<T*>(smraw);   // [n][LPB]
+  T* ring = xs + (size_t)maxn * LPB;     // [2][R][Wring][LPB]
   const int tid = threadIdx.x;
-  const int ix = blockIdx.x * LPB + tid;
-  const int n = a.ny;
+  const int valid = min(LPB, a.nx - ix0);
+  const bool live = tid < valid;
+  // 16-byte pieces when every segment start is 16-byte aligned, else 8-byte (n_x is even)
+  const int pb = ((a.nx * (int)sizeof(T)) % 16 == 0) ? 16 : 8;
   const int l = a.M0 + il;
-  const int iM = a.chain_lo[il], k = l - a.M0 - iM;
-  const int64_t slab = a.comp_off + ((int64_t)iM * a.nz + k) * a.ny * a.nx;
-  const bool live = ix < a.nx;
-#pragma unroll 8
-  for (int r = 0; r < n; ++r) xs[r * LPB + tid] = live ? t[slab + (int64_t)r * a.nx + ix] : (T)0;
+  auto xrow = [&](int r) -> int64_t {
+    const int j = r / nc, c = r - j * nc;
+    const int iM = lo + c, k = l - a.M0 - iM;
+    return a.comp_off + (((int64_t)iM * a.nz + k) * a.ny + j) * a.nx + ix0;
+  };
+  copy_segments<T, LPB>(n, valid, pb, [&](int r) { return t + xrow(r); }, [&](int r) { return xs + (size_t)r * LPB; });
+  cp_commit();
+  cp_wait_all();
   __syncthreads();
-  if (live) {
-    const int64_t nx = a.nx;
-    const T* Lb = L + a.lmul_off[il] + ix;
-    const T* Ub = U + a.band_off[il] + ix;
-    const unsigned char* Pb = Pv + a.piv_off[il] + ix;
-    T lb[D][KL];
-    int pb[D];
-#pragma unroll
-    for (int q = 0; q < D; ++q)
-      if (q < n) {
-        pb[q] = Pb[(int64_t)q * nx];
-        lb[q][0] = Lb[((int64_t)q * KL) * nx];
-        lb[q][1] = Lb[((int64_t)q * KL + 1) * nx];
-      }
-    for (int r0 = 0; r0 < n; r0 += D) {
-#pragma unroll
-      for (int q = 0; q < D; ++q) {
-        const int r = r0 + q;
-        if (r < n) {
-          const int pr = r + pb[q];
-          T xr = xs[pr * LPB + tid];
-          if (pr != r) {
-            xs[pr * LPB + tid] = xs[r * LPB + tid];
-            xs[r * LPB + tid] = xr;
-          }
-          if (r + 1 < n) xs[(r + 1) * LPB + tid] -= lb[q][0] * xr;
-          if (r + 2 < n) xs[(r + 2) * LPB + tid] -= lb[q][1] * xr;
-          const int rn = r + D;
-          if (rn < n) {
-            pb[q] = Pb[(int64_t)rn * nx];
-            lb[q][0] = Lb[((int64_t)rn * KL) * nx];
-            lb[q][1] = Lb[((int64_t)rn * KL + 1) * nx];
-          }
-        }
-      }
-    }
-    T ub[D][W];
-#pragma unroll
-    for (int q = 0; q < D; ++q) {
-      const int r = n - 1 - q;
-      if (r >= 0)
-#pragma unroll
-        for (int d = 0; d < W; ++d) ub[q][d] = Ub[((int64_t)r * W + d) * nx];
-    }
-    for (int r0 = 0; r0 < n; r0 += D) {
-#pragma unroll
-      for (int q = 0; q < D; ++q) {
-        const int r = n - 1 - (r0 + q);
-        if (r >= 0) {
-          T s = xs[r * LPB + tid];
-#pragma unroll
-          for (int d = 1; d < W; ++d)
-            if (r + d < n) s -= ub[q][d] * xs[(r + d) * LPB + tid];
-          xs[r * LPB + tid] = s / ub[q][0];
-          const int rn = r - D;
-          if (rn >= 0)
-#pragma unroll
-            for (int d = 0; d < W; ++d) ub[q][d] = Ub[((int64_t)rn * W + d) * nx];
-        }
-      }
-    }
+  const T* Lb = L + a.lmul_off[il] + ix0;
+  const T* Ub = U + a.band_off[il] + ix0;
+  switch (nc) {
+    case 1: ysolve_line<T, LPB, 2>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    case 2: ysolve_line<T, LPB, 5>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    case 3: ysolve_line<T, LPB, 7>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    case 4: ysolve_line<T, LPB, 9>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    case 5: ysolve_line<T, LPB, 11>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    case 6: ysolve_line<T, LPB, 13>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    case 7: ysolve_line<T, LPB, 15>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    default: ysolve_line<T, LPB, 17>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
   }
-  __syncthreads();
   if (live)
-#pragma unroll 8
-    for (int r = 0; r < n; ++r) t[slab + (int64_t)r * a.nx + ix] = xs[r * LPB + tid];
+    for (int r = 0; r < n; ++r) t[xrow(r) + tid] = xs[r * LPB + tid];
 }
 
 // ---------------------------------------------------------------------------
@@ -898,40 +934,69 @@ int launch_apply_scratch(fm_ctx* c, double E, const double* x, double* y, double
   return apply_t<double>(c, E, x, y, false, P, Q, R, false);
 }
 
-// Banded y solves of one component (Eq. prec-2 y stage with the M' chain), in place on
-// u[slab][j][i].
+// Banded y solves (Eq. prec-2 y stage with the M' chain) of the given components in one launch,
+// in place on u[slab][j][i].
 template <typename T>
-static int ysolve_banded(fm_ctx* c, fmi::Comp& cp, T* u) {
-  const T* U = std::is_same<T, double>::value ? (const T*)cp.yU : (const T*)cp.yU32;
-  const T* L = std::is_same<T, double>::value ? (const T*)cp.yL : (const T*)cp.yL32;
+static int ysolve_banded(fm_ctx* c, const std::vector<fmi::Comp*>& comps, T* u) {
+  if (comps.empty()) return FM_OK;
+  if (comps.size() > 3) return FM_ERR_ARG;
   const double ts = (double)sizeof(T);
-  double yfl = 0.0, yby = 0.0;  // per line 2n(2kl+ku) + n flops; factors + vector bytes
-  for (int il = 0; il < cp.nl; ++il) {
-    const int nc = cp.chain_n[il], n = nc * cp.ny, kl = (nc == 1) ? 2 : 2 * nc + 1;
-    yfl += (double)cp.nx * (2.0 * n * (3.0 * kl) + n);
-    yby += (double)cp.nx * ((double)n * (3.0 * kl + 1.0) * ts + n + 2.0 * n * ts);
+  double yfl = 0.0, yby = 0.0;  // per line 2n(kl + ku + kl) + n flops; factor and vector bytes
+  YBatch<T> yb;
+  int maxn = 1, wring = 5, gx = 1, gy = 1;
+  for (size_t q = 0; q < comps.size(); ++q) {
+    const fmi::Comp& cp = *comps[q];
+    for (int il = 0; il < cp.nl; ++il) {
+      const int nc = cp.chain_n[il], n = nc * cp.ny, kl = (nc == 1) ? 2 : 2 * nc + 1;
+      yfl += (double)cp.nx * (2.0 * n * (3.0 * kl) + n);
+      yby += (double)cp.nx * ((double)n * (3.0 * kl + 2.0) * ts + 2.0 * n * ts);
+    }
+    YArgs& ya = yb.a[q];
+    ya.nx = cp.nx; ya.ny = cp.ny; ya.nz = cp.nz; ya.M0 = c->M0; ya.nl = cp.nl; ya.comp_off = cp.off;
+    ya.chain_lo = (const int*)cp.d_chain_lo; ya.chain_n = (const int*)cp.d_chain_n;
+    ya.band_off = cp.d_band_off; ya.lmul_off = cp.d_lmul_off;
+    int maxnc = 1;
+    for (int v : cp.chain_n) maxnc = std::max(maxnc, v);
+    ya.maxn = maxnc * cp.ny;
+    yb.U[q] = std::is_same<T, double>::value ? (const T*)cp.yU : (const T*)cp.yU32;
+    yb.L[q] = std::is_same<T, double>::value ? (const T*)cp.yL : (const T*)cp.yL32;
+    const int klmax = (maxnc == 1) ? 2 : 2 * maxnc + 1;
+    maxn = std::max(maxn, ya.maxn);
+    wring = std::max(wring, 2 * klmax + 1);
+    gy = std::max(gy, cp.nl);
   }
-  YArgs ya;
-  ya.nx = cp.nx; ya.ny = cp.ny; ya.nz = cp.nz; ya.M0 = c->M0; ya.nl = cp.nl; ya.comp_off = cp.off;
-  ya.chain_lo = (const int*)cp.d_chain_lo; ya.chain_n = (const int*)cp.d_chain_n;
-  ya.band_off = cp.d_band_off; ya.lmul_off = cp.d_lmul_off; ya.piv_off = cp.d_piv_off;
-  int maxnc = 1;
-  for (int v : cp.chain_n) maxnc = std::max(maxnc, v);
-  const size_t line_bytes = (size_t)maxnc * cp.ny * sizeof(T);
+  int maxnx = 1;
+  for (auto* cp : comps) maxnx = std::max(maxnx, cp->nx);
+  // Lines per CTA, and factor rows per ring half: the CTAs are latency-bound, so the ring is sized
+  // for as many resident CTAs per SM as the grid can use (228 KB of shared memory per SM), with at
+  // least 8 rows of prefetch; failing that, the largest ring that fits 200 KB.
+  auto plan = [&](int lpb, int* R, size_t* sm) -> bool {
+    const size_t line = (size_t)maxn * lpb * sizeof(T), per_row = 2 * (size_t)wring * lpb * sizeof(T);
+    const int ctas = ((maxnx + lpb - 1) / lpb) * gy * (int)comps.size();
+    const int per_sm = std::max(1, std::min(8, (ctas + 151) / 152));
+    for (int want = per_sm; want >= 1; --want) {
+      const size_t cap = std::min<size_t>(200 * 1024, 233472 / want - 1024);
+      if (line + 8 * per_row > cap) continue;
+      *R = (int)std::min<size_t>(32, (cap - line) / per_row);
+      *sm = line + (size_t)*R * per_row;
+      return true;
+    }
+    if (line + 2 * per_row > 200 * 1024) return false;
+    *R = (int)std::min<size_t>(32, (200 * 1024 - line) / per_row);
+    *sm = line + (size_t)*R * per_row;
+    return true;
+  };
   const int tk_ = prof_begin(c, FM_KERNEL_YSOLVE);
-  if (maxnc == 1 && line_bytes * 32 <= 200 * 1024) {
-    dim3 gy((cp.nx + 31) / 32, cp.nl);
-    k_ysolve1<T, 32><<<gy, 32, line_bytes * 32, c->stream>>>(ya, U, L, cp.yP, u);
-  } else if (line_bytes * 64 <= 200 * 1024) {
-    dim3 gy((cp.nx + 63) / 64, cp.nl);
-    k_ysolve<T, 64><<<gy, 64, line_bytes * 64, c->stream>>>(ya, U, L, cp.yP, u);
-  } else if (line_bytes * 32 <= 200 * 1024) {
-    dim3 gy((cp.nx + 31) / 32, cp.nl);
-    k_ysolve<T, 32><<<gy, 32, line_bytes * 32, c->stream>>>(ya, U, L, cp.yP, u);
+  int R;
+  size_t sm;
+  if (plan(32, &R, &sm)) {
+    gx = (maxnx + 31) / 32;
+    k_ysolve<T, 32><<<dim3(gx, gy, (unsigned)comps.size()), 32, sm, c->stream>>>(yb, R, wring, maxn, u);
+  } else if (plan(8, &R, &sm)) {
+    gx = (maxnx + 7) / 8;
+    k_ysolve<T, 8><<<dim3(gx, gy, (unsigned)comps.size()), 8, sm, c->stream>>>(yb, R, wring, maxn, u);
   } else {
-    if (line_bytes * 8 > 200 * 1024) return FM_ERR_ARG;  // M' chains too long for one line in shared memory
-    dim3 gy((cp.nx + 7) / 8, cp.nl);
-    k_ysolve<T, 8><<<gy, 8, line_bytes * 8, c->stream>>>(ya, U, L, cp.yP, u);
+    return FM_ERR_ARG;  // M' chains too long for one line in shared memory
   }
   prof_end(c, tk_, yfl, yby);
   c->launches++;
@@ -939,24 +1004,26 @@ static int ysolve_banded(fm_ctx* c, fmi::Comp& cp, T* u) {
   return FM_OK;
 }
 
-static int ysolve32_cb(fm_ctx* c, fmi::Comp& cp) { return ysolve_banded<float>(c, cp, c->u32); }
-
+// y = P^{-1} x (Eq. prec-2), stage-major over the components: every component's z and x forward
+// stages (and the diagonalised y stage for n_M = 1), then one launch with the banded y solves of
+// all components that need them, then every component's x and z inverse stages.
 template <typename T, typename TIO>
 static int precond_impl(fm_ctx* c, const TIO* x, TIO* y, T* t) {
   const bool is32 = std::is_same<T, float>::value;
+  const bool tc = is32 && c->tc_active;
+  T* u = is32 ? (T*)c->u32 : (T*)c->u64;
+  std::vector<fmi::Comp*> banded;
+  int rc;
   for (auto& cp : c->comps) {
     const bool ymda = cp.ydiag_ok && (c->opts.y_solver == 2 || (c->opts.y_solver == 0 && is32));
-    if (is32 && c->tc_active) {  // x and y stages on the tensor cores
-      const int rc = fmi::precond_tc<TIO>(c, cp, x, y, ymda, ysolve32_cb);
-      if (rc) return rc;
+    if (!ymda) banded.push_back(&cp);
+    if (tc) {  // x and y stages on the tensor cores
+      if ((rc = fmi::precond_tc_front<TIO>(c, cp, x, ymda))) return rc;
       continue;
     }
     const int64_t nxy = (int64_t)cp.nx * cp.ny;
     const T* Wzb = std::is_same<T, double>::value ? (const T*)cp.Wzb : (const T*)cp.Wzb32;
-    const T* Wz = std::is_same<T, double>::value ? (const T*)cp.Wz : (const T*)cp.Wz32;
     const T* Wxb = std::is_same<T, double>::value ? (const T*)cp.Wxb : (const T*)cp.Wxb32;
-    const T* Wx = std::is_same<T, double>::value ? (const T*)cp.Wx : (const T*)cp.Wx32;
-    T* u = std::is_same<T, double>::value ? (T*)c->u64 : (T*)c->u32;
     const double ncomp = (double)nxy * cp.nz * c->nM;  // unknowns of this component
     const double ts = (double)sizeof(T);
     dim3 gz((unsigned)((nxy + 127) / 128), c->nM);
@@ -972,6 +1039,7 @@ static int precond_impl(fm_ctx* c, const TIO* x, TIO* y, T* t) {
       k_mix<T, false, true, false><<<gx, 256, 0, c->stream>>>(Wxb, t, u, cp.nx, cp.ny, cp.nz, cp.off, c->M0, nullptr, nullptr);
       prof_end(c, tk_, 2.0 * cp.nx * ncomp, 2.0 * ncomp * ts);
     }
+    c->launches += 2;
     if (ymda) {
       // n_M = 1: per-l diagonalisation of (A_l, S_y): W_y (Lambda_y + lambda_x)^{-1} W-bar_y on transposed slabs
       const T* Wyb = is32 ? (const T*)cp.Wyb32 : (const T*)cp.Wyb64;
@@ -990,10 +1058,22 @@ static int precond_impl(fm_ctx* c, const TIO* x, TIO* y, T* t) {
         prof_end(c, tk_, 2.0 * cp.ny * ncomp, 2.0 * ncomp * ts);
       }
       c->launches += 2;
-    } else {
-      const int rc = ysolve_banded<T>(c, cp, u);
-      if (rc) return rc;
     }
+  }
+  if ((rc = ysolve_banded<T>(c, banded, u))) return rc;
+  for (auto& cp : c->comps) {
+    if (tc) {
+      if ((rc = fmi::precond_tc_back<TIO>(c, cp, y))) return rc;
+      continue;
+    }
+    const int64_t nxy = (int64_t)cp.nx * cp.ny;
+    const T* Wz = std::is_same<T, double>::value ? (const T*)cp.Wz : (const T*)cp.Wz32;
+    const T* Wx = std::is_same<T, double>::value ? (const T*)cp.Wx : (const T*)cp.Wx32;
+    const double ncomp = (double)nxy * cp.nz * c->nM;
+    const double ts = (double)sizeof(T);
+    dim3 gz((unsigned)((nxy + 127) / 128), c->nM);
+    const size_t smz = ((size_t)cp.nz * cp.nz + (size_t)cp.nz * 128) * sizeof(T);
+    dim3 gx((cp.ny + 63) / 64, (cp.nx + 63) / 64, c->nM * cp.nz);
     {
       const int tk_ = prof_begin(c, FM_KERNEL_XMIX);
       k_mix<T, true, false, false><<<gx, 256, 0, c->stream>>>(Wx, u, t, cp.nx, cp.ny, cp.nz, cp.off, c->M0, nullptr, nullptr);
@@ -1004,7 +1084,7 @@ static int precond_impl(fm_ctx* c, const TIO* x, TIO* y, T* t) {
       k_zmix<T, TIO, T><<<gz, 128, smz, c->stream>>>(Wz, t, y, cp.nz, nxy, cp.off);
       prof_end(c, tk_, 2.0 * cp.nz * ncomp, ncomp * (8.0 + ts));
     }
-    c->launches += 4;
+    c->launches += 2;
   }
   FM_CUDA(cudaGetLastError());
   return FM_OK;
@@ -1264,12 +1344,8 @@ int kernels_init(fm_ctx* c) {
   FM_CUDA(cudaFuncSetAttribute(k_zmix<double, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<float, double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<float, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  FM_CUDA(cudaFuncSetAttribute(k_ysolve1<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  FM_CUDA(cudaFuncSetAttribute(k_ysolve1<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  FM_CUDA(cudaFuncSetAttribute(k_ysolve<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_ysolve<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_ysolve<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  FM_CUDA(cudaFuncSetAttribute(k_ysolve<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_ysolve<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_ysolve<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   return tc_kernels_init();

@@ -558,7 +558,7 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       cp.lmul_off[il] = lo;
       cp.piv_off[il] = po;
       bo += (int64_t)n * (2 * kl + 1) * nx;
-      lo += (int64_t)n * kl * nx;
+      lo += (int64_t)n * (kl + 1) * nx;
       po += (int64_t)n * nx;
     }
     cp.band_total = bo;
@@ -571,7 +571,6 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
     if ((rc = upload(c, (void**)&cp.d_piv_off, cp.piv_off.data(), nl * sizeof(int64_t)))) return rc;
     if ((rc = dev_alloc(c, (void**)&cp.yU, bo * 8))) return rc;
     if ((rc = dev_alloc(c, (void**)&cp.yL, lo * 8))) return rc;
-    if ((rc = dev_alloc(c, (void**)&cp.yP, po))) return rc;
     if ((rc = dev_alloc(c, (void**)&cp.yU32, bo * 4))) return rc;
     if ((rc = dev_alloc(c, (void**)&cp.yL32, lo * 4))) return rc;
     if (nM == 1) {
@@ -629,7 +628,7 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
     }
     const double nl = nM + nz - 1;
     bytes += 2.0 * nM * nz * nz * 12.0 + 2.0 * nl * nx * nx * 12.0;     // z and x decompositions
-    double bo = 0.0, lo = 0.0, po = 0.0;                                 // banded y factors
+    double bo = 0.0, lo = 0.0;                                           // banded y factors
     for (int il = 0; il < (int)nl; ++il) {
       const int l = M0 + il;
       int cnt = 0;
@@ -639,10 +638,9 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
       }
       const double n = cnt * ny, kl = (cnt == 1) ? 2 : 2 * cnt + 1;
       bo += n * (2 * kl + 1) * nx;
-      lo += n * kl * nx;
-      po += n * nx;
+      lo += n * (kl + 1) * nx;
     }
-    bytes += bo * 12.0 + lo * 12.0 + po;
+    bytes += bo * 12.0 + lo * 12.0;
     if (nM == 1) bytes += 2.0 * nl * ny * ny * 12.0 + nl * (nx + ny) * 20.0;  // per-l y diagonalisation
   }
   const double m = o->restart_m, ncv = o->ncv, n = (double)N;
@@ -665,7 +663,6 @@ int setup_shift(fm_ctx* c, double Estar) {
   for (auto& cp : c->comps) {
     const int nx = cp.nx, ny = cp.ny;
     std::vector<double> U((size_t)cp.band_total), L((size_t)cp.lmul_total);
-    std::vector<unsigned char> P((size_t)cp.piv_total);
     std::vector<double> vh(ny);
     for (int j = 0; j < ny; ++j) vh[j] = vhat(c, cp.label, cp.ay.pts[j], cp.Ry);
     std::vector<int> bad(cp.nl, 0);
@@ -702,13 +699,15 @@ int setup_shift(fm_ctx* c, double Estar) {
           bad[il] = 1;
           return;
         }
+        // per row r: U[r][0] = 1 / pivot, U[r][1..wu) the upper band; L[r][0] = pivot offset,
+        // L[r][1..kl] = multipliers
         double* Ug = &U[cpp->band_off[il]];
         double* Lg = &L[cpp->lmul_off[il]];
-        unsigned char* Pg = &P[cpp->piv_off[il]];
         for (int r = 0; r < n; ++r) {
-          for (int d = 0; d < wu; ++d) Ug[((size_t)r * wu + d) * nx + ix] = B[(size_t)r * wb + kl + d];
-          for (int d = 0; d < kl; ++d) Lg[((size_t)r * kl + d) * nx + ix] = Lm[(size_t)r * kl + d];
-          Pg[(size_t)r * nx + ix] = (unsigned char)(piv[r] - r);
+          Ug[((size_t)r * wu) * nx + ix] = 1.0 / B[(size_t)r * wb + kl];  // reciprocal of the pivot
+          for (int d = 1; d < wu; ++d) Ug[((size_t)r * wu + d) * nx + ix] = B[(size_t)r * wb + kl + d];
+          Lg[((size_t)r * (kl + 1)) * nx + ix] = (double)(piv[r] - r);
+          for (int d = 0; d < kl; ++d) Lg[((size_t)r * (kl + 1) + d + 1) * nx + ix] = Lm[(size_t)r * kl + d];
         }
       }
     });
@@ -716,7 +715,6 @@ int setup_shift(fm_ctx* c, double Estar) {
       if (b) return FM_ERR_NUMERIC;
     FM_CUDA(cudaMemcpyAsync(cp.yU, U.data(), U.size() * 8, cudaMemcpyHostToDevice, c->stream));
     FM_CUDA(cudaMemcpyAsync(cp.yL, L.data(), L.size() * 8, cudaMemcpyHostToDevice, c->stream));
-    FM_CUDA(cudaMemcpyAsync(cp.yP, P.data(), P.size(), cudaMemcpyHostToDevice, c->stream));
     std::vector<float> U32(U.begin(), U.end()), L32(L.begin(), L.end());
     FM_CUDA(cudaMemcpyAsync(cp.yU32, U32.data(), U32.size() * 4, cudaMemcpyHostToDevice, c->stream));
     FM_CUDA(cudaMemcpyAsync(cp.yL32, L32.data(), L32.size() * 4, cudaMemcpyHostToDevice, c->stream));

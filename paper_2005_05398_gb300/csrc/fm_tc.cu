@@ -534,10 +534,11 @@ int zstage(fm_ctx* c, const Comp& cp, const float* W, const TI* in, TO* out) {
 
 }  // namespace
 
-// y = P^{-1} x through the tensor-core chain (float32 stage buffers t32 / u32).  The banded y
-// solves (n_M > 1, or when chosen) run on u[slab][j][i] through the given callback.
+// Front half of y = P^{-1} x through the tensor-core chain (float32 stage buffers t32 / u32):
+// z forward, x forward and, for the per-l diagonalised y stage, both y products.  The result is
+// left in u[slab][j][i]; the banded y solves (when not diagonalised) then work in place there.
 template <typename TIO>
-int precond_tc(fm_ctx* c, Comp& cp, const TIO* x, TIO* y, bool ydiag, int (*ysolve)(fm_ctx*, Comp&)) {
+int precond_tc_front(fm_ctx* c, Comp& cp, const TIO* x, bool ydiag) {
   int rc;
   float* t = c->t32 + cp.off;
   float* u = c->u32 + cp.off;
@@ -550,16 +551,24 @@ int precond_tc(fm_ctx* c, Comp& cp, const TIO* x, TIO* y, bool ydiag, int (*ysol
     if ((rc = tc_stage(c, cp, cp.tm[4], cp.tm[6], nx, ny, ny, false, t, cp.dLx2, cp.dLy2, FM_KERNEL_YSOLVE))) return rc;
     // y inverse: rows i, K = j -> u[slab][j][i]
     if ((rc = tc_stage(c, cp, cp.tm[5], cp.tm[7], nx, ny, ny, true, u, nullptr, nullptr, FM_KERNEL_YSOLVE))) return rc;
-  } else {
-    if ((rc = ysolve(c, cp))) return rc;
   }
-  // x inverse: rows j, K = i -> t[slab][i][j]
+  return FM_OK;
+}
+
+// Back half: x inverse (rows j, K = i -> t[slab][i][j]) and z inverse into y.
+template <typename TIO>
+int precond_tc_back(fm_ctx* c, Comp& cp, TIO* y) {
+  int rc;
+  float* t = c->t32 + cp.off;
+  const int nx = cp.nx, ny = cp.ny;
   if ((rc = tc_stage(c, cp, cp.tm[1], cp.tm[3], ny, nx, nx, true, t, nullptr, nullptr, FM_KERNEL_XMIX))) return rc;
   return zstage<float, TIO, false>(c, cp, cp.Wz32, c->t32, y);
 }
 
-template int precond_tc<double>(fm_ctx*, Comp&, const double*, double*, bool, int (*)(fm_ctx*, Comp&));
-template int precond_tc<float>(fm_ctx*, Comp&, const float*, float*, bool, int (*)(fm_ctx*, Comp&));
+template int precond_tc_front<double>(fm_ctx*, Comp&, const double*, bool);
+template int precond_tc_front<float>(fm_ctx*, Comp&, const float*, bool);
+template int precond_tc_back<double>(fm_ctx*, Comp&, double*);
+template int precond_tc_back<float>(fm_ctx*, Comp&, float*);
 
 int tc_check(fm_ctx* c) {
   if (!c->tc_active || !c->tc_err) return FM_OK;
