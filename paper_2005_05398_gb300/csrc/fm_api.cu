@@ -48,38 +48,9 @@ static int nrm2(fm_ctx* c, const double* v, double* out) {
   return rc;
 }
 
-// Classical Gram-Schmidt of w against the orthonormal V[0..nv) with the DGKS test: a second pass
-// runs only when the first removed more than 1 - 1/sqrt(2) of the norm (w lay close to span V).
-// h receives the coefficients, *nrm the norm of the orthogonalised w.
-static int orthogonalize(fm_ctx* c, const double* V, int nv, double* w, double* h, double* nrm) {
-  std::vector<double> h1(nv + 1), h2(nv + 1);
-  int rc;
-  if ((rc = dot_many_x(c, V, c->N, nv, w, w, h1.data()))) return rc;  // V^T w and w.w
-  const double before = std::sqrt(std::max(h1[nv], 0.0));
-  double n2;
-  if ((rc = axpy_many_norm(c, V, c->N, nv, h1.data(), w, &n2))) return rc;
-  for (int i = 0; i < nv; ++i) h[i] = h1[i];
-  double after = std::sqrt(std::max(n2, 0.0));
-  if (after < 0.7071067811865476 * before) {
-    if ((rc = dot_many(c, V, c->N, nv, w, h2.data()))) return rc;
-    if ((rc = axpy_many_norm(c, V, c->N, nv, h2.data(), w, &n2))) return rc;
-    for (int i = 0; i < nv; ++i) h[i] += h2[i];
-    after = std::sqrt(std::max(n2, 0.0));
-  }
-  *nrm = after;
-  return FM_OK;
-}
-
 // z <- P_t^{-1}-correction of z = P^{-1} v:  z -= (W - U) (U^T W)^{-1} (U^T z)
 static int apply_tuning(fm_ctx* c, double* z) {
-  const int k = c->n_tune;
-  if (k == 0) return FM_OK;
-  std::vector<double> a(k), b(k, 0.0);
-  int rc;
-  if ((rc = dot_many(c, c->tuneU, c->N, k, z, a.data()))) return rc;
-  for (int i = 0; i < k; ++i)
-    for (int j = 0; j < k; ++j) b[i] += c->tuneGinv[(size_t)i * k + j] * a[j];
-  return axpy_many(c, c->tuneWU, c->N, k, b.data(), z, -1.0);
+  return tuning_correct(c, c->tuneU, c->tuneWU, c->tuneG_dev, c->n_tune, z);
 }
 
 // Tune the preconditioner to the columns of U (device, orthonormal, k <= 8): W = P^{-1} (H - E S) U.
@@ -101,6 +72,7 @@ static int set_tuning(fm_ctx* c, double E, const double* U, int k) {
   }
   c->tuneGinv.assign((size_t)k * k, 0.0);
   if (!fmh::invert(k, G.data(), c->tuneGinv.data())) return FM_OK;  // singular: leave untuned
+  FM_CUDA(cudaMemcpy(c->tuneG_dev, c->tuneGinv.data(), (size_t)k * k * sizeof(double), cudaMemcpyHostToDevice));
   c->n_tune = k;
   return FM_OK;
 }
@@ -150,8 +122,8 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
       if ((rc = launch_precond(c, Vj, Zj))) return rc;
       if ((rc = apply_tuning(c, Zj))) return rc;
       if ((rc = launch_apply(c, E, Zj, c->w, false))) return rc;
-      double hn;
-      if ((rc = orthogonalize(c, c->V, j + 1, c->w, h.data(), &hn))) return rc;
+      double hn;  // CGS2 writes the next basis vector V[j+1] = (w - V h) / hn
+      if ((rc = gs_cgs2(c, c->V, j + 1, c->w, c->V + (int64_t)(j + 1) * N, h.data(), &hn))) return rc;
       if (!std::isfinite(hn)) return FM_ERR_BREAKDOWN;
       for (int i = 0; i < j; ++i) {  // previous Givens rotations
         const double t = cs[i] * h[i] + sn[i] * h[i + 1];
@@ -168,7 +140,6 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
       ++total;
       jdone = j + 1;
       if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0) break;
-      if ((rc = scale_copy(c, c->w, 1.0 / hn, c->V + (int64_t)(j + 1) * N))) return rc;
     }
     for (int i = jdone - 1; i >= 0; --i) {  // R y = g
       double s = g[i];
@@ -449,7 +420,7 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
   if ((rc = setup_host(c, grids, n_grids))) return fail(rc);
   const int64_t N = c->N;
   const int m = o.restart_m;
-  c->red_blocks = 2 * 152;
+  c->red_blocks = 4 * 152;  // reduction blocks: four per SM
   if ((rc = dev_alloc(c, (void**)&c->P, N * 8)) || (rc = dev_alloc(c, (void**)&c->Q, N * 8)) ||
       (rc = dev_alloc(c, (void**)&c->R, N * 8)) || (rc = dev_alloc(c, (void**)&c->t64, N * 8)) ||
       (rc = dev_alloc(c, (void**)&c->u64, N * 8)) || (rc = dev_alloc(c, (void**)&c->t32, N * 4)) ||
@@ -460,8 +431,10 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
       (rc = dev_alloc(c, (void**)&c->AV, (size_t)(o.ncv + 1) * N * 8)) ||
       (rc = dev_alloc(c, (void**)&c->tmpN, N * 8)) || (rc = dev_alloc(c, (void**)&c->tmpN2, N * 8)) ||
       (rc = dev_alloc(c, (void**)&c->tmpN3, N * 8)) || (rc = dev_alloc(c, (void**)&c->tuneU, (size_t)8 * N * 8)) ||
-      (rc = dev_alloc(c, (void**)&c->tuneWU, (size_t)8 * N * 8)))
+      (rc = dev_alloc(c, (void**)&c->tuneWU, (size_t)8 * N * 8)) || (rc = dev_alloc(c, (void**)&c->gsd, 4096 * 8)) ||
+      (rc = dev_alloc(c, (void**)&c->gs_cnt, 256)) || (rc = dev_alloc(c, (void**)&c->tuneG_dev, 64 * 8)))
     return fail(rc);
+  if (cudaMemset(c->gs_cnt, 0, 256) != cudaSuccess) return fail(FM_ERR_CUDA);
   if (cudaMallocHost((void**)&c->red_host, 8192 * 8) != cudaSuccess) return fail(FM_ERR_OOM);
   if (o.precision == FM_PREC_MIXED) {  // float32 Krylov workspace of the mixed-precision solves
     if ((rc = dev_alloc(c, (void**)&c->V32, (size_t)(m + 1) * N * 4)) || (rc = dev_alloc(c, (void**)&c->Z32, (size_t)m * N * 4)) ||
@@ -678,12 +651,10 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
       worst_inner = std::max(worst_inner, res);
       std::vector<double> h(j + 1);
       double hn;
-      if ((rc = orthogonalize(c, V, j + 1, w, h.data(), &hn))) return rc;
+      if ((rc = gs_cgs2(c, V, j + 1, w, w, h.data(), &hn))) return rc;  // w <- (w - V h) / hn
       if (!std::isfinite(hn)) return FM_ERR_BREAKDOWN;
       for (int i = 0; i <= j; ++i) G[(size_t)i * m + j] = h[i];
       G[(size_t)(j + 1) * m + j] = hn;
-      if (hn > 0.0)
-        if ((rc = scale_copy(c, w, 1.0 / hn, w))) return rc;
       nsz = j + 1;
       if (nsz < k) continue;
       // Ritz pairs of the nsz x nsz projected matrix

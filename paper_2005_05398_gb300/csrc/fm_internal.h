@@ -139,7 +139,10 @@ struct fm_ctx {
   double* Z = nullptr;           // FGMRES preconditioned directions [m][N]
   double* w = nullptr;           // [N]
   double* r = nullptr;           // [N]
-  double* red = nullptr;         // reduction scratch
+  double* red = nullptr;         // reduction scratch (per-block partial sums)
+  double* gsd = nullptr;         // Gram-Schmidt coefficients and norms kept on the device
+  unsigned* gs_cnt = nullptr;    // arrival counter of the last-block reductions
+  double* tuneG_dev = nullptr;   // (U^T W)^{-1} of the tuned preconditioner, on the device
   double* red_host = nullptr;    // pinned
   int red_blocks = 0;
   // eigen workspace
@@ -195,6 +198,9 @@ int dot_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, d
 int dot_many_x(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_host);
 int axpy_many_norm(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double* nrm2_out);
 int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double sign);
+int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_dev);
+int gs_cgs2(fm_ctx* c, const double* V, int nv, double* w, double* vout, double* h, double* hn);
+int tuning_correct(fm_ctx* c, const double* U, const double* WmU, const double* Gdev, int k, double* z);
 int scale_copy(fm_ctx* c, const double* x, double a, double* y);   // y = a x
 int axpby(fm_ctx* c, double a, const double* x, double b, double* y);  // y = a x + b y
 int fill_normal(fm_ctx* c, double* x, uint64_t seed);

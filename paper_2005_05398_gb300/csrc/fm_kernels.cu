@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 #include <vector>
 
@@ -565,6 +566,7 @@ __global__ void __launch_bounds__(LPB) k_ysolve(const YBatch<T> yb, int R, int W
 // Krylov helpers
 // ---------------------------------------------------------------------------
 constexpr int kRedThreads = 256;
+constexpr int kGsMaxVec = 264;  // basis vectors one Gram-Schmidt pass takes (restart length <= 256)
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -578,12 +580,37 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// Called by every thread of every block at the end of a reduction kernel, after each block has
+// written partial[j * nb + b] (j < nv, nb = gridDim.x): the block that arrives last sums the
+// partials in a fixed order (lane-strided, then a shuffle tree) into out[j] and resets the
+// counter, so the reduction needs neither a second kernel nor a host round trip.
+__device__ void last_block_reduce(const double* partial, int nv, unsigned* counter, double* out) {
+  __shared__ unsigned ticket;
+  const int nb = (int)gridDim.x;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  if (ticket != (unsigned)(nb - 1)) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  for (int j = wid; j < nv; j += nw) {
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += __ldcg(&partial[(int64_t)j * nb + b]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[j] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
 // partial[j][block] = sum over this block's slice of V[j] . w  (j < nv), and for j = nv, when
 // 'extra' is given, extra . w.  The vectors are taken eight at a time so that every thread keeps
 // eight independent loads in flight per element; the eight partial sums are reduced together.
 __global__ void __launch_bounds__(kRedThreads) k_dot_many(const double* __restrict__ V, int64_t ldv, int nv,
                                                          const double* __restrict__ w, int64_t n,
-                                                         double* __restrict__ partial, const double* __restrict__ extra) {
+                                                         double* __restrict__ partial, const double* __restrict__ extra,
+                                                         unsigned* counter, double* __restrict__ out) {
   constexpr int JT = 8;
   __shared__ double sh[JT][kRedThreads / 32];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -622,12 +649,14 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_many(const double* __restri
     }
     __syncthreads();
   }
+  last_block_reduce(partial, nt, counter, out);
 }
 
 // float32 vectors: partial[j][block] (float64) = V[j] . w over the block's slice (eight vectors per pass)
 __global__ void __launch_bounds__(kRedThreads) k_dot_many32(const float* __restrict__ V, int64_t ldv, int nv,
                                                            const float* __restrict__ w, int64_t n,
-                                                           double* __restrict__ partial) {
+                                                           double* __restrict__ partial, unsigned* counter,
+                                                           double* __restrict__ out) {
   constexpr int JT = 8;
   __shared__ double sh[JT][kRedThreads / 32];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -659,13 +688,15 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_many32(const float* __restr
     }
     __syncthreads();
   }
+  last_block_reduce(partial, nv, counter, out);
 }
 
 // float32: w += sign * sum_j h[j] V[j], partial[block] = sum of the new w^2 (float64)
 __global__ void __launch_bounds__(kRedThreads) k_axpy_many_norm32(const float* __restrict__ V, int64_t ldv, int nv,
                                                                  const float* __restrict__ h, float sign,
                                                                  float* __restrict__ w, int64_t n,
-                                                                 double* __restrict__ partial) {
+                                                                 double* __restrict__ partial, unsigned* counter,
+                                                                 double* __restrict__ out) {
   __shared__ double sh[32];
   float acc = 0.0f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -684,6 +715,7 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_many_norm32(const float* _
   }
   const double a = block_sum((double)acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = a;
+  last_block_reduce(partial, 1, counter, out);
 }
 
 // y32 = (float)(a * x64)
@@ -719,7 +751,8 @@ __global__ void k_dot_finish(const double* __restrict__ partial, int nb, int nv,
 __global__ void __launch_bounds__(kRedThreads) k_axpy_many_norm(const double* __restrict__ V, int64_t ldv, int nv,
                                                                const double* __restrict__ h, double sign,
                                                                double* __restrict__ w, int64_t n,
-                                                               double* __restrict__ partial) {
+                                                               double* __restrict__ partial, unsigned* counter,
+                                                               double* __restrict__ out) {
   __shared__ double sh[32];
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -738,6 +771,67 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_many_norm(const double* __
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  last_block_reduce(partial, 1, counter, out);
+}
+
+// One pass of classical Gram-Schmidt with the coefficients on the device:
+//   w' = w - sum_j c_j V_j,  c = h, or c = G a (G k x k row-major, a of length k) when G is given.
+// MODE 0: w <- w', out[0] = ||w'||^2.
+// MODE 1 (closing pass): nu^2 = nrm2_prev - |c|^2 (the norm of w' by Pythagoras, V orthonormal and
+// c = V^T w), vout <- w' / nu (0 when nu^2 <= 0), out[0] = ||vout||^2 (1 up to rounding), out[1] = nu.
+template <int MODE>
+__global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restrict__ V, int64_t ldv, int nv,
+                                                        const double* __restrict__ h, const double* __restrict__ G,
+                                                        const double* __restrict__ a, double* w, double* vout,
+                                                        int64_t n, double* __restrict__ partial, unsigned* counter,
+                                                        double* __restrict__ out, const double* __restrict__ nrm2_prev) {
+  __shared__ double cs[kGsMaxVec];
+  __shared__ double sh[32];
+  __shared__ double inv_nu;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    double cj;
+    if (G) {
+      cj = 0.0;
+      for (int q = 0; q < nv; ++q) cj = fma(G[(int64_t)j * nv + q], a[q], cj);
+    } else {
+      cj = h[j];
+    }
+    cs[j] = cj;
+  }
+  __syncthreads();
+  if (MODE == 1 && threadIdx.x == 0) {
+    double c2 = 0.0;
+    for (int j = 0; j < nv; ++j) c2 = fma(cs[j], cs[j], c2);
+    const double nu2 = *nrm2_prev - c2;
+    const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
+    inv_nu = nu > 0.0 ? 1.0 / nu : 0.0;
+    if (blockIdx.x == 0) out[1] = nu;
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int j = 0;
+    for (; j + 3 < nv; j += 4) {
+      s0 = fma(cs[j], V[(int64_t)j * ldv + i], s0);
+      s1 = fma(cs[j + 1], V[(int64_t)(j + 1) * ldv + i], s1);
+      s2 = fma(cs[j + 2], V[(int64_t)(j + 2) * ldv + i], s2);
+      s3 = fma(cs[j + 3], V[(int64_t)(j + 3) * ldv + i], s3);
+    }
+    for (; j < nv; ++j) s0 = fma(cs[j], V[(int64_t)j * ldv + i], s0);
+    const double v = w[i] - ((s0 + s1) + (s2 + s3));
+    if (MODE == 0) {
+      w[i] = v;
+      acc = fma(v, v, acc);
+    } else {
+      const double o = v * inv_nu;
+      vout[i] = o;
+      acc = fma(o, o, acc);
+    }
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  last_block_reduce(partial, 1, counter, out);
 }
 
 // w += sign * sum_j h[j] V[j]
@@ -1102,22 +1196,26 @@ int dot_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, d
 }
 
 int dot_many_x(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_host) {
+  const int nt = nv + (extra ? 1 : 0);
+  int rc;
+  if ((rc = dot_many_dev(c, V, ldv, nv, w, extra, c->gsd))) return rc;
+  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  std::memcpy(h_host, c->red_host, nt * sizeof(double));
+  return prof_harvest(c);
+}
+
+// h_dev[j] = V[j] . w (j < nv), h_dev[nv] = extra . w when extra is given; stays on the device
+int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_dev) {
   const int nb = c->red_blocks;
   const int nt = nv + (extra ? 1 : 0);
-  {
-    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_many<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra);
-    prof_end(c, tk_, 2.0 * nt * (double)c->N, (nt + 1.0) * 8.0 * (double)c->N);
-  }
-  {
-    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_finish<<<nt, 32, 0, c->stream>>>(c->red, nb, nt, c->red + (int64_t)nb * 256);
-    prof_end(c, tk_, 0.0, 0.0);
-  }
-  c->launches += 2;
-  FM_CUDA(cudaMemcpyAsync(h_host, c->red + (int64_t)nb * 256, nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  FM_CUDA(cudaStreamSynchronize(c->stream));
-  return prof_harvest(c);
+  if (nt > kGsMaxVec) return FM_ERR_ARG;
+  const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+  k_dot_many<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
+  prof_end(c, tk_, 2.0 * nt * (double)c->N, (nt + 1.0) * 8.0 * (double)c->N);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
 }
 
 int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double sign) {
@@ -1135,24 +1233,89 @@ int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_h
 
 // w -= V h (h on the host), returns ||w||^2 after the update
 int axpy_many_norm(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double* nrm2_out) {
-  double* hd = c->red + (int64_t)c->red_blocks * 256 + 512;
-  FM_CUDA(cudaMemcpyAsync(hd, h_host, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  double* hd = c->gsd + 2 * kGsMaxVec;
+  if (nv > kGsMaxVec) return FM_ERR_ARG;
+  std::memcpy(c->red_host, h_host, nv * sizeof(double));
+  FM_CUDA(cudaMemcpyAsync(hd, c->red_host, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   const int nb = 4 * c->red_blocks;  // grid-stride blocks; one partial each
   {
     const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
-    k_axpy_many_norm<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, hd, -1.0, w, c->N, c->red);
+    k_axpy_many_norm<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, hd, -1.0, w, c->N, c->red, c->gs_cnt,
+                                                        c->gsd + 3 * kGsMaxVec);
     prof_end(c, tk_, (2.0 * nv + 2.0) * (double)c->N, (nv + 2.0) * 8.0 * (double)c->N);
   }
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd + 3 * kGsMaxVec, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  *nrm2_out = c->red_host[0];
+  return prof_harvest(c);
+}
+
+// Classical Gram-Schmidt with one re-orthogonalisation (CGS2) of w against the orthonormal
+// V[0..nv), all coefficients kept on the device:
+//   h1 = V^T w;  w' = w - V h1;  h2 = V^T w';  vout = (w' - V h2) / nu,  nu^2 = ||w'||^2 - |h2|^2.
+// Four launches and one host synchronisation.  On return h = h1 + h2 and *hn = ||w' - V h2||
+// (nu times the measured norm of vout, which is renormalised if it is not 1 to rounding);
+// *hn = 0 when w lies in span V to rounding (vout is then 0).  w is overwritten; vout may be w.
+int gs_cgs2(fm_ctx* c, const double* V, int nv, double* w, double* vout, double* h, double* hn) {
+  if (nv < 1 || nv > kGsMaxVec) return FM_ERR_ARG;
+  const int64_t N = c->N;
+  double* h1 = c->gsd;
+  double* h2 = c->gsd + kGsMaxVec;
+  double* sc = c->gsd + 3 * kGsMaxVec;  // [0] ||w'||^2, [1] ||vout||^2, [2] nu
+  const int nb2 = 4 * c->red_blocks;
+  int rc;
+  if ((rc = dot_many_dev(c, V, N, nv, w, nullptr, h1))) return rc;
   {
-    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_finish<<<1, 32, 0, c->stream>>>(c->red, nb, 1, c->red + (int64_t)c->red_blocks * 256);
-    prof_end(c, tk_, 0.0, 0.0);
+    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+    k_gs_axpy<0><<<nb2, kRedThreads, 0, c->stream>>>(V, N, nv, h1, nullptr, nullptr, w, nullptr, N, c->red, c->gs_cnt,
+                                                     sc, nullptr);
+    prof_end(c, tk_, (2.0 * nv + 2.0) * (double)N, (nv + 2.0) * 8.0 * (double)N);
+  }
+  if ((rc = dot_many_dev(c, V, N, nv, w, nullptr, h2))) return rc;
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+    k_gs_axpy<1><<<nb2, kRedThreads, 0, c->stream>>>(V, N, nv, h2, nullptr, nullptr, w, vout, N, c->red, c->gs_cnt,
+                                                     sc + 1, sc);
+    prof_end(c, tk_, (2.0 * nv + 2.0) * (double)N, (nv + 2.0) * 8.0 * (double)N);
   }
   c->launches += 2;
   FM_CUDA(cudaGetLastError());
-  FM_CUDA(cudaMemcpyAsync(nrm2_out, c->red + (int64_t)c->red_blocks * 256, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  // one read-back: h1, h2 and the three scalars
+  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, (3 * kGsMaxVec + 3) * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
   FM_CUDA(cudaStreamSynchronize(c->stream));
+  const double* hh = c->red_host;
+  for (int i = 0; i < nv; ++i) h[i] = hh[i] + hh[kGsMaxVec + i];
+  const double vn2 = hh[3 * kGsMaxVec + 1], nu = hh[3 * kGsMaxVec + 2];
+  if (!(nu > 0.0) || !(vn2 > 0.0)) {
+    *hn = std::isfinite(nu) && std::isfinite(vn2) ? 0.0 : nu + vn2;
+    return prof_harvest(c);
+  }
+  const double vn = std::sqrt(vn2);
+  *hn = nu * vn;
+  if (std::fabs(vn - 1.0) > 1e-12)  // Pythagoras lost digits: rescale to unit norm
+    if ((rc = scale_copy(c, vout, 1.0 / vn, vout))) return rc;
   return prof_harvest(c);
+}
+
+// z <- z - (W - U) G (U^T z) for the tuned preconditioner, G = (U^T W)^{-1} (k x k, on the device);
+// no host synchronisation
+int tuning_correct(fm_ctx* c, const double* U, const double* WmU, const double* Gdev, int k, double* z) {
+  if (k <= 0) return FM_OK;
+  if (k > kGsMaxVec) return FM_ERR_ARG;
+  double* a = c->gsd + 2 * kGsMaxVec;
+  int rc;
+  if ((rc = dot_many_dev(c, U, c->N, k, z, nullptr, a))) return rc;
+  const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+  k_gs_axpy<0><<<4 * c->red_blocks, kRedThreads, 0, c->stream>>>(WmU, c->N, k, nullptr, Gdev, a, z, nullptr, c->N,
+                                                                 c->red, c->gs_cnt, c->gsd + 3 * kGsMaxVec + 4,
+                                                                 nullptr);
+  prof_end(c, tk_, 2.0 * k * (double)c->N, (k + 2.0) * 8.0 * (double)c->N);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
 }
 
 int scale_copy(fm_ctx* c, const double* x, double a, double* y) {
@@ -1265,20 +1428,17 @@ int prof_harvest(fm_ctx* c) {
 
 int dot_many32(fm_ctx* c, const float* V, int64_t ldv, int nv, const float* w, double* h_host) {
   const int nb = c->red_blocks;
+  if (nv > kGsMaxVec) return FM_ERR_ARG;
   {
     const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_many32<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red);
+    k_dot_many32<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, c->gs_cnt, c->gsd);
     prof_end(c, tk_, 2.0 * nv * (double)c->N, (nv + 1.0) * 4.0 * (double)c->N);
   }
-  {
-    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_finish<<<nv, 32, 0, c->stream>>>(c->red, nb, nv, c->red + (int64_t)nb * 256);
-    prof_end(c, tk_, 0.0, 0.0);
-  }
-  c->launches += 2;
+  c->launches++;
   FM_CUDA(cudaGetLastError());
-  FM_CUDA(cudaMemcpyAsync(h_host, c->red + (int64_t)nb * 256, nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   FM_CUDA(cudaStreamSynchronize(c->stream));
+  std::memcpy(h_host, c->red_host, nv * sizeof(double));
   return prof_harvest(c);
 }
 
@@ -1290,20 +1450,16 @@ int axpy_many_norm32(fm_ctx* c, const float* V, int64_t ldv, int nv, const doubl
   const int nb = 4 * c->red_blocks;
   {
     const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
-    k_axpy_many_norm32<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, hd, sign, w, c->N, c->red);
+    k_axpy_many_norm32<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, hd, sign, w, c->N, c->red, c->gs_cnt,
+                                                          c->gsd + 3 * kGsMaxVec);
     prof_end(c, tk_, (2.0 * nv + 2.0) * (double)c->N, (nv + 2.0) * 4.0 * (double)c->N);
   }
-  {
-    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_finish<<<1, 32, 0, c->stream>>>(c->red, nb, 1, c->red + (int64_t)c->red_blocks * 256);
-    prof_end(c, tk_, 0.0, 0.0);
-  }
-  c->launches += 2;
+  c->launches++;
   FM_CUDA(cudaGetLastError());
   if (nrm2_out) {
-    FM_CUDA(cudaMemcpyAsync(nrm2_out, c->red + (int64_t)c->red_blocks * 256, sizeof(double), cudaMemcpyDeviceToHost,
-                            c->stream));
+    FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd + 3 * kGsMaxVec, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     FM_CUDA(cudaStreamSynchronize(c->stream));
+    *nrm2_out = c->red_host[0];
     return prof_harvest(c);
   }
   return FM_OK;

@@ -647,7 +647,7 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
   bytes += n * 8.0 * (5 + 2 + 3 + 16) + n * 4.0 * 2;                    // apply scratch, stage buffers, tuning
   bytes += n * 8.0 * ((m + 1) + std::max(m, ncv) + (ncv + 1));          // FGMRES and Arnoldi bases
   if (o->precision == FM_PREC_MIXED) bytes += n * 4.0 * ((m + 1) + m + 7);
-  bytes += (2.0 * 152 * 256 + 8192) * 8.0;
+  bytes += (4.0 * 152 * 256 + 8192 + 4096) * 8.0;
   *out = (int64_t)bytes;
   return FM_OK;
 }
