@@ -317,6 +317,77 @@ def run_kernel_loop(args):
     return 0
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+def run_serve(args):
+    """Independent requests through libfm's request loop: a saturated closed batch (throughput of
+    the batched workload, float32 preconditioner and plain float64), then Poisson arrival streams
+    at 0.5, 0.8 and 1.0 x the saturated rate (p50 / p99 latency, arrival to result)."""
+    import threading
+    import torch
+    from paper_2005_05398_gb300 import build, serve
+    from fm_inputs import request_mix
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    build.build()
+    mix = request_mix(args.requests, SEED_BASE + 5, scale=args.mix_scale)
+    total_free, total = torch.cuda.mem_get_info()
+    budget = int(0.9 * total)
+
+    def batch(precision):
+        srv = serve.Server(hbm_budget=budget, slots=args.slots)
+        t0 = time.perf_counter()
+        ids = [srv.submit(r["wl"], r["kind"], r["E"], k=r["k"], seed=r["seed"], precision=precision) for r in mix]
+        res = [srv.wait(i) for i in ids]
+        dt = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = [r["t_end_ms"] - r["t_submit_ms"] for r in res]
+        return {"precision": {0: "fp64", 1: "fp32", 2: "mixed"}[precision], "requests": len(res),
+                "makespan_s": dt, "requests_per_s": len(res) / dt,
+                "ok": sum(r["status"] == 0 for r in res), "not_converged": sum(r["status"] == -4 for r in res),
+                "iters": sum(r["iters"] for r in res), "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
+                "peak_busy": st["peak_busy"], "peak_gb": st["peak_in_use"] / 1e9}
+
+    def stream(rate, precision):
+        srv = serve.Server(hbm_budget=budget, slots=args.slots)
+        rng = np.random.default_rng(SEED_BASE + 9)
+        gaps = rng.exponential(1.0 / rate, size=len(mix))
+        ids = []
+
+        def feeder():
+            for r, g in zip(mix, gaps):
+                time.sleep(float(g))
+                ids.append(srv.submit(r["wl"], r["kind"], r["E"], k=r["k"], seed=r["seed"], precision=precision))
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        res = [srv.wait(i) for i in ids]
+        srv.close()
+        lat = [r["t_end_ms"] - r["t_submit_ms"] for r in res]
+        span = (max(r["t_end_ms"] for r in res) - min(r["t_submit_ms"] for r in res)) / 1e3
+        return {"offered_per_s": rate, "requests_per_s": len(res) / span, "p50_ms": _pct(lat, 50),
+                "p99_ms": _pct(lat, 99), "ok": sum(r["status"] == 0 for r in res)}
+
+    sat = batch(args.serve_precision)
+    out = {"metric": "served requests/s (fm_solve / fm_eigs mix, continuous batching)", "value": sat["requests_per_s"],
+           "unit": "requests/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic (seeded request mix)",
+           "config": {"workload": f"request mix ({args.mix_scale}): H-, He-like, Ps-; J, grids, E drawn per request",
+                      "requests": len(mix), "slots": args.slots, "hbm_budget_gb": budget / 1e9},
+           "saturated": sat}
+    if args.serve_fp64:
+        out["saturated_fp64"] = batch(0)
+    out["streams"] = [stream(f * sat["requests_per_s"], args.serve_precision) for f in (0.5, 0.8, 1.0)]
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,7 +405,15 @@ def main():
     ap.add_argument("--kernel-loop", choices=["apply", "precond", "solve"], default=None,
                     help="repeat one call --loops times on the workload (profiler captures)")
     ap.add_argument("--loops", type=int, default=5)
+    ap.add_argument("--serve", action="store_true", help="request-loop benchmark (batched and served workloads)")
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--mix-scale", default="full", choices=["full", "medium", "small"])
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serve-precision", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--serve-fp64", action="store_true", help="also time the batch with the float64 preconditioner")
     args = ap.parse_args()
+    if args.serve:
+        return run_serve(args)
     if args.kernel_loop:
         return run_kernel_loop(args)
     if args.impl == "reference":

@@ -83,3 +83,41 @@ def rand_vec(n, seed):
 
 
 SEED_BASE = 20050539
+
+
+# Independent-request mixes (batched and served workloads): per request a system drawn from
+# H-, He-like and Ps-, total momentum J (tau = +1), interval counts per radial axis and in z,
+# an energy, and what to compute (half linear solves with a N(0,1) right-hand side, half
+# nearest-eigenvalue solves).  Solves take E uniform in [-3, -0.2]; an eigen-request draws its
+# shift from the part of that range next to the system's bound and low box states, so that
+# shift-invert converges in a bounded number of Arnoldi steps.
+MIX_BOX = {"He": 40.0, "Hminus": 40.0, "Psminus": 80.0}
+MIX_EIG_SHIFT = {"He": (-3.0, -2.0), "Hminus": (-0.6, -0.45), "Psminus": (-0.3, -0.22)}
+MIX_SCALES = {
+    # name: (J range, radial interval range, z interval range)
+    "full": ((0, 4), (32, 128), (8, 24)),
+    "medium": ((0, 3), (16, 64), (4, 12)),
+    "small": ((0, 2), (8, 16), (3, 5)),
+}
+
+
+def request_mix(count, seed, scale="full", systems=("Hminus", "He", "Psminus")):
+    """Seeded list of request dicts {'wl', 'kind', 'E', 'k', 'seed'} (kind 'solve' or 'eigs')."""
+    rng = np.random.default_rng(seed)
+    (j_lo, j_hi), (r_lo, r_hi), (z_lo, z_hi) = MIX_SCALES[scale]
+    out = []
+    for i in range(int(count)):
+        system = systems[int(rng.integers(len(systems)))]
+        J = int(rng.integers(j_lo, j_hi + 1))
+        nx, ny = (int(v) for v in rng.integers(r_lo, r_hi + 1, size=2))
+        nz = int(rng.integers(z_lo, z_hi + 1))
+        kind = "solve" if i % 2 == 0 else "eigs"
+        if kind == "solve":
+            E = float(rng.uniform(-3.0, -0.2))
+        else:
+            E = float(rng.uniform(*MIX_EIG_SHIFT[system]))
+        Rb = MIX_BOX[system]
+        wl = make_workload(system, J, nint=(nx, ny, nz), R=(Rb, Rb), shift=E, k=1,
+                           name=f"{system}_J{J}_{nx}x{ny}x{nz}")
+        out.append({"wl": wl, "kind": kind, "E": E, "k": 1, "seed": int(seed) * 1000 + i})
+    return out

@@ -257,6 +257,71 @@ int fm_profile(fm_ctx* ctx, int enable);
  * entries.  Synchronises the stream. */
 int fm_profile_read(fm_ctx* ctx, double* ms, int64_t* launches, double* flops, double* bytes);
 
+/* ---------------------------------------------------------------------------------------
+ * Request loop for independent problems (serving).  The paper solves one problem at a time;
+ * this part has no counterpart there.  A server owns `slots` worker threads, each with its
+ * own CUDA stream.  A submitted request waits in arrival order until a slot is free and its
+ * device working set (fm_estimate_bytes plus the request's two vectors) fits the HBM budget
+ * next to the requests already running; a request that has been passed over 8 times by
+ * later, smaller ones blocks further passing until it is admitted.  Each admitted request
+ * gets its own context (1D factor sets, Krylov state) on the device for its lifetime, so
+ * the requests in flight overlap on the GPU and their results do not depend on the mix
+ * (every kernel reduces in a fixed order).
+ * ------------------------------------------------------------------------------------- */
+typedef struct fm_server fm_server;
+
+enum { FM_REQ_SOLVE = 0, FM_REQ_EIGS = 1 };
+enum { FM_SERVER_DRY_RUN = 1 }; /* host only: requests "run" for sim_ms, no CUDA call is made */
+
+/* One request: a problem (one grid for every solved component) and what to compute.
+ * kind FM_REQ_SOLVE: (H - E S) x = b with b ~ N(0,1) drawn from `seed` on the device;
+ * FM_REQ_EIGS: the k (1..8) eigenvalues nearest E, Arnoldi start ~ N(0,1) from `seed`.
+ * out_host (optional, host memory the caller keeps alive until fm_server_wait returns)
+ * receives x (n values) or the k eigenvectors (k n values). */
+typedef struct {
+  fm_system sys;
+  fm_grid grid;
+  fm_splitting split;
+  int kind;
+  double E;
+  int k;
+  uint64_t seed;
+  int precision;     /* FM_PREC_* */
+  double sim_ms;     /* FM_SERVER_DRY_RUN: simulated run time of the request */
+  double* out_host;
+} fm_request;
+
+/* Outcome of one request.  Times in ms on the server's steady clock (0 = creation). */
+typedef struct {
+  int status;         /* fm_status of the solve or eigen-solve */
+  int iters;          /* FGMRES iterations */
+  int64_t n;          /* unknowns */
+  int64_t bytes;      /* device bytes the request was admitted with */
+  double evals[8];    /* FM_REQ_EIGS: eigenvalues, nearest first */
+  double resid;       /* relative residual (solve) or largest eigen-residual (eigs) */
+  double out_norm;    /* ||x|| (solve); 1 per eigenvector (eigs) */
+  double t_submit_ms, t_start_ms, t_end_ms;
+} fm_result;
+
+/* hbm_budget <= 0: 90 % of the device memory (ignored with FM_SERVER_DRY_RUN, where it must be
+ * > 0).  slots in 1..64. */
+int fm_server_create(int device, int64_t hbm_budget, int slots, int flags, fm_server** out);
+
+/* Enqueue a request (copied); *id identifies it.  FM_ERR_OOM when the request alone exceeds the
+ * budget, FM_ERR_ARG for invalid requests (checked as fm_create and fm_eigs would). */
+int fm_server_submit(fm_server* s, const fm_request* r, int64_t* id);
+
+/* Block until request id has finished (timeout_ms < 0: no limit) and return its result once;
+ * FM_ERR_TIMEOUT when the limit passed first, FM_ERR_ARG for an unknown or collected id. */
+int fm_server_wait(fm_server* s, int64_t id, double timeout_ms, fm_result* out);
+
+/* Device bytes admitted now and at most so far, requests running now and at most so far,
+ * requests waiting for admission (any pointer may be NULL). */
+int fm_server_stats(fm_server* s, int64_t* in_use, int64_t* peak_in_use, int* busy, int* peak_busy, int* queued);
+
+/* Finish the queued and running requests, stop the workers, free the server. */
+void fm_server_destroy(fm_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,7 +45,25 @@ class fm_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class fm_request(ctypes.Structure):
+    _fields_ = [("sys", fm_system), ("grid", fm_grid), ("split", fm_splitting), ("kind", c_int), ("E", c_double),
+                ("k", c_int), ("seed", ctypes.c_uint64), ("precision", c_int), ("sim_ms", c_double),
+                ("out_host", c_void_p)]
+
+
+class fm_result(ctypes.Structure):
+    _fields_ = [("status", c_int), ("iters", c_int), ("n", c_int64), ("bytes", c_int64), ("evals", c_double * 8),
+                ("resid", c_double), ("out_norm", c_double), ("t_submit_ms", c_double), ("t_start_ms", c_double),
+                ("t_end_ms", c_double)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["evals"] = list(self.evals)
+        return d
+
+
 FM_OK, FM_ERR_NOT_CONVERGED, FM_ERR_SCRATCH_LIMIT, FM_ERR_TIMEOUT = 0, -4, -9, -10
+FM_REQ_SOLVE, FM_REQ_EIGS, FM_SERVER_DRY_RUN = 0, 1, 1
 FM_MMA_AUTO, FM_MMA_SIMT, FM_MMA_TF32 = 0, 1, 2
 KERNEL_CLASSES = ["apply_xy", "apply_z", "coupling", "zmix", "xmix", "ysolve", "dot", "axpy", "other"]
 
@@ -76,6 +94,12 @@ SIGNATURES = {
     "fm_host_decompose": (c_int, [c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "fm_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64), ctypes.POINTER(c_double),
                                 ctypes.POINTER(c_double)]),
+    "fm_server_create": (c_int, [c_int, c_int64, c_int, c_int, ctypes.POINTER(c_void_p)]),
+    "fm_server_submit": (c_int, [c_void_p, ctypes.POINTER(fm_request), ctypes.POINTER(c_int64)]),
+    "fm_server_wait": (c_int, [c_void_p, c_int64, c_double, ctypes.POINTER(fm_result)]),
+    "fm_server_stats": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64), ctypes.POINTER(c_int),
+                                ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    "fm_server_destroy": (None, [c_void_p]),
 }
 
 

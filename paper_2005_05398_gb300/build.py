@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libfm.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fm_api.cu", "fm_kernels.cu", "fm_tc.cu", "fm_noalloc.cu", "fm_setup.cpp", "fm_dense.cpp"]
+SOURCES = ["fm_api.cu", "fm_kernels.cu", "fm_tc.cu", "fm_noalloc.cu", "fm_setup.cpp", "fm_dense.cpp", "fm_serve.cpp"]
 
 
 def nvcc():

@@ -134,7 +134,7 @@ __device__ __forceinline__ float inv_sum2(float2 a, float2 b) {
   const float s = a.x + b.x;
   const float bb = s - a.x;
   const float e = (a.x - (s - bb)) + (b.x - bb);
-  return 1.0f / (s + (e + (a.y + b.y)));
+  return __frcp_rn(s + (e + (a.y + b.y)));
 }
 
 }  // namespace
@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t full0 = bars, empty0 = bars + 64, done = bars + 128, slot = bars + 136;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bars - base) + 140);
   volatile int* n_issued = reinterpret_cast<volatile int*>(gbase + (bars - base) + 144);
+  float2* dcol_s = reinterpret_cast<float2*>(gbase + (bars - base) + 256);  // [nb] column diagonal terms
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slab = blockIdx.y, row0 = blockIdx.x * 128;
   const int il = slab / a.nz + slab % a.nz;
@@ -236,6 +237,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mma_commit(done);  // arrives once every MMA issued above has completed
   }
   __syncwarp();
+  if (a.dRow) {  // the slab's column terms of the diagonal, staged while the MMAs run
+    for (int n = threadIdx.x; n < a.nb; n += kTcThreads)
+      dcol_s[n] = (n < a.N) ? a.dCol[(int64_t)il * a.N + n] : make_float2(1.f, 0.f);
+  }
+  __syncthreads();
 
   // epilogue: all four warps, warp w owns accumulator lanes (rows) 32w .. 32w + 31
   const bool ready = mbar_wait(done, 0);
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = c0 + j;
-          if (n < a.N) v[j] *= inv_sum2(drow, a.dCol[(int64_t)il * a.N + n]);
+          if (n < a.N) v[j] *= inv_sum2(drow, dcol_s[n]);
         }
       }
       if (a.trans_out) {  // out[n][r]: lanes hold consecutive rows, 128-byte stores per column
@@ -321,19 +327,27 @@ __global__ void __launch_bounds__(128) k_zmix_rb(const float* __restrict__ Wall,
     p0 = (int64_t)blockIdx.x * 128;
   }
   // input tile: Vs[k][q], q = jl * 8 + il (TRANS) or q = p - p0
-  for (int e = threadIdx.x; e < nz * 128; e += 128) {
-    const int k = e / 128, t = e % 128;
-    float v = 0.f;
+  {
+    // the thread's input element of every z row, eight rows of loads in flight at a time
+    const int t = threadIdx.x;
     int q = t;
+    int64_t src = -1;
     if (TRANS) {
       const int il = t / 16, jl = t % 16;  // consecutive threads walk j: coalesced reads
       const int i = i0 + il, j = j0 + jl;
       q = jl * 8 + il;
-      if (i < nx && j < ny) v = (float)in[base + (int64_t)k * nxy + (int64_t)i * ny + j];
+      if (i < nx && j < ny) src = base + (int64_t)i * ny + j;
     } else {
-      if (p0 + t < nxy) v = (float)in[base + (int64_t)k * nxy + p0 + t];
+      if (p0 + t < nxy) src = base + p0 + t;
     }
-    Vs[k * 128 + q] = v;
+    for (int k0 = 0; k0 < nz; k0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (src >= 0 && k0 + u < nz) ? (float)in[src + (int64_t)(k0 + u) * nxy] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < nz) Vs[(k0 + u) * 128 + q] = v[u];
+    }
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int lc = 0; lc < nz; lc += 64) {
@@ -429,7 +443,7 @@ int tmem_cols(int nb) {
 }
 
 size_t tc_smem_bytes(int nb, int stages, int ncols) {
-  size_t b = 1024 + (size_t)stages * (kTileA + (size_t)nb * 128) + 256;
+  size_t b = 1024 + (size_t)stages * (kTileA + (size_t)nb * 128) + 256 + (size_t)nb * sizeof(float2);
   // at most 512 / ncols CTAs may share an SM's tensor memory: ask for enough shared memory that
   // no more fit (228 KB per SM, 1 KB reserved per CTA)
   const int max_ctas = 512 / ncols;

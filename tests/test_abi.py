@@ -47,7 +47,8 @@ def test_struct_fields_match_header():
     from paper_2005_05398_gb300 import _lib
     src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "fm.h")).read(), flags=re.S)
     for cls, tag in ((_lib.fm_system, "fm_system"), (_lib.fm_grid, "fm_grid"), (_lib.fm_splitting, "fm_splitting"),
-                     (_lib.fm_opts, "fm_opts"), (_lib.fm_info, "fm_info")):
+                     (_lib.fm_opts, "fm_opts"), (_lib.fm_info, "fm_info"), (_lib.fm_request, "fm_request"),
+                     (_lib.fm_result, "fm_result")):
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + tag + ";", src).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         names = re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*(?:\[\d+\])?\s*[,;]", body)
