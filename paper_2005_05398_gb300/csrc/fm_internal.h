@@ -198,7 +198,8 @@ int dot_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, d
 int dot_many_x(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_host);
 int axpy_many_norm(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double* nrm2_out);
 int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double sign);
-int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_dev);
+int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_dev,
+                 bool lowp = false);
 int gs_cgs2(fm_ctx* c, const double* V, int nv, double* w, double* vout, double* h, double* hn);
 int tuning_correct(fm_ctx* c, const double* U, const double* WmU, const double* Gdev, int k, double* z);
 int scale_copy(fm_ctx* c, const double* x, double a, double* y);   // y = a x

@@ -604,9 +604,21 @@ __device__ void last_block_reduce(const double* partial, int nv, unsigned* count
   if (threadIdx.x == 0) *counter = 0u;
 }
 
+// The float with the sign, the exponent and the 20 leading mantissa bits of a double (truncated;
+// 0 below the float range), built with integer operations so that no FP64 instruction is issued.
+__device__ __forceinline__ float f64_lead_f32(double d) {
+  const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(d) >> 32);
+  const unsigned fe = ((hi >> 20) & 0x7FFu) - 896u;  // float exponent (wraps below the float range)
+  const unsigned sign = hi & 0x80000000u;
+  return __uint_as_float((fe - 1u < 254u) ? (sign | (fe << 23) | ((hi & 0xFFFFFu) << 3)) : sign);
+}
+
 // partial[j][block] = sum over this block's slice of V[j] . w  (j < nv), and for j = nv, when
 // 'extra' is given, extra . w.  The vectors are taken eight at a time so that every thread keeps
 // eight independent loads in flight per element; the eight partial sums are reduced together.
+// LOWP: products and per-thread sums in float32 from the leading bits of the operands (relative
+// accuracy about 1e-6 of sum |V_j| |w|), for the first Gram-Schmidt pass only.
+template <bool LOWP>
 __global__ void __launch_bounds__(kRedThreads) k_dot_many(const double* __restrict__ V, int64_t ldv, int nv,
                                                          const double* __restrict__ w, int64_t n,
                                                          double* __restrict__ partial, const double* __restrict__ extra,
@@ -627,17 +639,28 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_many(const double* __restri
       vp[u] = (j < nv) ? V + (int64_t)j * ldv : extra;
     }
     double acc[JT];
+    float accf[JT];
 #pragma unroll
-    for (int u = 0; u < JT; ++u) acc[u] = 0.0;
+    for (int u = 0; u < JT; ++u) {
+      acc[u] = 0.0;
+      accf[u] = 0.f;
+    }
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const double wi = w[i];
+      if (LOWP) {
+        const float wi = f64_lead_f32(w[i]);
 #pragma unroll
-      for (int u = 0; u < JT; ++u)
-        if (u < nj) acc[u] = fma(vp[u][i], wi, acc[u]);
+        for (int u = 0; u < JT; ++u)
+          if (u < nj) accf[u] = fmaf(f64_lead_f32(vp[u][i]), wi, accf[u]);
+      } else {
+        const double wi = w[i];
+#pragma unroll
+        for (int u = 0; u < JT; ++u)
+          if (u < nj) acc[u] = fma(vp[u][i], wi, acc[u]);
+      }
     }
 #pragma unroll
     for (int u = 0; u < JT; ++u) {
-      double v = acc[u];
+      double v = LOWP ? (double)accf[u] : acc[u];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
       if (lane == 0) sh[u][wid] = v;
     }
@@ -1206,12 +1229,14 @@ int dot_many_x(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w,
 }
 
 // h_dev[j] = V[j] . w (j < nv), h_dev[nv] = extra . w when extra is given; stays on the device
-int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_dev) {
+int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_dev,
+                 bool lowp) {
   const int nb = c->red_blocks;
   const int nt = nv + (extra ? 1 : 0);
   if (nt > kGsMaxVec) return FM_ERR_ARG;
   const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-  k_dot_many<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
+  if (lowp) k_dot_many<true><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
+  else k_dot_many<false><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
   prof_end(c, tk_, 2.0 * nt * (double)c->N, (nt + 1.0) * 8.0 * (double)c->N);
   c->launches++;
   FM_CUDA(cudaGetLastError());
@@ -1266,7 +1291,8 @@ int gs_cgs2(fm_ctx* c, const double* V, int nv, double* w, double* vout, double*
   double* sc = c->gsd + 3 * kGsMaxVec;  // [0] ||w'||^2, [1] ||vout||^2, [2] nu
   const int nb2 = 4 * c->red_blocks;
   int rc;
-  if ((rc = dot_many_dev(c, V, N, nv, w, nullptr, h1))) return rc;
+  // first pass: projections to about 1e-6, on the FP32 pipe; the float64 second pass removes what it leaves
+  if ((rc = dot_many_dev(c, V, N, nv, w, nullptr, h1, true))) return rc;
   {
     const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
     k_gs_axpy<0><<<nb2, kRedThreads, 0, c->stream>>>(V, N, nv, h1, nullptr, nullptr, w, nullptr, N, c->red, c->gs_cnt,

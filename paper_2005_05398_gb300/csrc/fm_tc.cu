@@ -301,18 +301,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // ---------------------------------------------------------------------------
 // z mode products, register-blocked: out[l][p] = sum_k W[l][k] in[k][p] for one (component, M')
-// and a tile of 128 points p = (i, j).  Warp w computes the outputs l = lc + w + 4u (u < 16) of
-// four points per lane; W is kept in shared memory permuted as Wp[k][w][u] so that a thread reads
-// its 16 weights of one k with four 16-byte loads.
+// and a tile of 128 points p = (i, j).  Eight warps; warp w computes the outputs l = lc + w + 8u
+// (u < 8) of four points per lane; W is kept in shared memory permuted as Wp[k][w][u] so that a
+// thread reads its 8 weights of one k with two 16-byte loads.
 //   TRANS = false: the tile is 128 consecutive points of the [i][j] plane; out[l][i][j].
 //   TRANS = true:  the tile is 8 (i) x 16 (j) points; out[l][j][i] (x contiguous).
 // ---------------------------------------------------------------------------
+constexpr int kZWarps = 8, kZThreads = 32 * kZWarps, kZOut = 64 / kZWarps;
+
 template <typename TI, typename TO, bool TRANS>
-__global__ void __launch_bounds__(128) k_zmix_rb(const float* __restrict__ Wall, const TI* __restrict__ in,
-                                                 TO* __restrict__ out, int nz, int nx, int ny, int64_t comp_off) {
+__global__ void __launch_bounds__(kZThreads) k_zmix_rb(const float* __restrict__ Wall, const TI* __restrict__ in,
+                                                       TO* __restrict__ out, int nz, int nx, int ny, int64_t comp_off) {
   extern __shared__ __align__(16) float zsm[];
   float* Vs = zsm;                    // [nz][128]
-  float* Wp = zsm + (size_t)nz * 128;  // [nz][4][16]
+  float* Wp = zsm + (size_t)nz * 128;  // [nz][kZWarps][kZOut]
   const int iM = blockIdx.y;
   const int64_t nxy = (int64_t)nx * ny;
   const float* W = Wall + (int64_t)iM * nz * nz;
@@ -326,10 +328,10 @@ __global__ void __launch_bounds__(128) k_zmix_rb(const float* __restrict__ Wall,
   } else {
     p0 = (int64_t)blockIdx.x * 128;
   }
-  // input tile: Vs[k][q], q = jl * 8 + il (TRANS) or q = p - p0
+  // input tile: Vs[k][q], q = jl * 8 + il (TRANS) or q = p - p0; thread t loads point t % 128 of the
+  // z rows k = t / 128, t / 128 + 2, ..., eight rows of loads in flight at a time
   {
-    // the thread's input element of every z row, eight rows of loads in flight at a time
-    const int t = threadIdx.x;
+    const int t = threadIdx.x % 128, k1 = threadIdx.x / 128;
     int q = t;
     int64_t src = -1;
     if (TRANS) {
@@ -340,34 +342,37 @@ __global__ void __launch_bounds__(128) k_zmix_rb(const float* __restrict__ Wall,
     } else {
       if (p0 + t < nxy) src = base + p0 + t;
     }
-    for (int k0 = 0; k0 < nz; k0 += 8) {
+    for (int k0 = k1; k0 < nz; k0 += 16) {
       float v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = (src >= 0 && k0 + u < nz) ? (float)in[src + (int64_t)(k0 + u) * nxy] : 0.f;
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + 2 * u;
+        v[u] = (src >= 0 && k < nz) ? (float)in[src + (int64_t)k * nxy] : 0.f;
+      }
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        if (k0 + u < nz) Vs[(k0 + u) * 128 + q] = v[u];
+        if (k0 + 2 * u < nz) Vs[(k0 + 2 * u) * 128 + q] = v[u];
     }
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int lc = 0; lc < nz; lc += 64) {
     __syncthreads();
-    for (int e = threadIdx.x; e < nz * 64; e += 128) {  // Wp[k][w][u] = W[lc + w + 4u][k]
-      const int k = e / 64, wu = e % 64, w = wu / 16, u = wu % 16;
-      const int l = lc + w + 4 * u;
+    for (int e = threadIdx.x; e < nz * 64; e += kZThreads) {  // Wp[k][w][u] = W[lc + w + 8u][k]
+      const int k = e / 64, wu = e % 64, w = wu / kZOut, u = wu % kZOut;
+      const int l = lc + w + kZWarps * u;
       Wp[e] = (l < nz) ? W[(int64_t)l * nz + k] : 0.f;
     }
     __syncthreads();
-    float acc[16][4];
+    float acc[kZOut][4];
 #pragma unroll
-    for (int u = 0; u < 16; ++u)
+    for (int u = 0; u < kZOut; ++u)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[u][q] = 0.f;
     for (int k = 0; k < nz; ++k) {
       const float4 v = *reinterpret_cast<const float4*>(&Vs[k * 128 + 4 * lane]);
-      const float4* wp = reinterpret_cast<const float4*>(&Wp[(k * 4 + warp) * 16]);
+      const float4* wp = reinterpret_cast<const float4*>(&Wp[(k * kZWarps + warp) * kZOut]);
 #pragma unroll
-      for (int u4 = 0; u4 < 4; ++u4) {
+      for (int u4 = 0; u4 < kZOut / 4; ++u4) {
         const float4 w = wp[u4];
         const float ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -380,8 +385,8 @@ __global__ void __launch_bounds__(128) k_zmix_rb(const float* __restrict__ Wall,
       }
     }
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int l = lc + warp + 4 * u;
+    for (int u = 0; u < kZOut; ++u) {
+      const int l = lc + warp + kZWarps * u;
       if (l >= nz) break;
       TO* ol = out + base + (int64_t)l * nxy;
       if (TRANS) {
@@ -539,7 +544,7 @@ int zstage(fm_ctx* c, const Comp& cp, const float* W, const TI* in, TO* out) {
   if (smem > 100 * 1024) return FM_ERR_ARG;
   const double ncomp = (double)nxy * nz * c->nM;
   const int tk_ = prof_begin(c, FM_KERNEL_ZMIX);
-  k_zmix_rb<TI, TO, TRANS><<<grid, 128, smem, c->stream>>>(W, in, out, nz, cp.nx, cp.ny, cp.off);
+  k_zmix_rb<TI, TO, TRANS><<<grid, kZThreads, smem, c->stream>>>(W, in, out, nz, cp.nx, cp.ny, cp.off);
   prof_end(c, tk_, 2.0 * nz * ncomp, ncomp * (double)(sizeof(TI) + sizeof(TO)));
   c->launches++;
   FM_CUDA(cudaGetLastError());
