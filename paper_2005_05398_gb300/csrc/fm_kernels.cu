@@ -618,6 +618,14 @@ __device__ __forceinline__ float f64_lead_f32(double d) {
 // eight independent loads in flight per element; the eight partial sums are reduced together.
 // LOWP: products and per-thread sums in float32 from the leading bits of the operands (relative
 // accuracy about 1e-6 of sum |V_j| |w|), for the first Gram-Schmidt pass only.
+// The vectors are read as 16-byte element pairs (n even, 16-byte aligned vectors), eight vectors and
+// two pairs per thread and iteration with every load issued before the FMAs, so that a thread keeps
+// 18 loads of 16 bytes in flight: the kernel is bound by memory latency otherwise.
+__device__ __forceinline__ double dot2(double2 a, double2 b, double acc) { return fma(a.y, b.y, fma(a.x, b.x, acc)); }
+__device__ __forceinline__ float dot2f(double2 a, double2 b, float acc) {
+  return fmaf(f64_lead_f32(a.y), f64_lead_f32(b.y), fmaf(f64_lead_f32(a.x), f64_lead_f32(b.x), acc));
+}
+
 template <bool LOWP>
 __global__ void __launch_bounds__(kRedThreads) k_dot_many(const double* __restrict__ V, int64_t ldv, int nv,
                                                          const double* __restrict__ w, int64_t n,
@@ -625,18 +633,21 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_many(const double* __restri
                                                          unsigned* counter, double* __restrict__ out) {
   constexpr int JT = 8;
   __shared__ double sh[JT][kRedThreads / 32];
-  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t npair = n / 2;
+  const int64_t chunk = (npair + gridDim.x - 1) / gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * chunk;
-  const int64_t hi = min(n, lo + chunk);
+  const int64_t hi = min(npair, lo + chunk);
   const int nt = nv + (extra ? 1 : 0);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  const int64_t bs = blockDim.x;
   for (int j0 = 0; j0 < nt; j0 += JT) {
     const int nj = min(JT, nt - j0);
-    const double* vp[JT];
+    const double2* vp[JT];
 #pragma unroll
     for (int u = 0; u < JT; ++u) {
       const int j = j0 + min(u, nj - 1);
-      vp[u] = (j < nv) ? V + (int64_t)j * ldv : extra;
+      vp[u] = reinterpret_cast<const double2*>((j < nv) ? V + (int64_t)j * ldv : extra);
     }
     double acc[JT];
     float accf[JT];
@@ -645,18 +656,41 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_many(const double* __restri
       acc[u] = 0.0;
       accf[u] = 0.f;
     }
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      if (LOWP) {
-        const float wi = f64_lead_f32(w[i]);
+    int64_t p = lo + threadIdx.x;
+    for (; p + bs < hi; p += 2 * bs) {
+      const double2 wa = w2[p], wb = w2[p + bs];
+      double2 va[JT], vb[JT];
 #pragma unroll
-        for (int u = 0; u < JT; ++u)
-          if (u < nj) accf[u] = fmaf(f64_lead_f32(vp[u][i]), wi, accf[u]);
-      } else {
-        const double wi = w[i];
+      for (int u = 0; u < JT; ++u)
+        if (u < nj) {
+          va[u] = vp[u][p];
+          vb[u] = vp[u][p + bs];
+        }
 #pragma unroll
-        for (int u = 0; u < JT; ++u)
-          if (u < nj) acc[u] = fma(vp[u][i], wi, acc[u]);
-      }
+      for (int u = 0; u < JT; ++u)
+        if (u < nj) {
+          if (LOWP) accf[u] = dot2f(vb[u], wb, dot2f(va[u], wa, accf[u]));
+          else acc[u] = dot2(vb[u], wb, dot2(va[u], wa, acc[u]));
+        }
+    }
+    for (; p < hi; p += bs) {
+      const double2 wa = w2[p];
+#pragma unroll
+      for (int u = 0; u < JT; ++u)
+        if (u < nj) {
+          if (LOWP) accf[u] = dot2f(vp[u][p], wa, accf[u]);
+          else acc[u] = dot2(vp[u][p], wa, acc[u]);
+        }
+    }
+    if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {  // odd length: the last element
+      const int64_t e = n - 1;
+#pragma unroll
+      for (int u = 0; u < JT; ++u)
+        if (u < nj) {
+          const double* vv = reinterpret_cast<const double*>(vp[u]);
+          if (LOWP) accf[u] = fmaf(f64_lead_f32(vv[e]), f64_lead_f32(w[e]), accf[u]);
+          else acc[u] = fma(vv[e], w[e], acc[u]);
+        }
     }
 #pragma unroll
     for (int u = 0; u < JT; ++u) {
@@ -833,16 +867,18 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restric
   __syncthreads();
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    // one FMA per basis vector on a single chain (no partial sums to add: FP64 issue is the bound);
+    // eight loads issued ahead of their FMAs
+    double v = w[i];
     int j = 0;
-    for (; j + 3 < nv; j += 4) {
-      s0 = fma(cs[j], V[(int64_t)j * ldv + i], s0);
-      s1 = fma(cs[j + 1], V[(int64_t)(j + 1) * ldv + i], s1);
-      s2 = fma(cs[j + 2], V[(int64_t)(j + 2) * ldv + i], s2);
-      s3 = fma(cs[j + 3], V[(int64_t)(j + 3) * ldv + i], s3);
+    for (; j + 7 < nv; j += 8) {
+      double t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = V[(int64_t)(j + u) * ldv + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v = fma(-cs[j + u], t[u], v);
     }
-    for (; j < nv; ++j) s0 = fma(cs[j], V[(int64_t)j * ldv + i], s0);
-    const double v = w[i] - ((s0 + s1) + (s2 + s3));
+    for (; j < nv; ++j) v = fma(-cs[j], V[(int64_t)j * ldv + i], v);
     if (MODE == 0) {
       w[i] = v;
       acc = fma(v, v, acc);
@@ -1234,6 +1270,10 @@ int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* 
   const int nb = c->red_blocks;
   const int nt = nv + (extra ? 1 : 0);
   if (nt > kGsMaxVec) return FM_ERR_ARG;
+  // 16-byte element pairs: every vector must start on a 16-byte boundary (n_x is even, so N is)
+  const uintptr_t al = reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w) |
+                       reinterpret_cast<uintptr_t>(extra) | (uintptr_t)(ldv * 8);
+  if (al & 15u) return FM_ERR_ARG;
   const int tk_ = prof_begin(c, FM_KERNEL_DOT);
   if (lowp) k_dot_many<true><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
   else k_dot_many<false><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
