@@ -64,6 +64,14 @@ WORKLOADS = {
     "he_l0_96x96x24": make_workload("He", 0, nint=(96, 96, 24), R=(40.0, 40.0), shift=-2.95, k=1,
                                     name="he_l0_96x96x24"),
 }
+# He, J = 10 (n_M = 11), the shape of the paper's high-momentum table (Section 4): equidistant z,
+# component 1 on a 280 x 280 box with 58 x 58 x 6 intervals, component 3 on a 2 x 2 box with 4 x 4 x 6;
+# the level nearest -2.0045 (the paper's lowest is near -2.0041)
+WORKLOADS["he_l10_58x58x6"] = make_workload("He", 10, nint=(58, 58, 6), R=(280.0, 280.0),
+                                            maps=(MAP_POW, MAP_POW, MAP_EQUI), shift=-2.0045, k=1,
+                                            name="he_l10_58x58x6")
+WORKLOADS["he_l10_58x58x6"]["grids"] = {1: {"nint": (58, 58, 6), "R": (280.0, 280.0)},
+                                        3: {"nint": (4, 4, 6), "R": (2.0, 2.0)}}
 for _J in (1, 2, 3):
     WORKLOADS[f"psm_l{_J}_64x64x16"] = make_workload(
         "Psminus", _J, nint=(64, 64, 16), R=(80.0, 80.0), shift=-0.27, k=4,

@@ -249,7 +249,7 @@ class Context:
         _check("fm_eigs", rc, (FM_ERR_NOT_CONVERGED,) if allow_not_converged else ())
         return list(ev), info.as_dict()
 
-    def fm_eigs_host(self, shift, k, v0_host=None, evecs_host=None):
+    def fm_eigs_host(self, shift, k, v0_host=None, evecs_host=None, allow_not_converged=False):
         """Host buffers: numpy float64 arrays (v0_host length n, evecs_host k*n) or pinned torch tensors."""
         ev = (c_double * k)()
         info = fm_info()
@@ -261,7 +261,8 @@ class Context:
                 return c_void_p(a.data_ptr())
             return a.ctypes.data_as(c_void_p)
         _check("fm_eigs_host", lib().fm_eigs_host(self.h, float(shift), int(k), hp(v0_host), ev, hp(evecs_host),
-                                                  ctypes.byref(info)))
+                                                  ctypes.byref(info)),
+               (FM_ERR_NOT_CONVERGED,) if allow_not_converged else ())
         return list(ev), info.as_dict()
 
     def fm_stats(self):

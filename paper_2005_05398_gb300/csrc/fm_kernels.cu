@@ -21,7 +21,7 @@
 
 namespace {
 
-constexpr int kMaxM = 8;  // largest n_M handled by the register arrays (J <= 7)
+constexpr int kMaxM = 12;  // largest n_M (J <= 11 for tau = +1)
 
 // ---------------------------------------------------------------------------
 // apply, pass 1: for one (component, M', z-dof k) plane c[i][j] (n_x x n_y) and a tile
@@ -556,7 +556,11 @@ __global__ void __launch_bounds__(LPB) k_ysolve(const YBatch<T> yb, int R, int W
     case 5: ysolve_line<T, LPB, 11>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
     case 6: ysolve_line<T, LPB, 13>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
     case 7: ysolve_line<T, LPB, 15>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    default: ysolve_line<T, LPB, 17>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    case 8: ysolve_line<T, LPB, 17>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    case 9: ysolve_line<T, LPB, 19>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    case 10: ysolve_line<T, LPB, 21>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    case 11: ysolve_line<T, LPB, 23>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+    default: ysolve_line<T, LPB, 25>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
   }
   if (live)
     for (int r = 0; r < n; ++r) t[xrow(r) + tid] = xs[r * LPB + tid];

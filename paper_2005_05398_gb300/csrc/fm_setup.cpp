@@ -598,7 +598,7 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
 int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const fm_splitting* split, const fm_opts* o,
                    int64_t* out) {
   const int M0 = (1 - S->tau) / 2, nM = S->J - M0 + 1;
-  if (nM <= 0 || nM > 8) return FM_ERR_ARG;
+  if (nM <= 0 || nM > 12) return FM_ERR_ARG;
   std::vector<int> labels;
   if (split->mode == FM_SPLIT_SCHRODINGER) labels = {1};
   else if (S->identical_pair == 12) labels = {1, 3};

@@ -42,6 +42,10 @@ CASES = {
                          shift=-0.27),
     "distinct_l1": dict(J=1, nint=(5, 5, 3), R=(12.0, 11.0), identical_pair=0, mass=(1.0, 3.0, 7.0),
                         charge=(-1.0, 2.0, -1.0)),
+    # high total momentum (n_M = 11, the paper's He J = 10 workload shape: equidistant z, a wide box
+    # for component 1 and a small one for component 3)
+    "he_l10": dict(J=10, nint=(3, 3, 2), R=(20.0, 20.0), maps=(0, 0, 1), shift=-2.0,
+                   grids={3: {"nint": (2, 2, 2), "R": (2.0, 2.0)}}),
 }
 
 
@@ -65,14 +69,19 @@ def test_apply_matches_oracle(pkg, name):
         ctx.fm_apply(E, _dev(x), y)
         got = y.cpu().numpy()
         scale = np.abs(H).max(axis=1).toarray().ravel() * np.abs(x).max() + 1e-300
-        assert np.max(np.abs(got - ref) / scale) < 1e-13, name
+        # rounding of a row grows with its number of terms (n_M = 11 rows carry ~1700): 1e-13 up to
+        # 256 terms, then with the square root of the count
+        nnz = np.diff(H.tocsr().indptr)
+        bound = 1e-13 * np.maximum(1.0, np.sqrt(nnz / 256.0))
+        assert np.max(np.abs(got - ref) / scale / bound) < 1.0, name
     ys = torch.empty(s.N, dtype=torch.float64, device="cuda")
     ctx.fm_apply_S(_dev(x), ys)
     assert np.max(np.abs(ys.cpu().numpy() - S @ x)) < 1e-13 * np.abs(x).max() * 4
     ctx.close()
 
 
-@pytest.mark.parametrize("name", ["he_l0_merkuriev", "he_l1", "he_l2_odd", "psm_l2", "he_l1_percomp", "psm_l3_pairs"])
+@pytest.mark.parametrize("name", ["he_l0_merkuriev", "he_l1", "he_l2_odd", "psm_l2", "he_l1_percomp", "psm_l3_pairs",
+                                  "he_l10"])
 def test_precond_fp64_matches_paper_form(pkg, name):
     """The GPU preconditioner (z/x mode products + banded y solves) equals the
     paper's Eq. prec-2 with y eigen-transforms and tridiagonal M' chains."""
@@ -175,7 +184,7 @@ def test_solve_matches_sparse_lu(pkg, precision):
 
 @pytest.mark.parametrize("name,k,precision", [("he_l0_merkuriev", 1, 0), ("he_l0_merkuriev", 3, 1), ("he_l1", 2, 1),
                                               ("psm_l2", 2, 1), ("psm_l3_pairs", 2, 1), ("he_l0_merkuriev", 3, 2),
-                                              ("psm_l2", 2, 2)])
+                                              ("psm_l2", 2, 2), ("he_l10", 2, 1)])
 def test_eigs_match_oracle(pkg, name, k, precision):
     from oracle.system import FMSystem
     from oracle import solvers
