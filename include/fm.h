@@ -116,7 +116,9 @@ typedef struct {
                         float32 preconditioner, banded LU otherwise), 1 = banded LU, 2 = per-l
                         diagonalisation of (A_l, S_y) when n_M = 1 (both invert the same matrix) */
   int tune;          /* fm_eigs: 1 = tune the preconditioner to the current Ritz vectors U (rank-k update
-                        P + (A U - P U) U^T, Freitag & Spence), 0 = plain preconditioner */
+                        P + (A U - P U) U^T, Freitag & Spence), dropped once an inner solve stalls;
+                        0 = plain preconditioner (default: with the relaxed inner tolerance the tuning no
+                        longer saves time, and near clusters of levels it misleads inexact solves) */
   int mma;           /* FM_MMA_AUTO, FM_MMA_SIMT or FM_MMA_TF32 */
   int device;        /* CUDA device ordinal */
   void* stream;      /* cudaStream_t, NULL = legacy default stream */
@@ -134,7 +136,7 @@ typedef struct {
 typedef struct fm_ctx fm_ctx;
 
 /* Default options: tol 1e-12, restart 64, max_iters 2000, FP64, ncv 20, 50 restarts,
- * eig_tol 1e-9, replaced z eigenvalues, tuned preconditioner, device 0, default stream. */
+ * eig_tol 1e-9, replaced z eigenvalues, plain preconditioner, device 0, default stream. */
 void fm_default_opts(fm_opts* opts);
 
 /* Build a context: 1D bases and collocation points (Section 3.1), pointwise potential

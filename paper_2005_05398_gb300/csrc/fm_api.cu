@@ -158,27 +158,6 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
   return converged ? FM_OK : FM_ERR_NOT_CONVERGED;
 }
 
-// float32 Gram-Schmidt (classical, DGKS re-orthogonalisation), coefficients and norm in float64
-static int orthogonalize32(fm_ctx* c, const float* V, int nv, float* w, double* h, double* nrm) {
-  std::vector<double> h1(nv), h2(nv);
-  int rc;
-  double before2;
-  if ((rc = dot_many32(c, w, c->N, 1, w, &before2))) return rc;
-  if ((rc = dot_many32(c, V, c->N, nv, w, h1.data()))) return rc;
-  double n2;
-  if ((rc = axpy_many_norm32(c, V, c->N, nv, h1.data(), -1.0f, w, &n2))) return rc;
-  for (int i = 0; i < nv; ++i) h[i] = h1[i];
-  double after = std::sqrt(std::max(n2, 0.0));
-  if (after < 0.7071067811865476 * std::sqrt(std::max(before2, 0.0))) {
-    if ((rc = dot_many32(c, V, c->N, nv, w, h2.data()))) return rc;
-    if ((rc = axpy_many_norm32(c, V, c->N, nv, h2.data(), -1.0f, w, &n2))) return rc;
-    for (int i = 0; i < nv; ++i) h[i] += h2[i];
-    after = std::sqrt(std::max(n2, 0.0));
-  }
-  *nrm = after;
-  return FM_OK;
-}
-
 // float32 right-preconditioned FGMRES for (H - E S) d = b (float32 operator, preconditioner and basis;
 // Givens and the small least-squares problem in float64).  d starts at zero.
 static int fgmres32(fm_ctx* c, double E, const float* b, float* d, double tol, int max_iters, int* iters_out) {
@@ -207,8 +186,8 @@ static int fgmres32(fm_ctx* c, double E, const float* b, float* d, double tol, i
       float* Zj = c->Z32 + (int64_t)j * N;
       if ((rc = launch_precond32(c, Vj, Zj))) return rc;
       if ((rc = launch_apply32(c, E, Zj, c->w32, false))) return rc;
-      double hn;
-      if ((rc = orthogonalize32(c, c->V32, j + 1, c->w32, h.data(), &hn))) return rc;
+      double hn;  // CGS2 writes the next basis vector V32[j+1] = (w - V h) / hn
+      if ((rc = gs_cgs2_32(c, c->V32, j + 1, c->w32, c->V32 + (int64_t)(j + 1) * N, h.data(), &hn))) return rc;
       if (!std::isfinite(hn)) return FM_ERR_BREAKDOWN;
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * h[i] + sn[i] * h[i + 1];
@@ -225,7 +204,6 @@ static int fgmres32(fm_ctx* c, double E, const float* b, float* d, double tol, i
       ++total;
       jdone = j + 1;
       if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0) break;
-      if ((rc = axpby32(c, (float)(1.0 / hn), c->w32, 0.0f, c->V32 + (int64_t)(j + 1) * N))) return rc;
     }
     for (int i = jdone - 1; i >= 0; --i) {
       double sacc = g[i];
@@ -340,7 +318,7 @@ void fm_default_opts(fm_opts* o) {
   o->max_restarts = 50;
   o->eig_tol = 1e-9;
   o->z_eigs = 0;
-  o->tune = 1;
+  o->tune = 0;
   o->y_solver = 0;
   o->mma = FM_MMA_AUTO;
   o->device = 0;
@@ -619,10 +597,16 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
   std::vector<std::vector<double>> hist;  // eigenvalue history of each wanted Ritz value
   const bool verbose = getenv("FM_VERBOSE") != nullptr;
   double worst_inner = 0.0;  // largest (final relative residual / requested tolerance) of an inner solve
+  // The tuned preconditioner speeds up inner solves that converge; once an inner solve stalls far above
+  // its tolerance (the shift sits in a cluster of levels and the solves reach their float64 floor), the
+  // tuning is dropped for the rest of the eigen-solve: its rank-k correction then steers the inexact
+  // solves away from the wanted direction.
+  bool tune_ok = true;
   double max_res = 0.0;
   // Inner solves to base_tol while the wanted Ritz pairs are far from converged; once their largest
   // relative Ritz residual r is small, the next operator application may be inexact by about
-  // base_tol / r (relaxation of inexact Arnoldi, Simoncini and Szyld), at most 1e-6.
+  // 0.1 base_tol / r (relaxation of inexact Arnoldi, Simoncini and Szyld, with a factor 10 of margin),
+  // at most 1e-7.
   const double base_tol = std::max(c->opts.tol, 0.1 * c->opts.eig_tol);
   double prev_res = 1.0;
   while (true) {
@@ -630,7 +614,7 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
     for (int j = kcur; j < m; ++j) {
       double* Vj = V + (int64_t)j * N;
       double* w = V + (int64_t)(j + 1) * N;
-      if (c->opts.tune && c->opts.precision != FM_PREC_MIXED && nsz >= 1 && !best.empty()) {
+      if (c->opts.tune && tune_ok && c->opts.precision != FM_PREC_MIXED && nsz >= 1 && !best.empty()) {
         // tuned preconditioner (Freitag-Spence): U = orthonormalised Ritz vectors of the wanted values
         std::vector<int> cols;
         for (const auto& rz : best)
@@ -648,12 +632,16 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
       FM_CUDA(cudaMemsetAsync(w, 0, N * 8, c->stream));
       int it = 0, rs = 0;
       double res = 0.0;
-      const double inner_tol = std::max(base_tol, std::min(1e-6, base_tol / std::max(prev_res, 1e-300)));
+      const double inner_tol = std::max(base_tol, std::min(1e-7, 0.1 * base_tol / std::max(prev_res, 1e-300)));
       rc = solve_any(c, shift, c->tmpN, w, inner_tol, c->opts.max_iters, &it, &rs, &res);
       inner += it;
       ++ops;
       if (rc != FM_OK && rc != FM_ERR_NOT_CONVERGED) return rc;
       worst_inner = std::max(worst_inner, res / inner_tol);
+      if (res > 100.0 * inner_tol && c->n_tune > 0) {
+        tune_ok = false;
+        c->n_tune = 0;
+      }
       std::vector<double> h(j + 1);
       double hn;
       if ((rc = gs_cgs2(c, V, j + 1, w, w, h.data(), &hn))) return rc;  // w <- (w - V h) / hn

@@ -201,6 +201,7 @@ int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_h
 int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_dev,
                  bool lowp = false);
 int gs_cgs2(fm_ctx* c, const double* V, int nv, double* w, double* vout, double* h, double* hn);
+int gs_cgs2_32(fm_ctx* c, const float* V, int nv, float* w, float* vout, double* h, double* hn);
 int tuning_correct(fm_ctx* c, const double* U, const double* WmU, const double* Gdev, int k, double* z);
 int scale_copy(fm_ctx* c, const double* x, double a, double* y);   // y = a x
 int axpby(fm_ctx* c, double a, const double* x, double b, double* y);  // y = a x + b y

@@ -897,6 +897,120 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restric
   last_block_reduce(partial, 1, counter, out);
 }
 
+// float32 counterparts of the Gram-Schmidt kernels (MIXED precision inner solves): vectors of
+// float32, coefficients, norms and reductions in float64.
+// Multi-dot: partial[j][block] of V[j] . w over 16-byte quads (n a multiple of 4, 16-byte aligned
+// vectors), eight vectors and two quads per thread and iteration, loads issued before the FMAs.
+__device__ __forceinline__ float dot4f(float4 a, float4 b, float acc) {
+  return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, acc))));
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_dot_many32v(const float* __restrict__ V, int64_t ldv, int nv,
+                                                            const float* __restrict__ w, int64_t n,
+                                                            double* __restrict__ partial, unsigned* counter,
+                                                            double* __restrict__ out) {
+  constexpr int JT = 8;
+  __shared__ double sh[JT][kRedThreads / 32];
+  const int64_t nq = n / 4;
+  const int64_t chunk = (nq + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(nq, lo + chunk);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const float4* w4 = reinterpret_cast<const float4*>(w);
+  const int64_t bs = blockDim.x;
+  for (int j0 = 0; j0 < nv; j0 += JT) {
+    const int nj = min(JT, nv - j0);
+    const float4* vp[JT];
+#pragma unroll
+    for (int u = 0; u < JT; ++u) vp[u] = reinterpret_cast<const float4*>(V + (int64_t)(j0 + min(u, nj - 1)) * ldv);
+    float acc[JT];
+#pragma unroll
+    for (int u = 0; u < JT; ++u) acc[u] = 0.f;
+    int64_t p = lo + threadIdx.x;
+    for (; p + bs < hi; p += 2 * bs) {
+      const float4 wa = w4[p], wb = w4[p + bs];
+      float4 va[JT], vb[JT];
+#pragma unroll
+      for (int u = 0; u < JT; ++u)
+        if (u < nj) {
+          va[u] = vp[u][p];
+          vb[u] = vp[u][p + bs];
+        }
+#pragma unroll
+      for (int u = 0; u < JT; ++u)
+        if (u < nj) acc[u] = dot4f(vb[u], wb, dot4f(va[u], wa, acc[u]));
+    }
+    for (; p < hi; p += bs) {
+      const float4 wa = w4[p];
+#pragma unroll
+      for (int u = 0; u < JT; ++u)
+        if (u < nj) acc[u] = dot4f(vp[u][p], wa, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < JT; ++u) {
+      double v = (double)acc[u];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[u][wid] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nj) {
+      double r = 0.0;
+      for (int q = 0; q < kRedThreads / 32; ++q) r += sh[threadIdx.x][q];
+      partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = r;
+    }
+    __syncthreads();
+  }
+  last_block_reduce(partial, nv, counter, out);
+}
+
+// w' = w - sum_j h_j V_j (float32, h from the device); MODE 0: w <- w', out[0] = ||w'||^2;
+// MODE 1: vout = w' / nu with nu^2 = nrm2_prev - |h|^2, out[0] = ||vout||^2, out[1] = nu.
+template <int MODE>
+__global__ void __launch_bounds__(kRedThreads) k_gs_axpy32(const float* __restrict__ V, int64_t ldv, int nv,
+                                                          const double* __restrict__ h, float* w, float* vout,
+                                                          int64_t n, double* __restrict__ partial, unsigned* counter,
+                                                          double* __restrict__ out,
+                                                          const double* __restrict__ nrm2_prev) {
+  __shared__ float cs[kGsMaxVec];
+  __shared__ double sh[32];
+  __shared__ float inv_nu;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = (float)h[j];
+  __syncthreads();
+  if (MODE == 1 && threadIdx.x == 0) {
+    double c2 = 0.0;
+    for (int j = 0; j < nv; ++j) c2 = fma(h[j], h[j], c2);
+    const double nu2 = *nrm2_prev - c2;
+    const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
+    inv_nu = nu > 0.0 ? (float)(1.0 / nu) : 0.f;
+    if (blockIdx.x == 0) out[1] = nu;
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float v = w[i];
+    int j = 0;
+    for (; j + 7 < nv; j += 8) {
+      float t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = V[(int64_t)(j + u) * ldv + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v = fmaf(-cs[j + u], t[u], v);
+    }
+    for (; j < nv; ++j) v = fmaf(-cs[j], V[(int64_t)j * ldv + i], v);
+    if (MODE == 0) {
+      w[i] = v;
+      acc += (double)v * (double)v;
+    } else {
+      const float o = v * inv_nu;
+      vout[i] = o;
+      acc += (double)o * (double)o;
+    }
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  last_block_reduce(partial, 1, counter, out);
+}
+
 // w += sign * sum_j h[j] V[j]
 __global__ void __launch_bounds__(256) k_axpy_many(const double* __restrict__ V, int64_t ldv, int nv,
                                                    const double* __restrict__ h, double sign, double* __restrict__ w,
@@ -1367,6 +1481,57 @@ int gs_cgs2(fm_ctx* c, const double* V, int nv, double* w, double* vout, double*
   *hn = nu * vn;
   if (std::fabs(vn - 1.0) > 1e-12)  // Pythagoras lost digits: rescale to unit norm
     if ((rc = scale_copy(c, vout, 1.0 / vn, vout))) return rc;
+  return prof_harvest(c);
+}
+
+// float32 CGS2 (MIXED precision inner solves): as gs_cgs2 on float32 vectors, coefficients and norms
+// in float64, one host synchronisation.
+int gs_cgs2_32(fm_ctx* c, const float* V, int nv, float* w, float* vout, double* h, double* hn) {
+  if (nv < 1 || nv > kGsMaxVec) return FM_ERR_ARG;
+  const int64_t N = c->N;
+  const uintptr_t al = reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w) | (uintptr_t)(N * 4);
+  if (al & 15u) return FM_ERR_ARG;
+  double* h1 = c->gsd;
+  double* h2 = c->gsd + kGsMaxVec;
+  double* sc = c->gsd + 3 * kGsMaxVec;
+  const int nb = c->red_blocks, nb2 = 4 * c->red_blocks;
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+    k_dot_many32v<<<nb, kRedThreads, 0, c->stream>>>(V, N, nv, w, N, c->red, c->gs_cnt, h1);
+    prof_end(c, tk_, 2.0 * nv * (double)N, (nv + 1.0) * 4.0 * (double)N);
+  }
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+    k_gs_axpy32<0><<<nb2, kRedThreads, 0, c->stream>>>(V, N, nv, h1, w, nullptr, N, c->red, c->gs_cnt, sc, nullptr);
+    prof_end(c, tk_, (2.0 * nv + 2.0) * (double)N, (nv + 2.0) * 4.0 * (double)N);
+  }
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+    k_dot_many32v<<<nb, kRedThreads, 0, c->stream>>>(V, N, nv, w, N, c->red, c->gs_cnt, h2);
+    prof_end(c, tk_, 2.0 * nv * (double)N, (nv + 1.0) * 4.0 * (double)N);
+  }
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+    k_gs_axpy32<1><<<nb2, kRedThreads, 0, c->stream>>>(V, N, nv, h2, w, vout, N, c->red, c->gs_cnt, sc + 1, sc);
+    prof_end(c, tk_, (2.0 * nv + 2.0) * (double)N, (nv + 2.0) * 4.0 * (double)N);
+  }
+  c->launches += 4;
+  FM_CUDA(cudaGetLastError());
+  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, (3 * kGsMaxVec + 3) * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  const double* hh = c->red_host;
+  for (int i = 0; i < nv; ++i) h[i] = hh[i] + hh[kGsMaxVec + i];
+  const double vn2 = hh[3 * kGsMaxVec + 1], nu = hh[3 * kGsMaxVec + 2];
+  if (!(nu > 0.0) || !(vn2 > 0.0)) {
+    *hn = std::isfinite(nu) && std::isfinite(vn2) ? 0.0 : nu + vn2;
+    return prof_harvest(c);
+  }
+  const double vn = std::sqrt(vn2);
+  *hn = nu * vn;
+  int rc;
+  if (std::fabs(vn - 1.0) > 1e-6)  // float32 vector: renormalise when Pythagoras lost digits
+    if ((rc = axpby32(c, (float)(1.0 / vn), vout, 0.0f, vout))) return rc;
   return prof_harvest(c);
 }
 

@@ -214,6 +214,22 @@ def test_eigs_match_oracle(pkg, name, k, precision):
     assert solvers.residual(H, S, ev[0], c) < 1e-7
 
 
+def test_eigs_tuned_preconditioner_matches_oracle(pkg):
+    """The optional tuned preconditioner (rank-k update on the Ritz vectors) changes the inner iteration
+    counts, never the eigenvalues."""
+    from oracle.system import FMSystem
+    from oracle import solvers
+    wl = _wl("he_l1")
+    s = FMSystem(wl)
+    Eo, _ = solvers.eigs_near(s.H(), s.S(), -2.12, 6)
+    Eo = Eo[np.abs(Eo.imag) <= 1e-10 * np.abs(Eo)][:2].real
+    ctx = pkg.Context(wl, restart_m=40, precision=1, tune=1)
+    ev, info = ctx.fm_eigs(-2.12, 2)
+    assert info["converged"] == 1
+    for i in range(2):
+        assert abs(ev[i] - Eo[i]) <= 1e-9 * abs(Eo[i]), (ev, Eo)
+
+
 def test_eigs_small_case_matches_golden(pkg):
     """He L=0, 24x24x8 intervals: the lowest level against the stored oracle value."""
     gold = json.load(open(os.path.join(GOLDEN, "oracle_he_l0_24x24x8.json")))
