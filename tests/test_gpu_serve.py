@@ -56,3 +56,18 @@ def test_results_alone_equal_results_in_mix(serve, precision):
         else:
             assert a["resid"] <= 1e-12 or a["status"] == -4
             assert np.linalg.norm(oa[0] - out_mix[i]) <= 1e-8 * np.linalg.norm(oa[0])
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_estimate_bounds_the_device_bytes_a_context_holds(serve, precision):
+    """Admission trusts fm_estimate_bytes: it must not undercount what fm_create allocates."""
+    import paper_2005_05398_gb300 as pkg
+    from paper_2005_05398_gb300._lib import fm_estimate_bytes
+    for r in request_mix(6, 11, scale="small"):
+        wl = r["wl"]
+        est = fm_estimate_bytes(wl, restart_m=40, ncv=20, precision=precision)
+        ctx = pkg.Context(wl, restart_m=40, ncv=20, precision=precision)
+        ctx.fm_set_shift(r["E"])
+        held = ctx.fm_stats()["device_bytes"]
+        ctx.close()
+        assert held <= est <= 1.5 * held + 2**22, (wl["name"], held, est)

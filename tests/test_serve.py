@@ -102,3 +102,20 @@ def test_rejections(serve):
     with pytest.raises(FMError):
         srv.wait(rid)  # collected already
     srv.close()
+
+
+def test_request_mix_is_seeded_and_in_range():
+    from fm_inputs import MIX_EIG_SHIFT, MIX_SCALES
+    a, b = request_mix(20, 5), request_mix(20, 5)
+    assert [r["wl"]["name"] for r in a] == [r["wl"]["name"] for r in b] and [r["E"] for r in a] == [r["E"] for r in b]
+    (j_lo, j_hi), (r_lo, r_hi), (z_lo, z_hi) = MIX_SCALES["full"]
+    for i, r in enumerate(a):
+        wl = r["wl"]
+        assert j_lo <= wl["J"] <= j_hi and wl["tau"] == 1
+        assert r_lo <= wl["nint"][0] <= r_hi and r_lo <= wl["nint"][1] <= r_hi and z_lo <= wl["nint"][2] <= z_hi
+        assert r["kind"] == ("solve" if i % 2 == 0 else "eigs")
+        if r["kind"] == "solve":
+            assert -3.0 <= r["E"] <= -0.2
+        else:
+            lo, hi = MIX_EIG_SHIFT[wl["system"]]
+            assert lo <= r["E"] <= hi
