@@ -197,7 +197,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
     ctx = pkg.Context(wl, precision={"fp64": 0, "fp32": 1, "mixed": 2}[args.precision], restart_m=args.restart,
-                      ncv=args.ncv, tune=args.tune, device=local, stream=stream)
+                      ncv=args.ncv, tune=args.tune, start_filter=args.start_filter, device=local, stream=stream)
     ctx.fm_set_shift(wl["shift"])
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -274,7 +274,7 @@ def run_ours(args):
                                    "; ".join(f"component {a}: {g['nint'][0]}x{g['nint'][1]}x{g['nint'][2]} intervals, "
                                              f"R={g['R'][0]:g}x{g['R'][1]:g}" for a, g in sorted(wl["grids"].items()))),
                           "n_unknowns": n, "k": args.k,
-                          "shift": wl["shift"], "precond_precision": args.precision, "restart_m": args.restart, "tune": args.tune,
+                          "shift": wl["shift"], "precond_precision": args.precision, "restart_m": args.restart, "tune": args.tune, "start_filter": args.start_filter,
                           "ncv": args.ncv, "l2": "inputs larger than L2 (Krylov basis and factors > 129 MB)",
                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
                "time_to_solution_s": ms_max / args.steps / 1e3,
@@ -403,6 +403,7 @@ def main():
     ap.add_argument("--restart", type=int, default=40)
     ap.add_argument("--ncv", type=int, default=20)
     ap.add_argument("--tune", type=int, default=0, choices=[0, 1], help="tuned preconditioner in fm_eigs")
+    ap.add_argument("--start-filter", type=int, default=8, help="preconditioner passes on the Arnoldi start vector")
     ap.add_argument("--k", type=int, default=None, help="eigenpairs per step (default: the workload's)")
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -120,6 +120,9 @@ typedef struct {
                         0 = plain preconditioner (default: with the relaxed inner tolerance the tuning no
                         longer saves time, and near clusters of levels it misleads inexact solves) */
   int mma;           /* FM_MMA_AUTO, FM_MMA_SIMT or FM_MMA_TF32 */
+  int start_filter;  /* fm_eigs: passes v <- P^{-1} S v / |.| applied to the start vector before the Arnoldi
+                        process (the tensor preconditioner approximates (H - E* S)^{-1}, so each pass
+                        enriches the directions of the levels nearest the shift); 0..16, default 8 */
   int device;        /* CUDA device ordinal */
   void* stream;      /* cudaStream_t, NULL = legacy default stream */
 } fm_opts;
@@ -136,7 +139,8 @@ typedef struct {
 typedef struct fm_ctx fm_ctx;
 
 /* Default options: tol 1e-12, restart 64, max_iters 2000, FP64, ncv 20, 50 restarts,
- * eig_tol 1e-9, replaced z eigenvalues, plain preconditioner, device 0, default stream. */
+ * eig_tol 1e-9, replaced z eigenvalues, plain preconditioner, 8 start-vector filter passes, device 0,
+ * default stream. */
 void fm_default_opts(fm_opts* opts);
 
 /* Build a context: 1D bases and collocation points (Section 3.1), pointwise potential

@@ -321,6 +321,7 @@ void fm_default_opts(fm_opts* o) {
   o->tune = 0;
   o->y_solver = 0;
   o->mma = FM_MMA_AUTO;
+  o->start_filter = 8;
   o->device = 0;
   o->stream = nullptr;
 }
@@ -377,7 +378,7 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
   if (o.z_eigs == 1 && nM != 1) return FM_ERR_ARG;
   if (o.restart_m < 1 || o.restart_m > 256 || o.max_iters < 1 || !(o.tol > 0) || o.ncv < 3 || o.ncv > 64 ||
       o.max_restarts < 0 || !(o.eig_tol > 0) || o.precision < 0 || o.precision > 2 || o.y_solver < 0 ||
-      o.y_solver > 2 || o.mma < 0 || o.mma > 2)
+      o.y_solver > 2 || o.mma < 0 || o.mma > 2 || o.start_filter < 0 || o.start_filter > 16)
     return FM_ERR_ARG;
   fm_ctx* c = new fm_ctx();
   c->sys = *sys;
@@ -589,6 +590,13 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
   if ((rc = nrm2(c, V, &nv))) return rc;
   if (!(nv > 0.0) || !std::isfinite(nv)) return FM_ERR_ARG;
   if ((rc = scale_copy(c, V, 1.0 / nv, V))) return rc;
+  for (int pass = 0; pass < c->opts.start_filter; ++pass) {  // v <- P^{-1} S v / ||P^{-1} S v||
+    if ((rc = launch_apply(c, 0.0, V, c->tmpN, true))) return rc;
+    if ((rc = launch_precond(c, c->tmpN, c->tmpN2))) return rc;
+    if ((rc = nrm2(c, c->tmpN2, &nv))) return rc;
+    if (!(nv > 0.0) || !std::isfinite(nv)) return FM_ERR_BREAKDOWN;
+    if ((rc = scale_copy(c, c->tmpN2, 1.0 / nv, V))) return rc;
+  }
   std::vector<double> G((size_t)(m + 1) * m, 0.0);  // projected matrix, row-major (m+1) x m
   int kcur = 0, restarts = 0, inner = 0, ops = 0, nsz = 0;
   bool converged = false, accepted_stable = false;
