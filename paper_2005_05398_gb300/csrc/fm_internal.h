@@ -196,7 +196,6 @@ int add32(fm_ctx* c, const float* y, double a, double* x);
 int axpby32(fm_ctx* c, float a, const float* x, float b, float* y);
 int dot_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, double* h_host);
 int dot_many_x(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_host);
-int axpy_many_norm(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double* nrm2_out);
 int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double sign);
 int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_dev,
                  bool lowp = false);

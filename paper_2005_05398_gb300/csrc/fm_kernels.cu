@@ -618,13 +618,12 @@ __device__ __forceinline__ float f64_lead_f32(double d) {
 }
 
 // partial[j][block] = sum over this block's slice of V[j] . w  (j < nv), and for j = nv, when
-// 'extra' is given, extra . w.  The vectors are taken eight at a time so that every thread keeps
-// eight independent loads in flight per element; the eight partial sums are reduced together.
+// 'extra' is given, extra . w; the last block reduces the partials into out[j].  The vectors are read
+// as 16-byte element pairs (n even, 16-byte aligned vectors), eight vectors and two pairs per thread
+// and iteration with every load issued before the FMAs, so that a thread keeps 18 loads of 16 bytes
+// in flight: the kernel is bound by memory latency otherwise.
 // LOWP: products and per-thread sums in float32 from the leading bits of the operands (relative
 // accuracy about 1e-6 of sum |V_j| |w|), for the first Gram-Schmidt pass only.
-// The vectors are read as 16-byte element pairs (n even, 16-byte aligned vectors), eight vectors and
-// two pairs per thread and iteration with every load issued before the FMAs, so that a thread keeps
-// 18 loads of 16 bytes in flight: the kernel is bound by memory latency otherwise.
 __device__ __forceinline__ double dot2(double2 a, double2 b, double acc) { return fma(a.y, b.y, fma(a.x, b.x, acc)); }
 __device__ __forceinline__ float dot2f(double2 a, double2 b, float acc) {
   return fmaf(f64_lead_f32(a.y), f64_lead_f32(b.y), fmaf(f64_lead_f32(a.x), f64_lead_f32(b.x), acc));
@@ -795,44 +794,6 @@ __global__ void k_add32(const float* __restrict__ y, double a, double* __restric
 __global__ void k_axpby32(float a, const float* __restrict__ x, float b, float* __restrict__ y, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i] + (b == 0.0f ? 0.0f : b * y[i]);
-}
-
-// h[j] = sum_b partial[j][b]: one warp per j, fixed order (lane-strided sums, then a shuffle tree)
-__global__ void k_dot_finish(const double* __restrict__ partial, int nb, int nv, double* __restrict__ h) {
-  const int j = blockIdx.x;
-  if (j >= nv) return;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += 32) s += partial[(int64_t)j * nb + b];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (threadIdx.x == 0) h[j] = s;
-}
-
-// w += sign * sum_j h[j] V[j], and partial[block] = sum over the block's elements of the new w^2
-// (grid-stride, four independent accumulators over j so that several loads are in flight)
-__global__ void __launch_bounds__(kRedThreads) k_axpy_many_norm(const double* __restrict__ V, int64_t ldv, int nv,
-                                                               const double* __restrict__ h, double sign,
-                                                               double* __restrict__ w, int64_t n,
-                                                               double* __restrict__ partial, unsigned* counter,
-                                                               double* __restrict__ out) {
-  __shared__ double sh[32];
-  double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int j = 0;
-    for (; j + 3 < nv; j += 4) {
-      s0 = fma(h[j], V[(int64_t)j * ldv + i], s0);
-      s1 = fma(h[j + 1], V[(int64_t)(j + 1) * ldv + i], s1);
-      s2 = fma(h[j + 2], V[(int64_t)(j + 2) * ldv + i], s2);
-      s3 = fma(h[j + 3], V[(int64_t)(j + 3) * ldv + i], s3);
-    }
-    for (; j < nv; ++j) s0 = fma(h[j], V[(int64_t)j * ldv + i], s0);
-    const double v = fma(sign, (s0 + s1) + (s2 + s3), w[i]);
-    w[i] = v;
-    acc = fma(v, v, acc);
-  }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
-  last_block_reduce(partial, 1, counter, out);
 }
 
 // One pass of classical Gram-Schmidt with the coefficients on the device:
@@ -1412,27 +1373,6 @@ int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_h
   c->launches++;
   FM_CUDA(cudaGetLastError());
   return FM_OK;
-}
-
-// w -= V h (h on the host), returns ||w||^2 after the update
-int axpy_many_norm(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_host, double* w, double* nrm2_out) {
-  double* hd = c->gsd + 2 * kGsMaxVec;
-  if (nv > kGsMaxVec) return FM_ERR_ARG;
-  std::memcpy(c->red_host, h_host, nv * sizeof(double));
-  FM_CUDA(cudaMemcpyAsync(hd, c->red_host, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  const int nb = 4 * c->red_blocks;  // grid-stride blocks; one partial each
-  {
-    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
-    k_axpy_many_norm<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, hd, -1.0, w, c->N, c->red, c->gs_cnt,
-                                                        c->gsd + 3 * kGsMaxVec);
-    prof_end(c, tk_, (2.0 * nv + 2.0) * (double)c->N, (nv + 2.0) * 8.0 * (double)c->N);
-  }
-  c->launches++;
-  FM_CUDA(cudaGetLastError());
-  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd + 3 * kGsMaxVec, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  FM_CUDA(cudaStreamSynchronize(c->stream));
-  *nrm2_out = c->red_host[0];
-  return prof_harvest(c);
 }
 
 // Classical Gram-Schmidt with one re-orthogonalisation (CGS2) of w against the orthonormal
