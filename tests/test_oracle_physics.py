@@ -116,7 +116,7 @@ def dmat(J, w):
     return np.array([[ph.wigner_d(J, M, Mp, w) for Mp in range(-J, J + 1)] for M in range(-J, J + 1)])
 
 
-@pytest.mark.parametrize("J", [0, 1, 2, 3, 5])
+@pytest.mark.parametrize("J", [0, 1, 2, 3, 5, 10, 11])
 def test_wigner_d(J):
     w = np.array([0.0, 0.3, 1.7, 3.0, np.pi, 4.4])
     for M in range(-J, J + 1):
@@ -140,14 +140,14 @@ def test_wigner_d_J1_closed_forms():
 
 def test_d_over_sin_is_the_quotient():
     w = np.array([0.2, 1.0, 2.5, 3.5, 5.9])
-    for J, M, Mp, k in ((2, 0, 2, 2), (3, 1, 3, 2), (3, 0, -2, 2), (2, 1, 2, 1)):
+    for J, M, Mp, k in ((2, 0, 2, 2), (3, 1, 3, 2), (3, 0, -2, 2), (2, 1, 2, 1), (10, 3, 9, 6), (11, 0, 11, 8)):
         assert np.allclose(ph.wigner_d_over_sin(J, M, Mp, w, k), ph.wigner_d(J, M, Mp, w) / np.sin(w) ** k, atol=1e-12)
 
 
 def test_F_basis_symmetry():
     """F_{M,-M'} = tau (-1)^{M'} F_{M,M'} (Section 2.2), through the d-functions at (0, w, 0)."""
     w = 1.3
-    for J in (1, 2, 3):
+    for J in (1, 2, 3, 10):
         for tau in (1, -1):
             for M in range(-J, J + 1):
                 for Mp in range(1, J + 1):

@@ -34,7 +34,7 @@ def _interp(g, fx, fy, fz):
     return np.einsum("k,i,j->kij", cz, cx, cy).reshape(-1)
 
 
-@pytest.mark.parametrize("J,tau", [(0, 1), (1, 1), (2, 1), (2, -1)])
+@pytest.mark.parametrize("J,tau", [(0, 1), (1, 1), (2, 1), (2, -1), (10, 1), (11, -1)])
 def test_local_operator_on_polynomials(J, tau):
     """H (without coupling) applied to interpolants of separable cubics equals Eq. FM-pre's
     left operator applied to the cubics, at every collocation point."""
