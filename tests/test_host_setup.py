@@ -52,6 +52,27 @@ def test_z_and_x_decompositions_match_lapack(lib, nint):
         _check(lib, A1, Sx, False)
 
 
+@pytest.mark.parametrize("zmap", [1, 2])
+def test_high_momentum_z_pencils(lib, zmap):
+    """The z problems of J = 10 and 11 (M' up to 11; equidistant and sin-mapped z nodes): real pencils
+    decompose like LAPACK, complex ones are reported."""
+    s = FMSystem(workload("he_l0_24x24x8", nint=(6, 6, 6), R=(40.0, 40.0), J=11, maps=(0, 0, zmap)))
+    g = s.g[1]
+    z = g.az.pts
+    Sz, D1z, D2z = g.az.mat(0), g.az.mat(1), g.az.mat(2)
+    checked = 0
+    for Mp in range(0, 12):
+        Dz = (1 - z * z)[:, None] * D2z - (2 * (Mp + 1) * z)[:, None] * D1z - Mp * (Mp + 1) * Sz
+        ev = sla.eig(Dz, Sz, right=False)
+        if np.abs(ev.imag).max() > 1e-10 * np.abs(ev).max():
+            with pytest.raises(lib.FMError):
+                lib.fm_host_decompose(Dz, Sz, True)
+            continue
+        _check(lib, Dz, Sz, True)
+        checked += 1
+    assert checked >= 4  # the rest are complex at this z grid and are checked to be reported
+
+
 def test_y_pencil_and_complex_detection(lib):
     s = FMSystem(workload("he_l0_24x24x8", nint=(24, 24, 8)))
     g = s.g[1]
