@@ -403,7 +403,7 @@ template <typename T, int LPB, typename SrcF, typename DstF>
 __device__ __forceinline__ void copy_segments(int nseg, int valid, int pb, SrcF src, DstF dst) {
   const int ep = pb / (int)sizeof(T);  // elements per piece
   const int pps = (valid + ep - 1) / ep;
-  const int spr = LPB / pps;           // segments per round
+  const int spr = LPB / pps;           // segments per pass of the CTA
   const int t = threadIdx.x;
   if (t >= spr * pps) return;
   const int k = t % pps;
