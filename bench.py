@@ -100,6 +100,16 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(ms, iters, dist, device):
+    """Whole-job figures of independent replicas: the slowest rank's time and the summed iterations."""
+    import torch
+    t = torch.tensor([float(ms), float(iters)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return tmax[0].item(), t[1].item()
+
+
 def roofline(prof, peaks, wname=WORKLOAD):
     """The dominant kernel class (largest device time) against its roofline."""
     bound_of = {"apply_xy": "alu", "apply_z": "alu", "coupling": "alu", "dot": "alu", "axpy": "alu",
@@ -232,11 +242,7 @@ def run_ours(args):
     launches = ctx.fm_stats()["launches"] - launches0
     iters = sum(i["iters"] for i in infos)
     if dist:
-        t = torch.tensor([ms, float(iters)], dtype=torch.float64, device=f"cuda:{local}")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max, iters_all = tmax[0].item(), t[1].item()
+        ms_max, iters_all = reduce_over_ranks(ms, iters, dist, f"cuda:{local}")
     else:
         ms_max, iters_all = ms, float(iters)
     value = iters_all / (ms_max * 1e-3)
