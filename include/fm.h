@@ -136,6 +136,11 @@ typedef struct {
   double ms;          /* wall time of the call */
 } fm_info;
 
+/* A context holds one problem's tables, factors and Krylov workspace on one device and orders its
+ * work on its stream.  One context must not be used by two host threads at once; different contexts
+ * may be used concurrently from different threads (each on its own stream), which is how the request
+ * loop below runs several problems side by side.  Calls that return host results (fm_solve, fm_eigs,
+ * fm_precond_apply, ...) synchronise the context's stream before they return. */
 typedef struct fm_ctx fm_ctx;
 
 /* Default options: tol 1e-12, restart 64, max_iters 2000, FP64, ncv 20, 50 restarts,
