@@ -19,8 +19,9 @@
  *    j_y fastest.  Solved components: particles {1, 3} when particles 1 and 2 are
  *    identical (Eq. 2-sym-part), {1, 2, 3} otherwise, {1} in the Schrodinger limit.
  *  - All work is ordered on the context's stream (fm_opts.stream, or the legacy
- *    default stream when NULL).  fm_apply / fm_apply_S / fm_precond_apply return
- *    without synchronising; fm_solve / fm_eigs synchronise before they return.
+ *    default stream when NULL).  fm_apply / fm_apply_S return without synchronising;
+ *    fm_precond_apply synchronises when its tensor-core stages ran (it reads their wait
+ *    flag); fm_solve / fm_eigs synchronise before they return.
  *  - A context is used by one host thread at a time.
  *  - Energies are in the units of the reduced-coordinate equations (Hartree for
  *    electron-mass units); box sizes R_x, R_y are in reduced Jacobi coordinates.
@@ -136,11 +137,9 @@ typedef struct {
   double ms;          /* wall time of the call */
 } fm_info;
 
-/* A context holds one problem's tables, factors and Krylov workspace on one device and orders its
- * work on its stream.  One context must not be used by two host threads at once; different contexts
- * may be used concurrently from different threads (each on its own stream), which is how the request
- * loop below runs several problems side by side.  Calls that return host results (fm_solve, fm_eigs,
- * fm_precond_apply, ...) synchronise the context's stream before they return. */
+/* A context holds one problem's tables, factors and Krylov workspace on one device.  Different
+ * contexts may be used concurrently from different host threads (each on its own stream), which is
+ * how the request loop below runs several problems side by side. */
 typedef struct fm_ctx fm_ctx;
 
 /* Default options: tol 1e-12, restart 64, max_iters 2000, FP64, ncv 20, 50 restarts,
