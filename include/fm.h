@@ -229,7 +229,8 @@ int fm_stats(const fm_ctx* ctx, int64_t* launches, int64_t* device_bytes);
  * (three planes of n_unknowns doubles) is a fixed array inside the library, 24 MiB that every
  * GPU loading the library holds until the process exits; n_unknowns above
  * FM_NOALLOC_MAX_UNKNOWNS gives FM_ERR_SCRATCH_LIMIT.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress, with that device current).  All calls
+ * the array's device address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture begins.  All calls
  * share the array: two calls whose kernels overlap on the GPU (different streams or
  * contexts running concurrently) race on it and produce wrong results.  Nothing in the
  * array needs clearing between calls.  Device buffers x and y must not overlap. */
