@@ -124,17 +124,33 @@ typedef struct {
   int start_filter;  /* fm_eigs: passes v <- P^{-1} S v / |.| applied to the start vector before the Arnoldi
                         process (the tensor preconditioner approximates (H - E* S)^{-1}, so each pass
                         enriches the directions of the levels nearest the shift); 0..16, default 8 */
+  int refine;        /* fm_eigs: most inverse-iteration steps c <- (H - shift S)^{-1} S c / |.| (float64 solves
+                        to tol) given to a returned pair whose backward error is above eig_tol; 0..8, default 2 */
   int device;        /* CUDA device ordinal */
   void* stream;      /* cudaStream_t, NULL = legacy default stream */
 } fm_opts;
 
+/* How fm_eigs' Arnoldi iteration stopped (fm_info.accept). */
+enum {
+  FM_ACCEPT_NONE = 0,    /* restart limit or breakdown before either rule held */
+  FM_ACCEPT_RITZ = 1,    /* every wanted Ritz pair met |h_{m+1,m} y_m| / |theta| <= eig_tol */
+  FM_ACCEPT_STABLE = 2   /* some pair only met the stable-energy rule (see fm_opts.eig_tol) */
+};
+
 typedef struct {
-  int iters;          /* FGMRES iterations (fm_solve) or total inner iterations (fm_eigs) */
+  int iters;          /* FGMRES iterations (fm_solve) or total inner iterations (fm_eigs, refinement included) */
   int restarts;       /* FGMRES restarts (refinement steps in FM_PREC_MIXED) or Arnoldi restarts */
-  int op_applies;     /* shift-invert operator applications (fm_eigs) */
+  int op_applies;     /* shift-invert operator applications (fm_eigs, refinement included) */
   int converged;      /* 1 when every requested quantity met its tolerance */
-  double resid;       /* final relative residual (fm_solve) or max eigen-residual (fm_eigs) */
+  double resid;       /* fm_solve: final relative residual |b - (H - E S) x| / |b|;
+                         fm_eigs: largest backward error eta of the returned pairs (see fm_eigs) */
   double ms;          /* wall time of the call */
+  int accept;         /* fm_eigs: FM_ACCEPT_* rule that stopped the Arnoldi iteration */
+  int refine_steps;   /* fm_eigs: inverse-iteration steps taken by the final float64 refinement (all pairs) */
+  double resid_S;     /* fm_eigs: largest |H c - E S c| / |S c| of the returned pairs */
+  double norm_H;      /* fm_eigs: the estimates of |H|_2 and |S|_2 in the backward error (power-iteration */
+  double norm_S;      /*          lower bounds, so that eta is never underestimated through them) */
+  double rq_dev;      /* fm_eigs: largest |E_R - E| / |E|, E_R = (S c)^T (H c) / |S c|^2 the Rayleigh estimate */
 } fm_info;
 
 /* A context holds one problem's tables, factors and Krylov workspace on one device.  Different
@@ -143,8 +159,8 @@ typedef struct {
 typedef struct fm_ctx fm_ctx;
 
 /* Default options: tol 1e-12, restart 64, max_iters 2000, FP64, ncv 20, 50 restarts,
- * eig_tol 1e-9, replaced z eigenvalues, plain preconditioner, 8 start-vector filter passes, device 0,
- * default stream. */
+ * eig_tol 1e-9, replaced z eigenvalues, plain preconditioner, 8 start-vector filter passes, 2 refinement
+ * steps, device 0, default stream. */
 void fm_default_opts(fm_opts* opts);
 
 /* Build a context: 1D bases and collocation points (Section 3.1), pointwise potential
@@ -195,9 +211,17 @@ int fm_solve(fm_ctx* ctx, double E, const double* rhs, double* x, fm_info* info)
  * operator application an FGMRES solve to max(tol, eig_tol / 10).  v0 (device, may be NULL = seeded normal start)
  * starts the iteration.  Only real eigenvalues are returned: complex-conjugate pairs of the
  * non-symmetric collocation pencil (non-physical in the bound-state problem) are passed over,
- * so the result is the k real eigenvalues nearest the shift.  An inner solve that ends more
- * than 1e4 times above its tolerance makes the call report FM_ERR_NOT_CONVERGED.
- * evals (host, k doubles) receive E sorted by |E - shift|;
+ * so the result is the k real eigenvalues nearest the shift.
+ * Final float64 certificate: for each returned pair, E = shift + 1/theta (the Ritz value) and its Ritz
+ * vector c (|c| = 1), the library forms H c and S c with the float64 operator and the backward error
+ * eta = |H c - E S c| / (|H| + |E| |S|): (E, c) is an exact eigenpair of a pencil within relative distance
+ * eta of (H, S).  A pair with eta > eig_tol gets up to opts.refine inverse-iteration steps
+ * c <- (H - shift S)^{-1} S c / |.|, E = shift + 1 / (c^T (H - shift S)^{-1} S c), a step kept only when it
+ * lowers eta.  The call returns FM_OK only when every pair ends with eta <= eig_tol, whichever rule stopped
+ * the Arnoldi iteration (info->accept); otherwise FM_ERR_NOT_CONVERGED with the pairs as computed.  The
+ * Rayleigh estimate E_R = (S c)^T (H c) / |S c|^2 is reported as a check (info->rq_dev): it weighs the
+ * high-frequency error of c with |H| and is less accurate than the Ritz value of the shift-invert operator.
+ * evals (host, k doubles) receive the certified E sorted by |E - shift|;
  * evecs (device, k * n_unknowns, may be NULL) the eigenvectors normalised to unit
  * 2-norm with their largest-magnitude entry positive.  info may be NULL. */
 int fm_eigs(fm_ctx* ctx, double shift, int k, const double* v0, double* evals, double* evecs, fm_info* info);
@@ -230,7 +254,9 @@ int fm_stats(const fm_ctx* ctx, int64_t* launches, int64_t* device_bytes);
  * GPU loading the library holds until the process exits; n_unknowns above
  * FM_NOALLOC_MAX_UNKNOWNS gives FM_ERR_SCRATCH_LIMIT.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture begins.  All calls
+ * call before any stream capture begins.  The address is kept per device and CUDA context: after a
+ * cudaDeviceReset (or a new primary context) the next call looks it up again, so that call, too,
+ * must come before any stream capture.  All calls
  * share the array: two calls whose kernels overlap on the GPU (different streams or
  * contexts running concurrently) race on it and produce wrong results.  Nothing in the
  * array needs clearing between calls.  Device buffers x and y must not overlap. */
@@ -314,8 +340,10 @@ typedef struct {
   double t_submit_ms, t_start_ms, t_end_ms;
 } fm_result;
 
-/* hbm_budget <= 0: 90 % of the device memory (ignored with FM_SERVER_DRY_RUN, where it must be
- * > 0).  slots in 1..64. */
+/* hbm_budget <= 0: the device memory free at creation (cudaMemGetInfo) less 5 % of the device, so that
+ * memory already held by other allocators in the process (a framework's caching allocator, other
+ * contexts) is not promised to requests; FM_ERR_OOM when nothing is left.  With FM_SERVER_DRY_RUN the
+ * budget must be given (> 0).  slots in 1..64. */
 int fm_server_create(int device, int64_t hbm_budget, int slots, int flags, fm_server** out);
 
 /* Enqueue a request (copied); *id identifies it.  FM_ERR_OOM when the request alone exceeds the

@@ -35,12 +35,13 @@ class fm_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("restart_m", c_int), ("max_iters", c_int), ("precision", c_int),
                 ("ncv", c_int), ("max_restarts", c_int), ("eig_tol", c_double), ("z_eigs", c_int),
                 ("y_solver", c_int), ("tune", c_int), ("mma", c_int), ("start_filter", c_int),
-                ("device", c_int), ("stream", c_void_p)]
+                ("refine", c_int), ("device", c_int), ("stream", c_void_p)]
 
 
 class fm_info(ctypes.Structure):
     _fields_ = [("iters", c_int), ("restarts", c_int), ("op_applies", c_int), ("converged", c_int),
-                ("resid", c_double), ("ms", c_double)]
+                ("resid", c_double), ("ms", c_double), ("accept", c_int), ("refine_steps", c_int),
+                ("resid_S", c_double), ("norm_H", c_double), ("norm_S", c_double), ("rq_dev", c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

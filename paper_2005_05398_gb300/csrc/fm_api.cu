@@ -301,6 +301,59 @@ struct Ritz {
   bool real;
 };
 
+// Lower bounds of |H|_2 and |S|_2: the largest |A v| over four normalised power steps from a seeded
+// start (|A v| <= |A|_2 for every unit v).  The backward error of fm_eigs divides by them, so an
+// underestimate can only make the reported error larger.  Computed once per context.
+static int operator_norms(fm_ctx* c, double* nH, double* nS) {
+  int rc;
+  if (!(c->normH > 0.0 && c->normS > 0.0)) {
+    double est[2] = {0.0, 0.0};
+    for (int which = 0; which < 2; ++which) {
+      double* v = c->tmpN;
+      double* w = c->tmpN2;
+      if ((rc = fill_normal(c, v, 0x5eedf00dull + (uint64_t)which))) return rc;
+      double nv;
+      if ((rc = nrm2(c, v, &nv))) return rc;
+      if ((rc = scale_copy(c, v, 1.0 / nv, v))) return rc;
+      for (int it = 0; it < 4; ++it) {
+        if ((rc = launch_apply(c, 0.0, v, w, which == 1))) return rc;
+        double nw;
+        if ((rc = nrm2(c, w, &nw))) return rc;
+        if (!(nw > 0.0) || !std::isfinite(nw)) return FM_ERR_NUMERIC;
+        est[which] = std::max(est[which], nw);
+        if ((rc = scale_copy(c, w, 1.0 / nw, v))) return rc;
+      }
+    }
+    c->normH = est[0];
+    c->normS = est[1];
+  }
+  *nH = c->normH;
+  *nS = c->normS;
+  return FM_OK;
+}
+
+// Float64 certificate of the pair (E, c) with |c| = 1: the backward error eta = |H c - E S c| / (|H| + |E| |S|),
+// |H c - E S c| / |S c|, and the Rayleigh estimate E_R = (S c)^T (H c) / |S c|^2 (the E that minimises the
+// residual, reported as a consistency check).  Uses tmpN and tmpN2.
+static int certify(fm_ctx* c, const double* cv, double E, double nH, double nS, double* eta, double* resS,
+                   double* E_R) {
+  int rc;
+  double* Hc = c->tmpN;
+  double* Sc = c->tmpN2;
+  if ((rc = launch_apply(c, 0.0, cv, Hc, false))) return rc;
+  if ((rc = launch_apply(c, 0.0, cv, Sc, true))) return rc;
+  double sh = 0.0, ss = 0.0;
+  if ((rc = dot_many(c, Sc, c->N, 1, Hc, &sh)) || (rc = dot_many(c, Sc, c->N, 1, Sc, &ss))) return rc;
+  if (!(ss > 0.0) || !std::isfinite(ss) || !std::isfinite(sh)) return FM_ERR_BREAKDOWN;
+  *E_R = sh / ss;
+  if ((rc = axpby(c, -E, Sc, 1.0, Hc))) return rc;  // Hc <- H c - E S c
+  double rn;
+  if ((rc = nrm2(c, Hc, &rn))) return rc;
+  *eta = rn / (nH + std::fabs(E) * nS);
+  *resS = rn / std::sqrt(ss);
+  return FM_OK;
+}
+
 }  // namespace fmi
 
 using namespace fmi;
@@ -322,6 +375,7 @@ void fm_default_opts(fm_opts* o) {
   o->y_solver = 0;
   o->mma = FM_MMA_AUTO;
   o->start_filter = 8;
+  o->refine = 2;
   o->device = 0;
   o->stream = nullptr;
 }
@@ -378,7 +432,7 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
   if (o.z_eigs == 1 && nM != 1) return FM_ERR_ARG;
   if (o.restart_m < 1 || o.restart_m > 256 || o.max_iters < 1 || !(o.tol > 0) || o.ncv < 3 || o.ncv > 64 ||
       o.max_restarts < 0 || !(o.eig_tol > 0) || o.precision < 0 || o.precision > 2 || o.y_solver < 0 ||
-      o.y_solver > 2 || o.mma < 0 || o.mma > 2 || o.start_filter < 0 || o.start_filter > 16)
+      o.y_solver > 2 || o.mma < 0 || o.mma > 2 || o.start_filter < 0 || o.start_filter > 16 || o.refine < 0 || o.refine > 8)
     return FM_ERR_ARG;
   fm_ctx* c = new fm_ctx();
   c->sys = *sys;
@@ -604,7 +658,6 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
   std::vector<double> Y;  // eigenvectors of the projected matrix (nsz x nsz)
   std::vector<std::vector<double>> hist;  // eigenvalue history of each wanted Ritz value
   const bool verbose = getenv("FM_VERBOSE") != nullptr;
-  double worst_inner = 0.0;  // largest (final relative residual / requested tolerance) of an inner solve
   // The tuned preconditioner speeds up inner solves that converge; once an inner solve stalls far above
   // its tolerance (the shift sits in a cluster of levels and the solves reach their float64 floor), the
   // tuning is dropped for the rest of the eigen-solve: its rank-k correction then steers the inexact
@@ -645,7 +698,6 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
       inner += it;
       ++ops;
       if (rc != FM_OK && rc != FM_ERR_NOT_CONVERGED) return rc;
-      worst_inner = std::max(worst_inner, res / inner_tol);
       if (res > 100.0 * inner_tol && c->n_tune > 0) {
         tune_ok = false;
         c->n_tune = 0;
@@ -745,13 +797,9 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
     ++restarts;
   }
   c->n_tune = 0;
-  // an inner solve that stalled far above its tolerance makes the Krylov relation, and so the Ritz
-  // residual, unreliable; energies that stayed stable over three steps do not rest on that residual
-  if (worst_inner > 1e4 && !accepted_stable) converged = false;
+  const int accept = converged ? (accepted_stable ? FM_ACCEPT_STABLE : FM_ACCEPT_RITZ) : FM_ACCEPT_NONE;
   if (nsz < k || (int)best.size() < k) return FM_ERR_NOT_CONVERGED;
-  // eigenvectors c = V y, energies E = shift + 1/theta
   std::vector<double> Ek(k);
-  std::vector<double> res_k(k, 0.0);
   for (int i = 0; i < k; ++i) {
     if (!best[i].real) return FM_ERR_NOT_CONVERGED;
     Ek[i] = shift + 1.0 / best[i].theta;
@@ -759,39 +807,93 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
   std::vector<int> ord(k);
   for (int i = 0; i < k; ++i) ord[i] = i;
   std::sort(ord.begin(), ord.end(), [&](int a, int b) { return std::fabs(Ek[a] - shift) < std::fabs(Ek[b] - shift); });
+  // Float64 certificate of every returned pair, whichever rule stopped the iteration above: the Ritz value
+  // E = shift + 1/theta with its Ritz vector c, and the backward error eta of (E, c) formed with the float64
+  // operator.  A pair above eig_tol gets inverse-iteration steps z = (H - shift S)^{-1} S c with the
+  // shift-invert operator's Rayleigh quotient theta = c^T z (|c| = 1), E = shift + 1/theta, a step kept only
+  // when it lowers eta.  The call converges when every pair ends at eta <= eig_tol.  (The energy stays the
+  // operator's Ritz value: the one-sided Rayleigh estimate through H weighs the high-frequency error of c
+  // with |H| and is the less accurate of the two; it is reported as a check.)
+  double nH, nS;
+  if ((rc = operator_norms(c, &nH, &nS))) return rc;
+  std::vector<double> eta_k(k, 0.0), resS_k(k, 0.0);
+  double rq_dev = 0.0;
+  int refine_steps = 0;
+  bool certified = true;
+  double* cvec = c->tmpN3;
+  double* z = c->tuneU;           // free once the eigen-iteration has ended (n_tune = 0)
+  double* keep = c->tuneU + N;
   for (int ii = 0; ii < k; ++ii) {
     const int i = ord[ii];
     std::vector<double> yv(nsz);
     for (int r = 0; r < nsz; ++r) yv[r] = Y[(size_t)r * nsz + best[i].col];
-    double* cvec = c->tmpN3;
     if ((rc = combine(c, V, N, nsz, yv.data(), 1, cvec, N))) return rc;
-    double nr, mx;
+    double nr;
     if ((rc = nrm2(c, cvec, &nr))) return rc;
+    if (!(nr > 0.0) || !std::isfinite(nr)) return FM_ERR_BREAKDOWN;
+    if ((rc = scale_copy(c, cvec, 1.0 / nr, cvec))) return rc;
+    double E = Ek[i], eta, resS, ER;
+    if ((rc = certify(c, cvec, E, nH, nS, &eta, &resS, &ER))) return rc;
+    for (int step = 0; step < c->opts.refine && eta > c->opts.eig_tol; ++step) {
+      if ((rc = launch_apply(c, 0.0, cvec, c->tmpN2, true))) return rc;  // S c
+      FM_CUDA(cudaMemsetAsync(z, 0, N * 8, c->stream));
+      int it = 0, rs = 0;
+      double res = 0.0;
+      rc = solve_any(c, shift, c->tmpN2, z, c->opts.tol, c->opts.max_iters, &it, &rs, &res);
+      inner += it;
+      ++ops;
+      ++refine_steps;
+      if (rc != FM_OK && rc != FM_ERR_NOT_CONVERGED) return rc;
+      double th = 0.0, nz;
+      if ((rc = dot_many(c, cvec, N, 1, z, &th)) || (rc = nrm2(c, z, &nz))) return rc;
+      if (!(nz > 0.0) || !std::isfinite(nz) || th == 0.0 || !std::isfinite(th)) break;
+      FM_CUDA(cudaMemcpyAsync(keep, cvec, N * 8, cudaMemcpyDeviceToDevice, c->stream));
+      if ((rc = scale_copy(c, z, 1.0 / nz, cvec))) return rc;
+      const double E2 = shift + 1.0 / th;
+      double eta2, resS2, ER2;
+      if ((rc = certify(c, cvec, E2, nH, nS, &eta2, &resS2, &ER2))) return rc;
+      if (!(eta2 < eta)) {  // no gain: keep the previous pair and stop
+        FM_CUDA(cudaMemcpyAsync(cvec, keep, N * 8, cudaMemcpyDeviceToDevice, c->stream));
+        break;
+      }
+      E = E2;
+      eta = eta2;
+      resS = resS2;
+      ER = ER2;
+    }
+    double mx;
     if ((rc = absmax(c, cvec, &mx))) return rc;
-    const double sc = (mx < 0 ? -1.0 : 1.0) / nr;
-    if ((rc = scale_copy(c, cvec, sc, cvec))) return rc;
-    // eigen-residual ||H c - E S c|| / ||S c|| in float64
-    if ((rc = launch_apply(c, Ek[i], cvec, c->tmpN, false))) return rc;
-    if ((rc = launch_apply(c, 0.0, cvec, c->tmpN2, true))) return rc;
-    double rn, sn;
-    if ((rc = nrm2(c, c->tmpN, &rn)) || (rc = nrm2(c, c->tmpN2, &sn))) return rc;
-    res_k[ii] = rn / sn;
-    evals[ii] = Ek[i];
+    if (mx < 0) {
+      if ((rc = scale_copy(c, cvec, -1.0, cvec))) return rc;
+    }
+    eta_k[ii] = eta;
+    resS_k[ii] = resS;
+    rq_dev = std::max(rq_dev, std::fabs(ER - E) / std::max(std::fabs(E), 1e-300));
+    evals[ii] = E;
+    if (!(eta <= c->opts.eig_tol)) certified = false;
     if (evecs) FM_CUDA(cudaMemcpyAsync(evecs + (int64_t)ii * N, cvec, N * 8, cudaMemcpyDeviceToDevice, c->stream));
   }
   FM_CUDA(cudaStreamSynchronize(c->stream));
+  if (verbose)
+    for (int ii = 0; ii < k; ++ii)
+      fprintf(stderr, "[fm_eigs] pair %d: E %.15f eta %.3e |r|/|Sc| %.3e (|H| %.3e |S| %.3e)\n", ii, evals[ii],
+              eta_k[ii], resS_k[ii], nH, nS);
   if (info) {
     std::memset(info, 0, sizeof(*info));
     info->iters = inner;
     info->restarts = restarts;
     info->op_applies = ops;
-    info->converged = converged;
-    double mr = 0.0;
-    for (double r : res_k) mr = std::max(mr, r);
-    info->resid = mr;
+    info->converged = certified ? 1 : 0;
+    info->resid = *std::max_element(eta_k.begin(), eta_k.end());
+    info->resid_S = *std::max_element(resS_k.begin(), resS_k.end());
+    info->norm_H = nH;
+    info->norm_S = nS;
+    info->rq_dev = rq_dev;
+    info->accept = accept;
+    info->refine_steps = refine_steps;
     info->ms = wall_ms() - t0;
   }
-  return converged ? FM_OK : FM_ERR_NOT_CONVERGED;
+  return certified ? FM_OK : FM_ERR_NOT_CONVERGED;
 }
 
 int fm_eigs_host(fm_ctx* c, double shift, int k, const double* v0_host, double* evals, double* evecs_host, fm_info* info) {

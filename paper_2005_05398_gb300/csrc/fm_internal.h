@@ -159,6 +159,7 @@ struct fm_ctx {
   double* tuneU = nullptr;       // [8][N]
   double* tuneWU = nullptr;      // [8][N]  W - U
   std::vector<double> tuneGinv;  // (U^T W)^{-1}, n_tune x n_tune, row-major
+  double normH = 0.0, normS = 0.0;  // power-iteration lower bounds of |H|_2 and |S|_2 (0 = not yet estimated)
   bool tc_active = false;        // float32 preconditioner x / y stages on the tensor cores
   int* tc_err = nullptr;         // device flag: a bounded wait of a tensor-core kernel expired
   int64_t launches = 0;

@@ -6,6 +6,7 @@
 // FM_NOALLOC_MAX_UNKNOWNS * 3 doubles (24 MiB) for it until the process exits.  Host code may not
 // use the array's name as a device address (in host code it names a host-side stand-in), so the
 // device address is obtained once per device with cudaGetSymbolAddress, with that device current.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -18,22 +19,49 @@ namespace {
 static __device__ __align__(256) double g_apply_scratch[3 * (size_t)FM_NOALLOC_MAX_UNKNOWNS];
 
 constexpr int kMaxDevices = 64;
-double* g_scratch_dev[kMaxDevices] = {nullptr};
+struct ScratchSlot {
+  CUcontext ctx = nullptr;   // the context the address was looked up in
+  double* addr = nullptr;
+};
+ScratchSlot g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
 
-// Device address of the scratch array on the current device (looked up on first use).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+CtxGetCurrentFn ctx_get_current() {
+  static std::once_flag once;
+  static CtxGetCurrentFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  });
+  return fn;
+}
+
+// Device address of the scratch array in the current context of `device` (current on entry).  The
+// address belongs to the module instance of that context: after a cudaDeviceReset, or when the primary
+// context was released and made again, the context differs and the address is looked up anew.
 int scratch_address(int device, double** out) {
   if (device < 0 || device >= kMaxDevices) return FM_ERR_ARG;
+  CtxGetCurrentFn get = ctx_get_current();
+  CUcontext cur = nullptr;
+  if (!get || get(&cur) != CUDA_SUCCESS || !cur) return FM_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_dev[device]) {
+  ScratchSlot& slot = g_scratch[device];
+  if (!slot.addr || slot.ctx != cur) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_apply_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
+      slot = ScratchSlot{};
       return FM_ERR_CUDA;
     }
-    g_scratch_dev[device] = static_cast<double*>(p);
+    slot.ctx = cur;
+    slot.addr = static_cast<double*>(p);
   }
-  *out = g_scratch_dev[device];
+  *out = slot.addr;
   return FM_OK;
 }
 

@@ -183,7 +183,10 @@ int fm_server_create(int device, int64_t hbm_budget, int slots, int flags, fm_se
   if (!(flags & FM_SERVER_DRY_RUN) && hbm_budget <= 0) {
     size_t fr = 0, tot = 0;
     if (cudaSetDevice(device) != cudaSuccess || cudaMemGetInfo(&fr, &tot) != cudaSuccess) return FM_ERR_CUDA;
-    hbm_budget = (int64_t)(0.9 * (double)tot);
+    // what is free now (another allocator in the process may hold part of the device), less a margin of
+    // 5 % of the device for the CUDA context, the library's module and allocator slack
+    hbm_budget = (int64_t)fr - (int64_t)(0.05 * (double)tot);
+    if (hbm_budget <= 0) return FM_ERR_OOM;
   }
   fm_server* s = new fm_server();
   s->device = device;

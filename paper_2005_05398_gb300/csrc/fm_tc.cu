@@ -105,6 +105,19 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
       : "memory");
 }
 
+// kind::f16 with BF16 A and B, float32 accumulation (same descriptor conventions as the TF32 form)
+__host__ __device__ constexpr uint32_t bf16_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -405,6 +418,506 @@ __global__ void __launch_bounds__(kZThreads) k_zmix_rb(const float* __restrict__
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Operand formats of the tensor-core mode products.  TF32: float32 storage, 32 elements per
+// 128-byte row of a swizzled K-major tile, K = 8 per MMA.  BF16: 64 elements per row, K = 16.
+// Both advance 32 bytes of K per MMA instruction.
+// ---------------------------------------------------------------------------
+struct OpTF32 {
+  using T = float;
+  static constexpr int kRow = 32;
+  static constexpr int kStep = 8;
+  static __device__ __forceinline__ uint32_t idesc(int n) { return tf32_idesc(n); }
+  static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    mma_tf32(d, a, b, id, acc);
+  }
+  static __device__ __forceinline__ float from(float v) { return v; }
+  static __device__ __forceinline__ float to_f(float v) { return v; }
+};
+struct OpBF16 {
+  using T = uint16_t;  // bfloat16 bits
+  static constexpr int kRow = 64;
+  static constexpr int kStep = 16;
+  static __device__ __forceinline__ uint32_t idesc(int n) { return bf16_idesc(n); }
+  static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    mma_bf16(d, a, b, id, acc);
+  }
+  static __device__ __forceinline__ uint16_t from(float v) {  // round to nearest even
+    uint16_t h;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(v));
+    return h;
+  }
+  static __device__ __forceinline__ float to_f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+};
+
+template <typename T>
+__device__ __forceinline__ float load_as_float(const T* p) { return (float)*p; }
+template <>
+__device__ __forceinline__ float load_as_float<uint16_t>(const uint16_t* p) { return __uint_as_float((uint32_t)*p << 16); }
+template <typename T>
+__device__ __forceinline__ void store_from_float(T* p, float v) { *p = (T)v; }
+template <>
+__device__ __forceinline__ void store_from_float<uint16_t>(uint16_t* p, float v) { *p = OpBF16::from(v); }
+
+// Byte offset of (row, byte within the 128-byte row) in a 128-byte-swizzled K-major tile whose base is
+// 1024-byte aligned: 8-row atoms of 1024 bytes, the 16-byte chunks of row r permuted by XOR with r mod 8.
+__device__ __forceinline__ uint32_t sw128(int row, int byte) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((byte >> 4) ^ row) & 7) << 4) + (byte & 15));
+}
+
+__device__ __forceinline__ void st_shared_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_shared_u16(uint32_t addr, uint16_t v) {
+  asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+template <typename Op>
+__device__ __forceinline__ void st_elem(uint32_t addr, float v) {
+  if constexpr (sizeof(typename Op::T) == 4) st_shared_u32(addr, __float_as_uint(v));
+  else st_shared_u16(addr, Op::from(v));
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// z mode products on the tensor cores (Eq. prec-2, the W-bar_z and W_z stages):
+//   out[M'][l][p] = sum_k W[M'][l][k] in[M'][k][p]
+// for every point p = (i, j) of a component.  A = W (rows l, K = k; n_z <= 128, TMA-loaded,
+// zero-filled to 128 rows and to the K padding), B = a tile of 128 points (rows) with their n_z values
+// (K), converted from the input type while it is written into shared memory, D in tensor memory
+// (128 lanes l x 128 columns p).  Persistent CTAs walk the (M', point tile) list.
+//   OUT_JI (forward):  in x[M'][k][i][j] -> out t[slab][j][i]; tiles of 32 i x 4 j, B row = jj * 32 + ii
+//   !OUT_JI (inverse): in u[slab][j][i]  -> out y[M'][k][i][j]; tiles of 8 i x 16 j, B row = ii * 16 + jj
+// (slab = M' * n_z + l).  Each thread of the epilogue owns one output plane l and writes runs of 32
+// (forward) or 16 (inverse) consecutive elements of it.
+// ---------------------------------------------------------------------------
+struct TcZArgs {
+  const void* in;
+  void* out;
+  int nz, nx, ny, nM;
+  int64_t off;         // component offset (elements) in both vectors
+  int tiles_i, tiles_j;
+  int kblocks;         // 128-byte K blocks of A and B
+  int ksteps;          // MMA instructions per tile
+  int* err;
+};
+
+template <typename TI, typename Op, typename TO, bool OUT_JI>
+__global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMap tmW, const TcZArgs a) {
+  using TB = typename Op::T;
+  constexpr int TI_ = OUT_JI ? 32 : 8, TJ_ = OUT_JI ? 4 : 16;
+  constexpr int kTile = 128 * 128;  // bytes of one K block (128 rows x 128 bytes)
+  extern __shared__ unsigned char tz_smem[];
+  const uint32_t raw = smem_u32(tz_smem);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = tz_smem + (base - raw);
+  const uint32_t sA = base, sB = base + (uint32_t)a.kblocks * kTile;
+  const uint32_t bars = sB + (uint32_t)a.kblocks * kTile;
+  const uint32_t abar = bars, mdone = bars + 8, slot = bars + 16;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bars - base) + 24);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(abar, 1);
+    mbar_init(mdone, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(128) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + (slot - base));
+  const int64_t nxy = (int64_t)a.nx * a.ny;
+  const int ntiles = a.tiles_i * a.tiles_j;
+  const int kpad = a.ksteps * Op::kStep;
+  const TI* in = static_cast<const TI*>(a.in);
+  TO* out = static_cast<TO*>(a.out);
+  int cur_iM = -1, a_loads = 0;
+  uint32_t a_phase = 0, m_phase = 0;
+  // thread -> point of the tile for coalesced loads (the contiguous index runs across lanes)
+  const int ii = OUT_JI ? tid / TJ_ : tid % TI_;
+  const int jj = OUT_JI ? tid % TJ_ : tid / TI_;
+  const int prow = OUT_JI ? jj * TI_ + ii : ii * TJ_ + jj;
+  for (int q = blockIdx.x; q < ntiles * a.nM; q += gridDim.x) {
+    const int iM = q / ntiles, t = q - iM * ntiles;
+    const int i0 = (t / a.tiles_j) * TI_, j0 = (t % a.tiles_j) * TJ_;
+    const bool reload = iM != cur_iM;
+    if (reload && tid == 0) {  // W of this M' (every thread of the previous tile has passed the MMA wait)
+      mbar_expect_tx(abar, (uint32_t)a.kblocks * kTile);
+      for (int kb = 0; kb < a.kblocks; ++kb) tma_load_3d(sA + kb * kTile, &tmW, kb * Op::kRow, 0, iM, abar);
+    }
+    if (reload) {
+      cur_iM = iM;
+      ++a_loads;
+    }
+    // B tile: row prow, K = k
+    {
+      const int i = i0 + ii, j = j0 + jj;
+      const bool ok = i < a.nx && j < a.ny;
+      const int64_t src = OUT_JI ? a.off + ((int64_t)iM * a.nz * a.nx + i) * a.ny + j
+                                 : a.off + ((int64_t)iM * a.nz * a.ny + j) * a.nx + i;
+      for (int k0 = 0; k0 < kpad; k0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int k = k0 + u;
+          v[u] = (ok && k < a.nz) ? load_as_float<TI>(in + src + (int64_t)k * nxy) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int k = k0 + u;
+          if (k < kpad) {
+            const int kb = k / Op::kRow, byte = (k % Op::kRow) * (int)sizeof(TB);
+            st_elem<Op>(sB + kb * kTile + sw128(prow, byte), v[u]);
+          }
+        }
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 32) {
+      bool ok = !*abort_flag;
+      if (ok && reload) {
+        ok = mbar_wait(abar, a_phase);
+        if (!ok) *abort_flag = 1;
+      }
+      if (ok) {
+        tc_fence_after();
+        const uint32_t id = Op::idesc(128);
+        for (int ks = 0; ks < a.ksteps; ++ks) {
+          const int kb = (ks * Op::kStep) / Op::kRow, kin = (ks * Op::kStep) % Op::kRow;
+          const uint32_t off = (uint32_t)(kb * kTile) + (uint32_t)(kin * (int)sizeof(TB));
+          Op::mma(tmem, sw128_desc(sA + off), sw128_desc(sB + off), id, ks ? 1u : 0u);
+        }
+      }
+      mma_commit(mdone);  // arrives when the MMAs above (if any) have completed
+    }
+    if (reload) a_phase ^= 1u;
+    const bool ready = mbar_wait(mdone, m_phase);
+    m_phase ^= 1u;
+    tc_fence_after();
+    if (!ready) *abort_flag = 1;
+    if (__syncthreads_or(*abort_flag)) break;
+    // epilogue: thread = output plane l (its TMEM lane), 32 columns (points) per load
+    const int l = warp * 32 + lane;
+    for (int c0 = 0; c0 < 128; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (l >= a.nz) continue;
+      const int64_t plane = (int64_t)iM * a.nz + l;
+      if (OUT_JI) {  // 32 consecutive i at j = j0 + c0 / 32
+        const int j = j0 + c0 / 32;
+        if (j < a.ny) {
+          TO* o = out + a.off + (plane * a.ny + j) * a.nx + i0;
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            if (i0 + e < a.nx) store_from_float<TO>(o + e, v[e]);
+        }
+      } else {  // two runs of 16 consecutive j at i = i0 + c0 / 16, + 1
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = i0 + c0 / 16 + h;
+          if (i >= a.nx) continue;
+          TO* o = out + a.off + (plane * a.nx + i) * a.ny + j0;
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (j0 + e < a.ny) store_from_float<TO>(o + e, v[16 * h + e]);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  __syncthreads();
+  if (tid == 0 && *abort_flag && a_loads > 0) (void)mbar_wait(abar, a_phase ^ 1u);  // let an issued W load land
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+  }
+  if (tid == 0 && *abort_flag) atomicExch(a.err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// The x and y stages of Eq. prec-2 for n_M = 1 (per-l y diagonalisation), fused per slab l:
+//   D1 = W-bar_x^l T,  D2 = (W-bar_y^l D1^T) / (lambda_x^l + lambda_y^l),  D3 = W_y^l D2,  D4 = W_x^l D3^T
+// (T = the slab t[l][j][i] written by the z stage; out u[l][j][i] = D4).  The slab stays on chip: it is
+// the B operand of four GEMMs in turn, rewritten in shared memory from the accumulator between them;
+// only the four W^l matrices stream from memory, through a ring of 128-row x 128-byte K blocks (TMA).
+// Six warps: 0-3 epilogue (each owns a quarter of the tensor-memory lanes), 4 TMA producer, 5 MMA issuer.
+//   GEMM 0: A = W-bar_x (rows i', K = i), B = T [j][i]          -> D[i'][j]   -> B[i'][j]   (own row)
+//   GEMM 1: A = W-bar_y (rows j', K = j), B [i'][j]             -> D[j'][i']  -> diagonal -> B[i'][j'] (columns)
+//   GEMM 2: A = W_y (rows j'', K = j'),   B [i'][j']            -> D[j''][i'] -> B[j''][i'] (own row)
+//   GEMM 3: A = W_x (rows i, K = i'),     B [j''][i']           -> D[i][j'']  -> out[l][j][i] (columns)
+// The near-singular diagonal 1/(lambda_x + lambda_y) is summed from float pairs (inv_sum2).
+// ---------------------------------------------------------------------------
+struct FusedComp {
+  CUtensorMap tm_in;    // slab input [ns][ny][nx], box {row elements, round16(ny)}
+  CUtensorMap tm_w[4];  // W-bar_x, W-bar_y, W_y, W_x: [nl][n][n], box {row elements, 128}
+  void* out;            // [ns][ny][nx]
+  const float2* dLx2;   // [nl][nx] lambda_x as float pairs
+  const float2* dLy2;   // [nl][ny] lambda_y (with -E*) as float pairs
+  int nx, ny, ns;
+};
+struct FusedArgs {
+  FusedComp c[3];
+  int ncomp, total;
+  int rowsB, kbB;       // B tile: rows (multiple of 16) and 128-byte K blocks
+  int stages, ncols;    // A ring depth, tensor-memory columns
+  int* err;
+};
+
+constexpr int kFusedThreads = 192;
+
+template <typename Op>
+__global__ void __launch_bounds__(kFusedThreads, 1) k_tc_fused_xy(const __grid_constant__ FusedArgs a) {
+  using TB = typename Op::T;
+  constexpr uint32_t kItem = 128 * 128;  // one A ring item: 128 rows x 128 bytes
+  extern __shared__ unsigned char tf_smem[];
+  const uint32_t raw = smem_u32(tf_smem);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = tf_smem + (base - raw);
+  const uint32_t bstride = (uint32_t)a.rowsB * 128u;  // bytes per K block of B
+  const uint32_t sB = base, sA = base + (uint32_t)a.kbB * bstride;
+  const uint32_t sD = sA + (uint32_t)a.stages * kItem;  // dLx2 of the slab: 256 float2
+  const uint32_t bars = sD + 256 * 8;
+  const uint32_t full0 = bars, empty0 = bars + 64, bload = bars + 128, bfree = bars + 136, dfull = bars + 144,
+                 dfree = bars + 152, mfin = bars + 160, slot = bars + 168;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bars - base) + 176);
+  volatile int* n_items = reinterpret_cast<volatile int*>(gbase + (bars - base) + 180);
+  volatile int* n_bloads = reinterpret_cast<volatile int*>(gbase + (bars - base) + 184);
+  float2* dlx_s = reinterpret_cast<float2*>(gbase + (sD - base));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(bload, 1);
+    mbar_init(bfree, 1);
+    mbar_init(dfull, 1);
+    mbar_init(dfree, 128);
+    mbar_init(mfin, 1);
+    *abort_flag = 0;
+    *n_items = 0;
+    *n_bloads = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(a.ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + (slot - base));
+  auto locate = [&](int q, int* comp, int* slab) {
+    int cq = 0;
+    while (cq + 1 < a.ncomp && q >= a.c[cq].ns) {
+      q -= a.c[cq].ns;
+      ++cq;
+    }
+    *comp = cq;
+    *slab = q;
+  };
+  // GEMM g: rows (M) and K are n_x for g = 0, 3 and n_y for g = 1, 2; N is the other one
+  auto gM = [](const FusedComp& cp, int g) { return (g == 0 || g == 3) ? cp.nx : cp.ny; };
+  auto gN = [](const FusedComp& cp, int g) { return (g == 0 || g == 3) ? cp.ny : cp.nx; };
+
+  if (warp == 4) {
+    if (lane == 0) {  // TMA producer
+      int it = 0, si = 0;
+      for (int q = blockIdx.x; q < a.total && !*abort_flag; q += gridDim.x, ++si) {
+        int ci, slab;
+        locate(q, &ci, &slab);
+        const FusedComp& cp = a.c[ci];
+        if (si > 0 && !mbar_wait(bfree, (uint32_t)(si - 1) & 1u)) {
+          *abort_flag = 1;
+          break;
+        }
+        const int kb0 = (cp.nx + Op::kRow - 1) / Op::kRow, rows0 = (cp.ny + 15) / 16 * 16;
+        mbar_expect_tx(bload, (uint32_t)(kb0 * rows0 * 128));
+        for (int kb = 0; kb < kb0; ++kb) tma_load_3d(sB + kb * bstride, &cp.tm_in, kb * Op::kRow, 0, slab, bload);
+        *n_bloads = si + 1;
+        for (int g = 0; g < 4 && !*abort_flag; ++g) {
+          const int M = gM(cp, g), mt = (M + 127) / 128, kbs = (M + Op::kRow - 1) / Op::kRow;
+          for (int kb = 0; kb < kbs && !*abort_flag; ++kb)
+            for (int m = 0; m < mt; ++m, ++it) {
+              const int s = it % a.stages;
+              if (it >= a.stages && !mbar_wait(empty0 + 8 * s, ((uint32_t)(it / a.stages) & 1u) ^ 1u)) {
+                *abort_flag = 1;
+                break;
+              }
+              mbar_expect_tx(full0 + 8 * s, kItem);
+              tma_load_3d(sA + s * kItem, &cp.tm_w[g], kb * Op::kRow, m * 128, slab, full0 + 8 * s);
+              *n_items = it + 1;
+            }
+        }
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {  // MMA issuer
+      int it = 0, si = 0, gc = 0;
+      bool ok = true;
+      for (int q = blockIdx.x; q < a.total && ok; q += gridDim.x, ++si) {
+        int ci, slab;
+        locate(q, &ci, &slab);
+        const FusedComp& cp = a.c[ci];
+        for (int g = 0; g < 4 && ok; ++g, ++gc) {
+          if (g == 0) ok = mbar_wait(bload, (uint32_t)si & 1u);
+          if (ok && gc > 0) ok = mbar_wait(dfree, (uint32_t)(gc - 1) & 1u);
+          if (!ok || *abort_flag) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int M = gM(cp, g), K = M, N = gN(cp, g), nb = (N + 15) / 16 * 16;
+          const int mt = (M + 127) / 128, kbs = (K + Op::kRow - 1) / Op::kRow;
+          const uint32_t id = Op::idesc(nb);
+          for (int kb = 0; kb < kbs && ok; ++kb)
+            for (int m = 0; m < mt; ++m, ++it) {
+              const int s = it % a.stages;
+              if (!mbar_wait(full0 + 8 * s, (uint32_t)(it / a.stages) & 1u) || *abort_flag) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+#pragma unroll
+              for (int kk = 0; kk < Op::kRow / Op::kStep; ++kk) {
+                if (kb * Op::kRow + kk * Op::kStep >= K) break;
+                const uint32_t koff = (uint32_t)(kk * Op::kStep * (int)sizeof(TB));
+                Op::mma(tmem + (uint32_t)(m * 256), sw128_desc(sA + s * kItem + koff),
+                        sw128_desc(sB + kb * bstride + koff), id, (kb | kk) ? 1u : 0u);
+              }
+              mma_commit(empty0 + 8 * s);
+            }
+          if (!ok) break;
+          mma_commit(dfull);
+          if (g == 3) mma_commit(bfree);
+        }
+      }
+      if (!ok) *abort_flag = 1;
+      mma_commit(mfin);  // arrives once every MMA issued above has completed
+    }
+  } else {  // epilogue warps 0-3
+    int si = 0, gc = 0;
+    for (int q = blockIdx.x; q < a.total; q += gridDim.x, ++si) {
+      int ci, slab;
+      locate(q, &ci, &slab);
+      const FusedComp& cp = a.c[ci];
+      for (int e = threadIdx.x; e < cp.nx; e += 128) dlx_s[e] = cp.dLx2[(int64_t)slab * cp.nx + e];
+      named_sync(1, 128);
+      bool ok = true;
+      for (int g = 0; g < 4; ++g, ++gc) {
+        ok = mbar_wait(dfull, (uint32_t)gc & 1u);
+        tc_fence_after();
+        if (!ok) *abort_flag = 1;
+        if (*abort_flag) {
+          ok = false;
+          break;
+        }
+        const int M = gM(cp, g), N = gN(cp, g), nb = (N + 15) / 16 * 16;
+        const int nbM = (M + 15) / 16 * 16;  // rows of the next B tile (its N)
+        const int mt = (M + 127) / 128;
+        for (int m = 0; m < mt; ++m) {
+          const int r = m * 128 + warp * 32 + lane;  // D row of this thread
+          float2 dly = make_float2(0.f, 0.f);
+          if (g == 1 && r < cp.ny) dly = cp.dLy2[(int64_t)slab * cp.ny + r];
+          for (int c0 = 0; c0 < nb; c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * 256 + c0), v);
+            if (g == 0 || g == 2) {
+              // own row: B[N = r][K = c0 .. c0 + 31]
+              if (r < nbM) {
+                const int kb = c0 / Op::kRow, byte0 = (c0 % Op::kRow) * (int)sizeof(TB);
+                const uint32_t rowb = sB + kb * bstride;
+                if constexpr (sizeof(TB) == 4) {
+#pragma unroll
+                  for (int qd = 0; qd < 8; ++qd)
+                    st_shared_v4(rowb + sw128(r, byte0 + 16 * qd), __float_as_uint(v[4 * qd]),
+                                 __float_as_uint(v[4 * qd + 1]), __float_as_uint(v[4 * qd + 2]),
+                                 __float_as_uint(v[4 * qd + 3]));
+                } else {
+#pragma unroll
+                  for (int qd = 0; qd < 4; ++qd) {
+                    uint32_t w4[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h)
+                      w4[h] = (uint32_t)OpBF16::from(v[8 * qd + 2 * h]) | ((uint32_t)OpBF16::from(v[8 * qd + 2 * h + 1]) << 16);
+                    st_shared_v4(rowb + sw128(r, byte0 + 16 * qd), w4[0], w4[1], w4[2], w4[3]);
+                  }
+                }
+              }
+            } else if (g == 1) {
+              // diagonal, then columns: B[N = c][K = r] (the 32 lanes fill 32 consecutive K of row c)
+              // K positions up to the next GEMM's padded K (= n_y rounded to the MMA step) only
+              if (r < (cp.ny + Op::kStep - 1) / Op::kStep * Op::kStep) {
+                const int kb = r / Op::kRow, byte = (r % Op::kRow) * (int)sizeof(TB);
+                const uint32_t colb = sB + kb * bstride;
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                  const int cc = c0 + e;
+                  float x = v[e];
+                  if (r < cp.ny && cc < cp.nx) x *= inv_sum2(dlx_s[cc], dly);
+                  else x = 0.f;
+                  if (cc < nb) st_elem<Op>(colb + sw128(cc, byte), x);
+                }
+              }
+            } else {
+              // out[l][j = c][i = r]: the 32 lanes write 32 consecutive i
+              if (r < cp.nx) {
+                TB* o = static_cast<TB*>(cp.out) + (int64_t)slab * cp.ny * cp.nx + r;
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                  const int cc = c0 + e;
+                  if (cc < cp.ny) {
+                    if constexpr (sizeof(TB) == 4) o[(int64_t)cc * cp.nx] = v[e];
+                    else o[(int64_t)cc * cp.nx] = OpBF16::from(v[e]);
+                  }
+                }
+              }
+            }
+          }
+        }
+        if (g < 3) fence_async_smem();
+        tc_fence_before();
+        mbar_arrive(dfree);
+      }
+      if (!ok) break;
+    }
+  }
+  // tear-down: every issued MMA has completed (mfin) and every issued TMA load has landed
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!mbar_wait(mfin, 0)) *abort_flag = 1;
+    if (*abort_flag) {
+      const int n = *n_items;
+      for (int it = (n > a.stages ? n - a.stages : 0); it < n; ++it)
+        (void)mbar_wait(full0 + 8 * (it % a.stages), (uint32_t)(it / a.stages) & 1u);
+      const int nb = *n_bloads;
+      if (nb > 0) (void)mbar_wait(bload, (uint32_t)(nb - 1) & 1u);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.ncols) : "memory");
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, 1);
 }
 
 // ---------------------------------------------------------------------------
