@@ -36,7 +36,7 @@ MAP_POW, MAP_EQUI, MAP_SIN = 0, 1, 2
 def make_workload(system="He", J=0, tau=1, p=1, identical_pair=12,
                   nint=(24, 24, 8), R=(40.0, 40.0), maps=(MAP_POW, MAP_POW, MAP_SIN),
                   mode=MERKURIEV, nu=2.01, x0=1.0, y0=float("inf"), vs_cut=1e-20,
-                  shift=-2.95, k=1, name=None):
+                  shift=-2.95, k=1, name=None, basis=0):
     """Return a plain dict describing one Faddeev-Merkuriev problem."""
     sysd = SYSTEMS[system]
     return {
@@ -50,6 +50,7 @@ def make_workload(system="He", J=0, tau=1, p=1, identical_pair=12,
         "mode": int(mode), "nu": float(nu), "x0": float(x0), "y0": float(y0),
         "vs_cut": float(vs_cut),
         "shift": float(shift), "k": int(k),
+        "basis": int(basis),  # 0 = cubic Hermite, 1 = quintic Hermite (S_5^3, Section 4)
     }
 
 
@@ -72,6 +73,15 @@ WORKLOADS["he_l10_58x58x6"] = make_workload("He", 10, nint=(58, 58, 6), R=(280.0
                                             name="he_l10_58x58x6")
 WORKLOADS["he_l10_58x58x6"]["grids"] = {1: {"nint": (58, 58, 6), "R": (280.0, 280.0)},
                                         3: {"nint": (4, 4, 6), "R": (2.0, 2.0)}}
+# He J = 1 (2^1P, 3^1P), the paper's Table pardiso: quintic Hermite basis, boxes (1: 36, 36; 3: 9, 6) and
+# its five basis rows (n_x, n_y, n_z) = (3N+1, 3N+1, 3N_z+3) per component, written here as interval counts
+PARDISO_ROWS = [((7, 7, 2), (6, 6, 3)), ((10, 10, 2), (7, 7, 4)), ((13, 13, 3), (8, 8, 5)),
+                ((16, 16, 3), (9, 9, 6)), ((19, 19, 3), (9, 9, 6))]
+for _r, (_n1, _n3) in enumerate(PARDISO_ROWS, 1):
+    WORKLOADS[f"he_j1_pardiso_row{_r}"] = make_workload("He", 1, nint=_n1, R=(36.0, 36.0), shift=-2.10, k=2,
+                                                       name=f"he_j1_pardiso_row{_r}", basis=1)
+    WORKLOADS[f"he_j1_pardiso_row{_r}"]["grids"] = {1: {"nint": _n1, "R": (36.0, 36.0)},
+                                                     3: {"nint": _n3, "R": (9.0, 6.0)}}
 for _J in (1, 2, 3):
     WORKLOADS[f"psm_l{_J}_64x64x16"] = make_workload(
         "Psminus", _J, nint=(64, 64, 16), R=(80.0, 80.0), shift=-0.27, k=4,

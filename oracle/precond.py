@@ -30,8 +30,12 @@ Readings:
 * ``z_eigs="computed"`` keeps Lambda~_z (allowed only with n_M = 1); then
   L_alpha = L exactly, the left-hand operator of Eq. FM-fin.
 * A z pencil with complex-conjugate pairs (high modes of M' >= 2-3) is
-  represented by a real basis: see ``decompose_pairs``.  Any other complex 1D
-  spectrum is rejected (complex arithmetic is not on this path).
+  represented by a real basis: see ``decompose_pairs``.
+* The y pencils of step 3 may have complex-conjugate pairs (their top modes on
+  coarse grids, notably with the quintic basis): they are then kept complex,
+  as the paper computes in complex arithmetic (Section 4), and the component's
+  stages run in complex arithmetic; the result is real up to rounding and its
+  real part is returned.  A complex x pencil is rejected.
 """
 from __future__ import annotations
 
@@ -47,16 +51,25 @@ class ComplexSpectrum(RuntimeError):
     pass
 
 
-def decompose(A1, A2, order="ascending"):
-    """(W-bar, W, lambda) with W-bar A1 W = diag(lambda), W-bar A2 W = I (Eq. WW-scale)."""
+def decompose(A1, A2, order="ascending", allow_complex=False):
+    """(W-bar, W, lambda) with W-bar A1 W = diag(lambda), W-bar A2 W = I (Eq. WW-scale).
+
+    LAPACK's left eigenvectors satisfy vl^H A1 = lambda vl^H A2; W-bar's rows are vl^H scaled by
+    1 / (vl^H A2 w).  A complex spectrum raises ComplexSpectrum unless ``allow_complex``, which keeps
+    the complex eigenpairs (sorted by real part, then imaginary part)."""
     lam, VL, VR = sla.eig(A1, A2, left=True, right=True)
-    if np.max(np.abs(lam.imag)) > 1e-10 * np.max(np.abs(lam)):
+    cplx = np.max(np.abs(lam.imag)) > 1e-10 * np.max(np.abs(lam))
+    if cplx and not allow_complex:
         raise ComplexSpectrum("complex 1D spectrum")
-    idx = np.argsort(lam.real if order == "ascending" else -lam.real)
-    lam, VL, VR = lam.real[idx], VL[:, idx].real, VR[:, idx].real
+    key = lam.real if order == "ascending" else -lam.real
+    idx = np.lexsort((lam.imag, key))
+    if cplx:
+        lam, VL, VR = lam[idx], VL[:, idx], VR[:, idx]
+    else:
+        lam, VL, VR = lam.real[idx], VL[:, idx].real, VR[:, idx].real
     W = VR
-    scale = np.einsum("ki,kl,li->i", VL, A2, W)  # vl_i^T A2 w_i
-    Wbar = (VL / scale[None, :]).T
+    scale = np.einsum("ki,kl,li->i", VL.conj(), A2, W)  # vl_i^H A2 w_i
+    Wbar = (VL.conj() / scale[None, :]).T
     return Wbar, W, lam
 
 
@@ -113,10 +126,11 @@ class Preconditioner:
         g = s.g[a]
         z, x, y = g.az.pts, g.ax.pts, g.ay.pts
         Sz, D1z, D2z, Sx, D2x, Sy, D2y = self._mats(g)
-        C = {"Wz": [], "Wzb": [], "Lz": [], "Wx": {}, "Wxb": {}, "Lx": {}, "Wy": {}, "Wyb": {}, "Ly": {}}
+        C = {"Wz": [], "Wzb": [], "Lz": [], "Wx": {}, "Wxb": {}, "Lx": {}, "Wy": {}, "Wyb": {}, "Ly": {},
+             "complex": False}
         # z decompositions per M' (Eq. z-dec), normalised to g_l^{M'}(1)
         onez = g.az.basis.matrix(np.array([1.0]), 0)[0]
-        top = 2 * g.az.basis.N  # value function of the node z = 1
+        top = g.az.basis.q * g.az.basis.N  # value function of the node z = 1
         for Mp in s.Mps:
             Dz = (1 - z * z)[:, None] * D2z - (2 * (Mp + 1) * z)[:, None] * D1z - Mp * (Mp + 1) * Sz
             try:
@@ -143,8 +157,9 @@ class Preconditioner:
             Wb, W, lx = decompose(A1, Sx)
             C["Wx"][l], C["Wxb"][l], C["Lx"][l] = W, Wb, lx
             for i in range(g.nx):
-                Wb, W, ly = decompose(B + lx[i] * Sy, A2y)
+                Wb, W, ly = decompose(B + lx[i] * Sy, A2y, allow_complex=True)
                 C["Wy"][(l, i)], C["Wyb"][(l, i)], C["Ly"][(l, i)] = W, Wb, ly
+                C["complex"] = C["complex"] or np.iscomplexobj(ly)
         return C
 
     def _ll1(self, C, l):
@@ -174,6 +189,8 @@ class Preconditioner:
         g = s.g[a]
         C = self.comp[a]
         J = s.J
+        if C["complex"]:  # complex y eigenpairs: the stages in complex arithmetic
+            v = v.astype(np.complex128)
         t = np.empty_like(v)
         for iM in range(s.nM):  # W-bar_z
             t[iM] = np.einsum("lk,kij->lij", C["Wzb"][iM], v[iM])
@@ -189,7 +206,7 @@ class Preconditioner:
             n = len(ch)
             for i in range(g.nx):
                 ly = C["Ly"][(l, i)]
-                A = np.zeros((n, n, g.ny))
+                A = np.zeros((n, n, g.ny), dtype=np.result_type(ly.dtype, np.float64))
                 for r, iM in enumerate(ch):
                     Mp = s.Mps[iM]
                     A[r, r] = ly + J * (J + 1) - 2 * Mp * Mp + self._ll1(C, l)
@@ -211,7 +228,7 @@ class Preconditioner:
         res = np.empty_like(u)
         for iM in range(s.nM):
             res[iM] = np.einsum("kl,lij->kij", C["Wz"][iM], u[iM])
-        return res
+        return res.real if C["complex"] else res
 
     # ------------------------------------------------------------------
     def dense_L(self, a):

@@ -1,4 +1,4 @@
-"""Cubic Hermite splines, node maps and Gauss-point collocation (oracle).
+"""Hermite splines (cubic and quintic), node maps and Gauss-point collocation (oracle).
 
 ORACLE -- test infrastructure only (see ``oracle/__init__``).
 
@@ -8,8 +8,8 @@ Dirichlet conditions at both ends.  Section 4: spline nodes come from mapping
 an equidistant grid (Eq. map-pow for x, y; the sin map for z), and collocation
 is at Gaussian points.
 
-This build uses cubic Hermite splines (two functions per node: value and
-slope) with two Gauss-Legendre points per interval.  The x, y bases drop the
+Two bases.  Cubic Hermite splines (two functions per node: value and slope,
+r = 4) with two Gauss-Legendre points per interval.  The x, y bases drop the
 value functions at both end nodes (2N functions on N intervals, 2N collocation
 points).  The z basis keeps all 2N+2 functions (no condition at z = -1, +1);
 the system is squared by taking three Gauss-Legendre points in the first and
@@ -17,6 +17,18 @@ the last z interval and two in every other one (a reading: the paper does not
 state how its z system is squared).  All z collocation points are interior, so
 no collocation point is a collinear configuration, where the coupling term of
 Eq. FM-pre is 0/0.
+
+Quintic Hermite splines S_5^3 (Section 4: degree 5, two continuous
+derivatives, three functions per node -- value, first and second derivative --
+so r = 6), three Gauss-Legendre points per interval.  The x, y bases drop the
+value functions at both ends (3N+1 functions: the counts of the paper's tables,
+e.g. 22 = 3*7 + 1); the z basis keeps all 3N+3.  Reading: the paper does not say
+how these systems are squared; here the first x / y interval takes four Gauss
+points (3N+1), and the first, the last and the middle (index N // 2) z
+intervals take one more each (3N+3; a single interval takes six).  Collocating
+at an end node instead would put a row of zeros into the value matrix S (every
+basis function vanishes where the Dirichlet value function was dropped), which
+the 1D decompositions of the preconditioner cannot invert.
 """
 from __future__ import annotations
 
@@ -63,46 +75,74 @@ def make_nodes(kind, nint, a, b):
 
 
 # --------------------------------------------------------------------------
-# the four cubic Hermite shape functions of one interval
+# Hermite shape functions of one interval
 # --------------------------------------------------------------------------
-def hermite_shapes(s, h, deriv):
+CUBIC, QUINTIC = 0, 1
+
+
+def hermite_shapes(s, h, deriv, basis=CUBIC):
     """Shape functions on an interval of length h at local coordinate s in [0, 1].
 
-    Column order: value at left node, slope at left node, value at right
-    node, slope at right node.  ``deriv`` is the order of the derivative in
-    the global variable t = t_left + h s.
+    Cubic (4 columns): value at the left node, slope at the left node, value
+    at the right node, slope at the right node.  Quintic (6 columns): value,
+    first and second derivative at the left node, then the same at the right
+    node.  Each is the polynomial whose (value, derivatives) at the two nodes
+    are one unit vector of those conditions (first derivatives with respect to
+    the global variable t = t_left + h s, hence the factors h, h^2).
+    ``deriv`` is the order of the derivative in t.
     """
     s = np.asarray(s, dtype=np.float64)
     h = np.asarray(h, dtype=np.float64)
-    if deriv == 0:
-        cols = [(1 + 2 * s) * (1 - s) ** 2, s * (1 - s) ** 2 * h, s * s * (3 - 2 * s), s * s * (s - 1) * h]
-    elif deriv == 1:
-        cols = [6 * s * (s - 1) / h, (1 - s) * (1 - 3 * s), 6 * s * (1 - s) / h, s * (3 * s - 2)]
-    elif deriv == 2:
-        cols = [(12 * s - 6) / h ** 2, (6 * s - 4) / h, (6 - 12 * s) / h ** 2, (6 * s - 2) / h]
-    else:
-        raise ValueError(deriv)
+    if basis == CUBIC:
+        if deriv == 0:
+            cols = [(1 + 2 * s) * (1 - s) ** 2, s * (1 - s) ** 2 * h, s * s * (3 - 2 * s), s * s * (s - 1) * h]
+        elif deriv == 1:
+            cols = [6 * s * (s - 1) / h, (1 - s) * (1 - 3 * s), 6 * s * (1 - s) / h, s * (3 * s - 2)]
+        elif deriv == 2:
+            cols = [(12 * s - 6) / h ** 2, (6 * s - 4) / h, (6 - 12 * s) / h ** 2, (6 * s - 2) / h]
+        else:
+            raise ValueError(deriv)
+        return np.stack(np.broadcast_arrays(*cols), axis=-1)
+    if basis != QUINTIC:
+        raise ValueError(basis)
+    # polynomials in s as coefficient lists (ascending powers), scaled to the global variable
+    polys = [
+        np.array([1.0, 0.0, 0.0, -10.0, 15.0, -6.0]),           # value, left
+        np.array([0.0, 1.0, 0.0, -6.0, 8.0, -3.0]),             # first derivative, left (x h)
+        np.array([0.0, 0.0, 0.5, -1.5, 1.5, -0.5]),             # second derivative, left (x h^2)
+        np.array([0.0, 0.0, 0.0, 10.0, -15.0, 6.0]),            # value, right
+        np.array([0.0, 0.0, 0.0, -4.0, 7.0, -3.0]),             # first derivative, right (x h)
+        np.array([0.0, 0.0, 0.0, 0.5, -1.0, 0.5]),              # second derivative, right (x h^2)
+    ]
+    hpow = [0, 1, 2, 0, 1, 2]
+    cols = []
+    for c, e in zip(polys, hpow):
+        d = np.polynomial.polynomial.polyder(c, deriv) if deriv else c
+        cols.append(np.polynomial.polynomial.polyval(s, d) * h ** (e - deriv))
     return np.stack(np.broadcast_arrays(*cols), axis=-1)
 
 
 class HermiteBasis:
-    """Cubic Hermite basis on the nodes ``t`` (optionally Dirichlet at both ends).
+    """Hermite basis on the nodes ``t`` (optionally Dirichlet at both ends).
 
-    Global (full) function numbering: 2m = value function of node m,
-    2m+1 = slope function of node m.  With Dirichlet conditions the value
-    functions of the first and last nodes are dropped; the remaining
-    functions keep their relative order.
+    Global (full) function numbering with q functions per node (q = 2 cubic,
+    3 quintic): q m + d = the function of node m carrying the d-th derivative.
+    With Dirichlet conditions the value functions of the first and last nodes
+    are dropped; the remaining functions keep their relative order.
     """
 
-    def __init__(self, t, dirichlet):
+    def __init__(self, t, dirichlet, basis=CUBIC):
         self.t = np.asarray(t, dtype=np.float64)
         self.N = len(self.t) - 1
+        self.kind = basis
+        self.q = 2 if basis == CUBIC else 3
+        self.r = 2 * self.q
         self.dirichlet = bool(dirichlet)
-        nfull = 2 * (self.N + 1)
+        nfull = self.q * (self.N + 1)
         keep = np.ones(nfull, dtype=bool)
         if dirichlet:
             keep[0] = False
-            keep[2 * self.N] = False
+            keep[self.q * self.N] = False
         self.full_to_red = np.full(nfull, -1, dtype=np.int64)
         self.full_to_red[keep] = np.arange(int(keep.sum()))
         self.n = int(keep.sum())
@@ -121,7 +161,7 @@ class HermiteBasis:
         return np.clip(m, 0, self.N - 1)
 
     def local(self, p, deriv):
-        """For points p: (columns (P,4), values (P,4)); column -1 = dropped function.
+        """For points p: (columns (P,r), values (P,r)); column -1 = dropped function.
 
         Points outside [t_0, t_N] get all-zero values (the expansion is zero
         outside its box).
@@ -130,8 +170,8 @@ class HermiteBasis:
         m = self.locate(p)
         h = self.t[m + 1] - self.t[m]
         s = (p - self.t[m]) / h
-        vals = hermite_shapes(s, h, deriv)
-        full = 2 * m[:, None] + np.arange(4)[None, :]
+        vals = hermite_shapes(s, h, deriv, self.kind)
+        full = self.q * m[:, None] + np.arange(self.r)[None, :]
         cols = self.full_to_red[full]
         outside = (p < self.a) | (p > self.b)
         vals = np.where(outside[:, None], 0.0, vals)
@@ -142,7 +182,7 @@ class HermiteBasis:
         """Dense matrix B[q, f] = (d/dt)^deriv S^f(p_q)."""
         cols, vals = self.local(p, deriv)
         B = np.zeros((len(p), self.n))
-        for c in range(4):
+        for c in range(self.r):
             ok = cols[:, c] >= 0
             np.add.at(B, (np.nonzero(ok)[0], cols[ok, c]), vals[ok, c])
         return B
@@ -157,21 +197,38 @@ class HermiteBasis:
         return np.concatenate(out)
 
     def collocation_points(self, closed):
-        """Two Gauss points per interval; with ``closed`` (all 2N+2 functions kept)
-        the first and last intervals take three (one interval alone takes four)."""
-        counts = np.full(self.N, 2)
-        if closed:
-            if self.N == 1:
-                counts[0] = 4
-            else:
-                counts[0] = counts[-1] = 3
+        """Gauss points, as many as functions.  Cubic: two per interval; with ``closed``
+        (all 2N+2 functions kept) the first and last intervals take three (one
+        interval alone takes four).  Quintic: three per interval; the first interval
+        takes four without ``closed`` (3N+1 functions), and with ``closed`` (3N+3) the
+        first, the last and the middle interval N // 2 take one more each (one interval
+        alone takes six)."""
+        if self.kind == CUBIC:
+            counts = np.full(self.N, 2)
+            if closed:
+                if self.N == 1:
+                    counts[0] = 4
+                else:
+                    counts[0] = counts[-1] = 3
+            return self.gauss_points(counts)
+        counts = np.full(self.N, 3)
+        if not closed:
+            counts[0] += 1
+        elif self.N == 1:
+            counts[0] = 6
+        else:
+            counts[0] += 1
+            counts[-1] += 1
+            counts[self.N // 2] += 1
         return self.gauss_points(counts)
 
-    def coefficients_of(self, f, df):
-        """Hermite interpolation coefficients (value, slope at every node) of f."""
-        full = np.empty(2 * (self.N + 1))
-        full[0::2] = f(self.t)
-        full[1::2] = df(self.t)
+    def coefficients_of(self, f, df, d2f=None):
+        """Hermite interpolation coefficients of f (value and derivatives at every node)."""
+        full = np.empty(self.q * (self.N + 1))
+        full[0::self.q] = f(self.t)
+        full[1::self.q] = df(self.t)
+        if self.q == 3:
+            full[2::3] = d2f(self.t)
         keep = self.full_to_red >= 0
         return full[keep]
 
@@ -179,9 +236,9 @@ class HermiteBasis:
 class Axis:
     """One coordinate axis of a component: basis plus collocation points."""
 
-    def __init__(self, kind, nint, a, b, dirichlet):
+    def __init__(self, kind, nint, a, b, dirichlet, basis=CUBIC):
         self.nodes = make_nodes(kind, nint, a, b)
-        self.basis = HermiteBasis(self.nodes, dirichlet)
+        self.basis = HermiteBasis(self.nodes, dirichlet, basis)
         self.pts = self.basis.collocation_points(closed=not dirichlet)
         self.n = self.basis.n
         assert len(self.pts) == self.n, (len(self.pts), self.n)

@@ -42,12 +42,12 @@ MERKURIEV, NO_SPLIT, SCHRODINGER = 0, 1, 2
 class Grid:
     """Spline axes of one solved component (Section 3.1 notation (n_x, n_y, n_z), (R_x, R_y))."""
 
-    def __init__(self, nint, R, maps, nM):
+    def __init__(self, nint, R, maps, nM, basis=0):
         nix, niy, niz = nint
         self.Rx, self.Ry = float(R[0]), float(R[1])
-        self.ax = Axis(maps[0], nix, 0.0, self.Rx, dirichlet=True)
-        self.ay = Axis(maps[1], niy, 0.0, self.Ry, dirichlet=True)
-        self.az = Axis(maps[2], niz, -1.0, 1.0, dirichlet=False)
+        self.ax = Axis(maps[0], nix, 0.0, self.Rx, dirichlet=True, basis=basis)
+        self.ay = Axis(maps[1], niy, 0.0, self.Ry, dirichlet=True, basis=basis)
+        self.az = Axis(maps[2], niz, -1.0, 1.0, dirichlet=False, basis=basis)
         self.nx, self.ny, self.nz = self.ax.n, self.ay.n, self.az.n
         self.npts = self.nz * self.nx * self.ny
         self.csize = nM * self.npts
@@ -87,7 +87,7 @@ class FMSystem:
             nint = grids.get(a, {}).get("nint", wl["nint"])
             R = grids.get(a, {}).get("R", wl["R"])
             mx, my, mz = wl["maps"]
-            g = Grid(nint, R, (mx, my, mz), self.nM)
+            g = Grid(nint, R, (mx, my, mz), self.nM, int(wl.get("basis", 0)))
             self.g[a] = g
             self.off[a] = off
             off += g.csize

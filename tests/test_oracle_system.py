@@ -16,39 +16,42 @@ from oracle.system import FMSystem
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def _poly_fns(rng, a, b, dirichlet):
-    """A random cubic (vanishing at a and b when dirichlet) with its first two derivatives."""
+def _poly_fns(rng, a, b, dirichlet, degree=3):
+    """A random polynomial of the given degree (vanishing at a and b when dirichlet) with its first two
+    derivatives."""
     if dirichlet:
-        q0, q1 = rng.standard_normal(2)
-        co = np.polymul(np.polymul([1.0, -a], [-1.0, b]), [q1, q0])
+        co = np.polymul(np.polymul([1.0, -a], [-1.0, b]), rng.standard_normal(degree - 1))
     else:
-        co = rng.standard_normal(4)
+        co = rng.standard_normal(degree + 1)
     return (lambda t: np.polyval(co, t), lambda t: np.polyval(np.polyder(co), t),
             lambda t: np.polyval(np.polyder(co, 2), t))
 
 
 def _interp(g, fx, fy, fz):
-    cx = g.ax.basis.coefficients_of(fx[0], fx[1])
-    cy = g.ay.basis.coefficients_of(fy[0], fy[1])
-    cz = g.az.basis.coefficients_of(fz[0], fz[1])
+    cx = g.ax.basis.coefficients_of(fx[0], fx[1], fx[2])
+    cy = g.ay.basis.coefficients_of(fy[0], fy[1], fy[2])
+    cz = g.az.basis.coefficients_of(fz[0], fz[1], fz[2])
     return np.einsum("k,i,j->kij", cz, cx, cy).reshape(-1)
 
 
-@pytest.mark.parametrize("J,tau", [(0, 1), (1, 1), (2, 1), (2, -1), (10, 1), (11, -1)])
-def test_local_operator_on_polynomials(J, tau):
-    """H (without coupling) applied to interpolants of separable cubics equals Eq. FM-pre's
-    left operator applied to the cubics, at every collocation point."""
-    wl = workload("he_l0_24x24x8", J=J, tau=tau, nint=(4, 3, 3), R=(7.0, 9.0))
+@pytest.mark.parametrize("J,tau,basis", [(0, 1, 0), (1, 1, 0), (2, 1, 0), (2, -1, 0), (10, 1, 0), (11, -1, 0),
+                                         (0, 1, 1), (2, 1, 1), (3, -1, 1)])
+def test_local_operator_on_polynomials(J, tau, basis):
+    """H (without coupling) applied to interpolants of separable polynomials equals Eq. FM-pre's
+    left operator applied to the polynomials, at every collocation point (cubics for the cubic
+    Hermite basis, quintics for the quintic one)."""
+    wl = workload("he_l0_24x24x8", J=J, tau=tau, nint=(4, 3, 3), R=(7.0, 9.0), basis=basis)
     s = FMSystem(wl)
     a = 1
     g = s.g[a]
     rng = np.random.default_rng(7)
     F = []
     c = np.zeros(s.N)
+    deg = 3 if basis == 0 else 5
     for iM in range(s.nM):
-        fx = _poly_fns(rng, 0.0, g.Rx, True)
-        fy = _poly_fns(rng, 0.0, g.Ry, True)
-        fz = _poly_fns(rng, -1.0, 1.0, False)
+        fx = _poly_fns(rng, 0.0, g.Rx, True, deg)
+        fy = _poly_fns(rng, 0.0, g.Ry, True, deg)
+        fz = _poly_fns(rng, -1.0, 1.0, False, deg)
         F.append((fx, fy, fz))
         c[s.off[a] + iM * g.npts: s.off[a] + (iM + 1) * g.npts] = _interp(g, fx, fy, fz)
     out = s.H_local() @ c
@@ -220,3 +223,24 @@ def test_splitting_invariance_J2():
     Em = _levels(J, nint, shift, MERKURIEV)
     d = np.array([np.min(np.abs(Es - e)) for e in Em])
     assert np.sum(d < 1e-4) >= 2, (Em, Es, d)
+
+
+def test_quintic_table_basis_sizes_and_he_2P():
+    """The quintic basis on the paper's Table pardiso grids (boxes 1: 36, 36; 3: 9, 6): the unknown counts
+    are the printed ones (17 376 and 31 818 for the first two rows, i.e. 2 n_M sum n_x n_y n_z with
+    3N+1 / 3N+3 functions), and on the first row the two lowest J = 1 levels lie within 5e-4 of the
+    benchmark energies (the paper's own first-row values are about 1.4e-3 away)."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_energies.json")))
+    E2P, E3P = gold["He_2_1P"]["value"], gold["He_3_1P"]["value"]
+    sizes = []
+    for n1, n3 in (((7, 7, 2), (6, 6, 3)), ((10, 10, 2), (7, 7, 4))):
+        wl = workload("he_l0_24x24x8", J=1, nint=n1, R=(36.0, 36.0), basis=1)
+        wl["grids"] = {3: {"nint": n3, "R": (9.0, 6.0)}}
+        sizes.append(FMSystem(wl).N)
+    assert sizes == [17376, 31818]
+    wl = workload("he_l0_24x24x8", J=1, nint=(7, 7, 2), R=(36.0, 36.0), basis=1)
+    wl["grids"] = {3: {"nint": (6, 6, 3), "R": (9.0, 6.0)}}
+    s = FMSystem(wl)
+    E, _ = solvers.eigs_near(s.H(), s.S(), -2.10, 3)
+    E = np.sort(E.real)[:2]
+    assert abs(E[0] - E2P) < 5e-4 and abs(E[1] - E3P) < 5e-4, E
