@@ -334,14 +334,16 @@ ACCEPT = {0: "none", 1: "ritz_residual", 2: "stable_energy"}
 def precision_modes(pkg, wl, args, copts, stream):
     """Every precision mode on the same workload and start vector: set-up time, time-to-solution of one
     eigen-solve (CUDA events on the context's stream, after one untimed solve), inner iterations, the
-    certified eigenvalue and its deviation from the float64 mode."""
+    certified eigenvalue and its deviation from the float64 mode.  fp64: float64 everywhere; fp32 /
+    mixed: float32 preconditioner with TF32 tensor-core mode products (mixed also runs float32 inner
+    solves inside float64 refinement); *_bf16: the same with BF16 operands in the mode products."""
     import torch
     n = None
     out = {}
-    for name, code in (("fp64", 0), ("fp32", 1), ("mixed", 2)):
+    for name, code, mma in (("fp64", 0, 0), ("fp32", 1, 0), ("mixed", 2, 0), ("fp32_bf16", 1, 3), ("mixed_bf16", 2, 3)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        c = pkg.Context(wl, precision=code, **copts)
+        c = pkg.Context(wl, precision=code, mma=mma, **copts)
         c.fm_set_shift(wl["shift"])
         torch.cuda.synchronize()
         setup = time.perf_counter() - t0
@@ -375,7 +377,8 @@ def run_kernel_loop(args):
     from paper_2005_05398_gb300 import build
     build.build()
     wl = workload(args.workload)
-    ctx = pkg.Context(wl, precision={"fp64": 0, "fp32": 1, "mixed": 2}[args.precision], restart_m=args.restart, ncv=4)
+    ctx = pkg.Context(wl, precision={"fp64": 0, "fp32": 1, "mixed": 2}[args.precision], restart_m=args.restart, ncv=4,
+                      mma=args.mma)
     ctx.fm_set_shift(wl["shift"])
     x = torch.tensor(rand_vec(ctx.n, SEED_BASE), dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
@@ -393,6 +396,81 @@ def run_kernel_loop(args):
     print(json.dumps({"kernel_loop": args.kernel_loop, "workload": args.workload, "loops": args.loops,
                       "kernels": {k: v for k, v in prof.items() if v["launches"]}}))
     ctx.close()
+    return 0
+
+
+def run_pardiso(args):
+    """The paper's Table pardiso workload on this GPU: He J = 1, 2^1P and 3^1P (k = 2), quintic Hermite
+    basis, its five basis rows; per row and precision mode the set-up and solve times, device memory and
+    the certified levels with their distance to the benchmark energies the paper quotes (context for the
+    paper's CPU timings, which were taken on other hardware)."""
+    import torch
+    import paper_2005_05398_gb300 as pkg
+    from paper_2005_05398_gb300 import build
+    build.build()
+    bench_E = (-2.12384308649810135925, -2.05514636209194353689)  # the benchmark values of Table pardiso
+    rows = []
+    for r in range(1, 6):
+        wl = workload(f"he_j1_pardiso_row{r}")
+        for name, code in (("fp64", 0), ("fp32", 1)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c = pkg.Context(wl, precision=code, restart_m=args.restart, ncv=args.ncv)
+            c.fm_set_shift(wl["shift"])
+            torch.cuda.synchronize()
+            setup = time.perf_counter() - t0
+            c.fm_eigs(wl["shift"], 2, allow_not_converged=True)  # warm-up
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ev, info = c.fm_eigs(wl["shift"], 2, allow_not_converged=True)
+            torch.cuda.synchronize()
+            solve = time.perf_counter() - t1
+            ev = sorted(ev)
+            rows.append({"row": r, "mode": name, "n_unknowns": c.n,
+                         "bases": {a: [comp["nx"], comp["ny"], comp["nz"]] for a, comp in
+                                   zip((1, 3), c.components)},
+                         "setup_s": setup, "solve_s": solve, "time_to_solution_s": setup + solve,
+                         "device_gb": c.fm_stats()["device_bytes"] / 1e9, "inner_iters": info["iters"],
+                         "E": ev, "dE_benchmark": [e - b for e, b in zip(ev, bench_E)],
+                         "converged": info["converged"], "backward_error": info["resid"]})
+            c.close()
+    print(json.dumps({"workload": "He J=1 2^1P/3^1P, Table pardiso bases, quintic Hermite", "rows": rows}))
+    return 0
+
+
+def run_conv3d(args):
+    """He 3^1D (J = 2) on the paper's convergence domains with the quintic basis: a sequence of component-1
+    radial bases up to the paper's final one (4 246 848 unknowns); per basis the set-up and solve times, the
+    certified level and its distance to the benchmark energy the paper quotes."""
+    import torch
+    import paper_2005_05398_gb300 as pkg
+    from paper_2005_05398_gb300 import build
+    from fm_inputs import he_3d_workload, CONV3D_SEQUENCE
+    build.build()
+    bench_E = -2.05562073285224648939  # the benchmark value of Fig. He-conv
+    rows = []
+    for n1, n3 in CONV3D_SEQUENCE[-args.conv_points:]:
+        wl = he_3d_workload(n1, n3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = pkg.Context(wl, precision={"fp64": 0, "fp32": 1, "mixed": 2}[args.precision], restart_m=args.restart,
+                        ncv=args.ncv)
+        c.fm_set_shift(wl["shift"])
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        ev, info = c.fm_eigs(wl["shift"], 1, allow_not_converged=True)
+        torch.cuda.synchronize()
+        solve = time.perf_counter() - t1
+        rows.append({"bases": {a: [comp["nx"], comp["ny"], comp["nz"]] for a, comp in zip((1, 3), c.components)},
+                     "n_unknowns": c.n, "setup_s": setup, "solve_s": solve, "device_gb": c.fm_stats()["device_bytes"] / 1e9,
+                     "inner_iters": info["iters"], "E": ev[0], "dE_benchmark": ev[0] - bench_E,
+                     "rel_err": abs(ev[0] - bench_E) / abs(bench_E), "converged": info["converged"],
+                     "backward_error": info["resid"]})
+        print(json.dumps(rows[-1]), flush=True)
+        c.close()
+    print(json.dumps({"workload": "He 3^1D J=2, quintic Hermite, domains (1: 45, 45; 3: 11, 6)", "precision": args.precision,
+                      "rows": rows}))
     return 0
 
 
@@ -487,7 +565,11 @@ def main():
     ap.add_argument("--kernel-loop", choices=["apply", "precond", "solve"], default=None,
                     help="repeat one call --loops times on the workload (profiler captures)")
     ap.add_argument("--loops", type=int, default=5)
+    ap.add_argument("--mma", type=int, default=0, choices=[0, 1, 2, 3], help="mode products: auto, SIMT, TF32, BF16")
     ap.add_argument("--serve", action="store_true", help="request-loop benchmark (batched and served workloads)")
+    ap.add_argument("--pardiso", action="store_true", help="the paper's Table pardiso rows (He J=1, quintic basis)")
+    ap.add_argument("--conv3d", action="store_true", help="He 3^1D convergence sequence (J=2, quintic basis)")
+    ap.add_argument("--conv-points", type=int, default=5)
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--mix-scale", default="full", choices=["full", "medium", "small"])
     ap.add_argument("--slots", type=int, default=8)
@@ -496,6 +578,10 @@ def main():
     args = ap.parse_args()
     if args.serve:
         return run_serve(args)
+    if args.pardiso:
+        return run_pardiso(args)
+    if args.conv3d:
+        return run_conv3d(args)
     if args.kernel_loop:
         return run_kernel_loop(args)
     if args.impl == "reference":

@@ -82,6 +82,21 @@ for _r, (_n1, _n3) in enumerate(PARDISO_ROWS, 1):
                                                        name=f"he_j1_pardiso_row{_r}", basis=1)
     WORKLOADS[f"he_j1_pardiso_row{_r}"]["grids"] = {1: {"nint": _n1, "R": (36.0, 36.0)},
                                                      3: {"nint": _n3, "R": (9.0, 6.0)}}
+# He 3^1D (J = 2, tau = 1, p = 1), the paper's convergence study (Fig. He-conv): quintic Hermite basis on the
+# domains (1: 45, 45; 3: 11, 6); its final basis (1: 238, 238, 24; 3: 52, 40, 27), 4 246 848 unknowns, and a
+# sequence that refines the radial bases of component 1 toward it (interval counts; n = 3N+1, n_z = 3N_z+3)
+CONV3D_FINAL = ((79, 79, 7), (17, 13, 8))
+
+
+def he_3d_workload(n1=CONV3D_FINAL[0], n3=CONV3D_FINAL[1]):
+    w = make_workload("He", 2, nint=n1, R=(45.0, 45.0), shift=-2.0557, k=1,
+                      name=f"he_j2_3d_{n1[0]}x{n1[1]}x{n1[2]}", basis=1)
+    w["grids"] = {1: {"nint": tuple(n1), "R": (45.0, 45.0)}, 3: {"nint": tuple(n3), "R": (11.0, 6.0)}}
+    return w
+
+
+WORKLOADS["he_j2_3d_final"] = he_3d_workload()
+CONV3D_SEQUENCE = [((n, n, 7), CONV3D_FINAL[1]) for n in (31, 43, 55, 67, 79)]
 for _J in (1, 2, 3):
     WORKLOADS[f"psm_l{_J}_64x64x16"] = make_workload(
         "Psminus", _J, nint=(64, 64, 16), R=(80.0, 80.0), shift=-0.27, k=4,

@@ -66,14 +66,16 @@ typedef struct {
 enum { FM_MAP_POW = 0, FM_MAP_EQUI = 1, FM_MAP_SIN = 2 };
 
 /* Spline grid of one solved component, notation (n_x, n_y, n_z; R_x, R_y) of Section 4.
- * Cubic Hermite splines, nint intervals per axis: 2*nint functions in x and y
- * (Dirichlet at 0 and R), 2*nint + 2 in z on [-1, 1].  Node maps: Eq. map-pow
- * (FM_MAP_POW, x and y), equidistant, and sin(pi u / 2) (FM_MAP_SIN, z only). */
+ * nint intervals per axis.  Cubic Hermite splines: 2*nint functions in x and y (Dirichlet at 0
+ * and R), 2*nint + 2 in z on [-1, 1].  Quintic Hermite (value, first and second derivative per node):
+ * 3*nint + 1 in x and y, 3*nint + 3 in z (the counts of the paper's tables).  Collocation at Gauss
+ * points, as many as functions.  Node maps: Eq. map-pow (FM_MAP_POW, x and y), equidistant, and
+ * sin(pi u / 2) (FM_MAP_SIN, z only). */
 typedef struct {
   int nint_x, nint_y, nint_z;
   double Rx, Ry;
   int xmap, ymap, zmap;
-  int basis; /* 0 = cubic Hermite (the only basis of this library) */
+  int basis; /* 0 = cubic Hermite (r = 4), 1 = quintic Hermite S_5^3 (r = 6, Section 4); one basis for all */
 } fm_grid;
 
 enum { FM_SPLIT_MERKURIEV = 0, FM_SPLIT_NONE = 1, FM_SPLIT_SCHRODINGER = 2 };
@@ -92,14 +94,20 @@ typedef struct {
 /* Precision modes.  FP64: float64 everywhere.  FP32: float32 preconditioner, float64 operator,
  * FGMRES and Gram-Schmidt.  MIXED: float64 iterative refinement on the true float64 residual
  * around float32 FGMRES corrections (float32 operator, preconditioner and Gram-Schmidt), each
- * solved to a relative 3e-5; the result meets the same float64 tolerance. */
+ * solved to the relative residual fm_opts.inner_tol32 (default 3e-5); the result meets the same
+ * float64 tolerance. */
 enum { FM_PREC_FP64 = 0, FM_PREC_FP32 = 1, FM_PREC_MIXED = 2 };
 
-/* Mode products of the float32 preconditioner (FP32 and MIXED precision).  AUTO: the x and y
- * stages run as TF32 tensor-core GEMMs (float32 accumulation) on every component whose n_x and
- * n_y are multiples of 4 in [16, 256], on float32 CUDA cores otherwise.  SIMT: float32 CUDA cores
- * always.  TF32: tensor cores, FM_ERR_ARG from fm_create when a component is not eligible. */
-enum { FM_MMA_AUTO = 0, FM_MMA_SIMT = 1, FM_MMA_TF32 = 2 };
+/* Mode products of the float32 preconditioner (FP32 and MIXED precision).  AUTO: TF32 tensor-core
+ * GEMMs (float32 accumulation) on every component whose n_x and n_y are multiples of 4 in [16, 256],
+ * float32 CUDA cores otherwise.  SIMT: float32 CUDA cores always.  TF32: tensor cores, FM_ERR_ARG
+ * from fm_create when a component is not eligible.  BF16: BF16 operands with float32 accumulation
+ * (8 significand bits per operand: a looser preconditioner, the same float64 results) for the z stages
+ * and, with n_M = 1, the fused x / y chain; the x stages around the banded y solves (n_M > 1) stay
+ * TF32; needs n_x, n_y multiples of 8 in [16, 256] and n_z <= 128 (else FM_ERR_ARG).
+ * On the tensor cores the z stages run as tcgen05 GEMMs when n_z <= 128, and for n_M = 1 the x and y
+ * stages of one slab (z mode) run in one kernel that keeps the slab on chip. */
+enum { FM_MMA_AUTO = 0, FM_MMA_SIMT = 1, FM_MMA_TF32 = 2, FM_MMA_BF16 = 3 };
 
 typedef struct {
   double tol;        /* relative residual of fm_solve (FGMRES true residual), e.g. 1e-12 */
@@ -120,12 +128,14 @@ typedef struct {
                         P + (A U - P U) U^T, Freitag & Spence), dropped once an inner solve stalls;
                         0 = plain preconditioner (default: with the relaxed inner tolerance the tuning no
                         longer saves time, and near clusters of levels it misleads inexact solves) */
-  int mma;           /* FM_MMA_AUTO, FM_MMA_SIMT or FM_MMA_TF32 */
+  int mma;           /* FM_MMA_AUTO, FM_MMA_SIMT, FM_MMA_TF32 or FM_MMA_BF16 */
   int start_filter;  /* fm_eigs: passes v <- P^{-1} S v / |.| applied to the start vector before the Arnoldi
                         process (the tensor preconditioner approximates (H - E* S)^{-1}, so each pass
                         enriches the directions of the levels nearest the shift); 0..16, default 8 */
   int refine;        /* fm_eigs: most inverse-iteration steps c <- (H - shift S)^{-1} S c / |.| (float64 solves
                         to tol) given to a returned pair whose backward error is above eig_tol; 0..8, default 2 */
+  double inner_tol32; /* FM_PREC_MIXED: relative residual of each float32 inner solve, in [1e-7, 0.5]
+                        (default 3e-5; smaller means fewer refinement steps, more float32 iterations each) */
   int device;        /* CUDA device ordinal */
   void* stream;      /* cudaStream_t, NULL = legacy default stream */
 } fm_opts;
@@ -270,13 +280,22 @@ int fm_apply_noalloc(fm_ctx* ctx, double E, const double* x, double* y);
 int fm_host_decompose(int n, const double* A1, const double* A2, int descending, double* Wbar, double* W,
                       double* lam);
 
+/* Host-side diagnostic (no GPU involved): one spline axis exactly as fm_create builds it (Section 3.1,
+ * Section 4): node map 'map' (FM_MAP_*) of 'nint' intervals on [a, b], Dirichlet at both ends or not,
+ * basis 0 (cubic Hermite, r = 4) or 1 (quintic Hermite, r = 6).  Outputs: *n functions (= collocation
+ * points), *r taps per point; pts[n] the collocation points, base[n] the first tap's function index, and
+ * S, D1, D2 [n][r] the values, first and second derivatives of functions base + t at each point.  The
+ * caller provides arrays for n <= 3 (nint + 1) points and r = 6 taps.  FM_ERR_ARG for invalid input. */
+int fm_host_axis(int map, int nint, double a, double b, int dirichlet, int basis, int* n, int* r, double* pts,
+                 int* base, double* S, double* D1, double* D2);
+
 /* Kernel classes of the per-kernel timing below. */
 enum {
   FM_KERNEL_APPLY_XY = 0,  /* operator apply, y and x passes */
   FM_KERNEL_APPLY_Z,       /* operator apply, z pass + pointwise terms + M' couplings */
   FM_KERNEL_COUPLING,      /* V^(s) coupling gather */
   FM_KERNEL_ZMIX,          /* preconditioner z mode products */
-  FM_KERNEL_XMIX,          /* preconditioner x mode products */
+  FM_KERNEL_XMIX,          /* preconditioner x mode products (with the y stage where they run fused) */
   FM_KERNEL_YSOLVE,        /* preconditioner banded y solves */
   FM_KERNEL_DOT,           /* Krylov multi-dot products */
   FM_KERNEL_AXPY,          /* Krylov multi-axpy updates */

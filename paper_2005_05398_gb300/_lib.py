@@ -35,7 +35,7 @@ class fm_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("restart_m", c_int), ("max_iters", c_int), ("precision", c_int),
                 ("ncv", c_int), ("max_restarts", c_int), ("eig_tol", c_double), ("z_eigs", c_int),
                 ("y_solver", c_int), ("tune", c_int), ("mma", c_int), ("start_filter", c_int),
-                ("refine", c_int), ("device", c_int), ("stream", c_void_p)]
+                ("refine", c_int), ("inner_tol32", c_double), ("device", c_int), ("stream", c_void_p)]
 
 
 class fm_info(ctypes.Structure):
@@ -94,6 +94,8 @@ SIGNATURES = {
     "fm_stats": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)]),
     "fm_profile": (c_int, [c_void_p, c_int]),
     "fm_host_decompose": (c_int, [c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "fm_host_axis": (c_int, [c_int, c_int, c_double, c_double, c_int, c_int, ctypes.POINTER(c_int),
+                             ctypes.POINTER(c_int), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "fm_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64), ctypes.POINTER(c_double),
                                 ctypes.POINTER(c_double)]),
     "fm_server_create": (c_int, [c_int, c_int64, c_int, c_int, ctypes.POINTER(c_void_p)]),
@@ -158,7 +160,7 @@ def make_structs(wl):
         g.nint_x, g.nint_y, g.nint_z = nint
         g.Rx, g.Ry = R
         g.xmap, g.ymap, g.zmap = wl["maps"]
-        g.basis = 0
+        g.basis = int(wl.get("basis", 0))
         gl.append(g)
     grids = (fm_grid * len(gl))(*gl)
     sp = fm_splitting()
@@ -199,6 +201,21 @@ def fm_host_decompose(A1, A2, descending=False):
     p = lambda a: a.ctypes.data_as(c_void_p)
     _check("fm_host_decompose", lib().fm_host_decompose(n, p(A1), p(A2), int(descending), p(Wb), p(W), p(lam)))
     return Wb, W, lam
+
+
+def fm_host_axis(kind, nint, a, b, dirichlet, basis=0):
+    """One spline axis as libfm's set-up builds it (host only): dict of numpy arrays pts, base, S, D1, D2."""
+    import numpy as np
+    cap = 3 * (int(nint) + 1)
+    pts, base = np.empty(cap), np.empty(cap, dtype=np.int32)
+    S, D1, D2 = np.empty((cap, 6)), np.empty((cap, 6)), np.empty((cap, 6))
+    n, r = c_int(), c_int()
+    p = lambda x: x.ctypes.data_as(c_void_p)
+    _check("fm_host_axis", lib().fm_host_axis(int(kind), int(nint), float(a), float(b), int(bool(dirichlet)), int(basis),
+                                              ctypes.byref(n), ctypes.byref(r), p(pts), p(base), p(S), p(D1), p(D2)))
+    n, r = n.value, r.value
+    S, D1, D2 = (np.ascontiguousarray(X.reshape(-1)[: n * r].reshape(n, r)) for X in (S, D1, D2))
+    return {"n": n, "r": r, "pts": pts[:n].copy(), "base": base[:n].copy(), "S": S, "D1": D1, "D2": D2}
 
 
 class Context:

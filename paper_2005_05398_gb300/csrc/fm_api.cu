@@ -225,7 +225,7 @@ static int fgmres32(fm_ctx* c, double E, const float* b, float* d, double tol, i
 }
 
 // Mixed precision: float64 iterative refinement (true residual r = b - (H - E S) x in float64)
-// around float32 FGMRES corrections, each solved to a relative 3e-5.
+// around float32 FGMRES corrections, each solved to the relative residual opts.inner_tol32.
 static int ir_solve(fm_ctx* c, double E, const double* b, double* x, double tol, int max_iters, int* iters_out,
                     int* outer_out, double* resid_out) {
   int rc;
@@ -256,7 +256,7 @@ static int ir_solve(fm_ctx* c, double E, const double* b, double* x, double tol,
     beta_prev = beta;
     if ((rc = to32(c, r, 1.0 / beta, c->d32))) return rc;  // normalised residual as the float32 right-hand side
     int it = 0;
-    if ((rc = fgmres32(c, E, c->d32, c->e32, 3e-5, max_iters - total, &it))) return rc;
+    if ((rc = fgmres32(c, E, c->d32, c->e32, c->opts.inner_tol32, max_iters - total, &it))) return rc;
     total += it;
     ++*outer_out;
     if ((rc = add32(c, c->e32, beta, x))) return rc;  // x += beta * correction
@@ -376,6 +376,7 @@ void fm_default_opts(fm_opts* o) {
   o->mma = FM_MMA_AUTO;
   o->start_filter = 8;
   o->refine = 2;
+  o->inner_tol32 = 3e-5;
   o->device = 0;
   o->stream = nullptr;
 }
@@ -432,7 +433,8 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
   if (o.z_eigs == 1 && nM != 1) return FM_ERR_ARG;
   if (o.restart_m < 1 || o.restart_m > 256 || o.max_iters < 1 || !(o.tol > 0) || o.ncv < 3 || o.ncv > 64 ||
       o.max_restarts < 0 || !(o.eig_tol > 0) || o.precision < 0 || o.precision > 2 || o.y_solver < 0 ||
-      o.y_solver > 2 || o.mma < 0 || o.mma > 2 || o.start_filter < 0 || o.start_filter > 16 || o.refine < 0 || o.refine > 8)
+      o.y_solver > 2 || o.mma < 0 || o.mma > 3 || o.start_filter < 0 || o.start_filter > 16 || o.refine < 0 || o.refine > 8 ||
+      !(o.inner_tol32 >= 1e-7 && o.inner_tol32 <= 0.5))
     return FM_ERR_ARG;
   fm_ctx* c = new fm_ctx();
   c->sys = *sys;
@@ -448,9 +450,19 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
     fm_destroy(c);
     return e;
   };
+  const bool verbose = getenv("FM_VERBOSE") != nullptr;
+  double tph = wall_ms();
+  auto phase = [&](const char* what) {
+    if (!verbose) return;
+    const double now = wall_ms();
+    fprintf(stderr, "[fm_create] %-26s %8.1f ms\n", what, now - tph);
+    tph = now;
+  };
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(FM_ERR_CUDA);
   if ((rc = kernels_init(c))) return fail(rc);
+  phase("kernel attributes");
   if ((rc = setup_host(c, grids, n_grids))) return fail(rc);
+  phase("tables and decompositions");
   const int64_t N = c->N;
   const int m = o.restart_m;
   c->red_blocks = 4 * 152;  // reduction blocks: four per SM
@@ -476,8 +488,16 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
         (rc = dev_alloc(c, (void**)&c->P32, N * 4)) || (rc = dev_alloc(c, (void**)&c->Q32, N * 4)) ||
         (rc = dev_alloc(c, (void**)&c->R32, N * 4)))
       return fail(rc);
+    int64_t st = 0;  // coupling sources regrouped by y interval for the float32 gather
+    for (auto& cp : c->comps) {
+      cp.ystage_off = st;
+      st += (int64_t)c->nM * cp.nz * cp.nx * cp.ay.nint * cp.r;
+    }
+    if ((rc = dev_alloc(c, (void**)&c->ystage32, (size_t)st * 4))) return fail(rc);
   }
+  phase("workspace allocation");
   if ((rc = tc_setup(c))) return fail(rc);
+  phase("tensor maps");
   c->m_alloc = m;
   c->ncv_alloc = o.ncv;
   *out = c;

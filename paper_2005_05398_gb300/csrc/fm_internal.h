@@ -12,20 +12,34 @@
 namespace fmi {
 
 // One spline axis (Section 3.1): nodes, collocation points and, per collocation
-// point, the four nonzero basis functions as taps base+t, t = 0..3 (a tap outside
-// [0, n) carries the value 0).
+// point, the r nonzero basis functions as taps base+t, t = 0..r-1 (a tap outside
+// [0, n) carries the value 0).  Cubic Hermite: q = 2 functions per node, r = 4;
+// quintic Hermite S_5^3: q = 3, r = 6.
+constexpr int kMaxTaps = 6;
 struct Axis {
   int kind = 0, nint = 0, n = 0;
+  int q = 2, r = 4;                    // functions per node, taps per point
+  int kl = 0, ku = 0;                  // band half-widths of the 1D collocation matrices (row - col, col - row)
   double a = 0, b = 0;
   bool dirichlet = false;
   std::vector<double> nodes, pts;
   std::vector<int> base;               // per point
-  std::vector<double> S, D1, D2;       // per point, 4 values each
-  void build(int kind, int nint, double a, double b, bool dirichlet);
+  std::vector<double> S, D1, D2;       // per point, r values each
+  void build(int kind, int nint, double a, double b, bool dirichlet, int basis = 0);
   int locate(double p) const;          // interval m with nodes[m] <= p <= nodes[m+1]
-  // taps of an arbitrary point (values, first derivatives or second derivatives)
-  void eval(double p, int deriv, int* base_out, double v[4]) const;
+  // taps of an arbitrary point (values, first derivatives or second derivatives); v holds r values
+  void eval(double p, int deriv, int* base_out, double v[kMaxTaps]) const;
+  // rows of c[x][y] a tile of tx consecutive collocation points reads (from the base of its first point)
+  int tile_rows(int tx) const;
 };
+
+// Half-width of the banded y systems of one l (Section 3.2, the M' chain of n_c components interleaved
+// with y): the 1D band of the y collocation matrices times n_c, plus the M' coupling to the neighbours.
+inline int band_kl(const Axis& ay, int nc) {
+  const int k = ay.kl > ay.ku ? ay.kl : ay.ku;
+  return nc == 1 ? k : k * nc + 1;
+}
+constexpr int kMaxBandKL = 25;  // widest banded y system the y-solve kernel takes
 
 // Device-side 1D tap tables of one axis.
 struct AxisDev {
@@ -51,6 +65,8 @@ struct Tabs32 {
 
 struct Comp {
   int label = 0;                 // particle label alpha
+  int r = 4;                     // taps per point of the component's basis (4 cubic, 6 quintic)
+  int64_t ystage_off = 0;        // offset of the component in fm_ctx::ystage32 ([nM][nz][nx][nint_y][r])
   Tabs32 f32;
   Axis ax, ay, az;
   int nx = 0, ny = 0, nz = 0;
@@ -67,7 +83,7 @@ struct Comp {
   int n_act = 0;
   int* act_pt = nullptr;         // [n_act] point index (k*nx + i)*ny + j
   int* cpl_base = nullptr;       // [ns][3][n_act]  (z, x, y tap bases)
-  double* cpl_val = nullptr;     // [ns][12][n_act] (Sz[4], Sx[4], Sy[4])
+  double* cpl_val = nullptr;     // [ns][3 r][n_act] (Sz[r], Sx[r], Sy[r])
   double* cpl_w = nullptr;       // [ns][nM*nM][n_act] weight of (M', M'')
   // preconditioner, E-independent
   double* Wz = nullptr;          // [nM][nz][nz]
@@ -101,6 +117,15 @@ struct Comp {
   // tensor-core chain: TMA maps of the stage buffers and of the float32 W matrices
   // 0 t[slab][j][i], 1 u[slab][j][i], 2 W-bar_x, 3 W_x, 4 u[slab][i][j], 5 t[slab][i][j], 6 W-bar_y, 7 W_y
   CUtensorMap tm[8];
+  // tensor-core z stages and the fused n_M = 1 x / y chain (BF16 or TF32 operands)
+  void* Wz_tc = nullptr;         // [nM][nz][ldz] W_z, rows zero-padded to ldz (16-byte TMA strides)
+  void* Wzb_tc = nullptr;        // [nM][nz][ldz] W-bar_z
+  int ldz = 0;
+  uint16_t *Wx16 = nullptr, *Wxb16 = nullptr, *Wy16 = nullptr, *Wyb16 = nullptr;  // BF16 copies
+  CUtensorMap tmz[2];            // W-bar_z, W_z for the z-stage kernel
+  CUtensorMap tmf[5];            // fused chain: slab t[slab][j][i], W-bar_x, W-bar_y, W_y, W_x
+  bool tcz = false;              // z stages on the tensor cores
+  bool fused = false;            // n_M = 1: x / y stages in one kernel per slab (with the y diagonalisation)
 };
 
 }  // namespace fmi
@@ -135,6 +160,7 @@ struct fm_ctx {
   float* r32 = nullptr;          // [N]
   float* d32 = nullptr;          // [N]
   float* e32 = nullptr;          // [N]
+  float* ystage32 = nullptr;     // float32 sources of the coupling regrouped by y interval (MIXED precision)
   double* V = nullptr;           // FGMRES basis [(m+1)][N]
   double* Z = nullptr;           // FGMRES preconditioned directions [m][N]
   double* w = nullptr;           // [N]
@@ -161,6 +187,7 @@ struct fm_ctx {
   std::vector<double> tuneGinv;  // (U^T W)^{-1}, n_tune x n_tune, row-major
   double normH = 0.0, normS = 0.0;  // power-iteration lower bounds of |H|_2 and |S|_2 (0 = not yet estimated)
   bool tc_active = false;        // float32 preconditioner x / y stages on the tensor cores
+  bool bf16 = false;             // ... with BF16 operands (z stages and the fused chain), else TF32
   int* tc_err = nullptr;         // device flag: a bounded wait of a tensor-core kernel expired
   int64_t launches = 0;
   int64_t device_bytes = 0;
@@ -219,10 +246,14 @@ bool tc_component_ok(const Comp& cp);
 int tc_setup(fm_ctx* c);       // after the stage buffers exist: encode the TMA maps
 int tc_kernels_init();
 int tc_check(fm_ctx* c);       // FM_ERR_TIMEOUT when a tensor-core kernel gave up a wait
+// tensor-core chain over all components: z and x forward (+ y for the diagonalised n_M = 1 form, fused
+// per slab where eligible); the components left for the banded y solves are returned in 'banded'
 template <typename TIO>
-int precond_tc_front(fm_ctx* c, Comp& cp, const TIO* x, bool ydiag);   // z, x forward (+ diagonalised y)
+int precond_tc_front(fm_ctx* c, const TIO* x, std::vector<Comp*>* banded);
 template <typename TIO>
-int precond_tc_back(fm_ctx* c, Comp& cp, TIO* y);                       // x, z inverse
+int precond_tc_back(fm_ctx* c, TIO* y);                                 // x, z inverse
+bool tc_uses_ydiag(const fm_ctx* c, const Comp& cp);                    // the n_M = 1 y diagonalisation runs
+uint16_t f2bf(float v);                                                 // float -> bfloat16 bits (nearest even)
 }  // namespace fmi
 
 #define FM_CUDA(call)                                   \

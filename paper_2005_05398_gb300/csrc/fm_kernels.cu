@@ -26,23 +26,24 @@ constexpr int kMaxM = 12;  // largest n_M (J <= 11 for tau = +1)
 // ---------------------------------------------------------------------------
 // apply, pass 1: for one (component, M', z-dof k) plane c[i][j] (n_x x n_y) and a tile
 // of TX x-collocation points: P = (S_x (x) S_y) c, Q = (D2_x (x) S_y) c, R = (S_x (x) D2_y) c.
+// R taps per point (4 cubic, 6 quintic); the tile reads 'rows' rows of c from the base of its
+// first point (the host sizes 'rows' from the axis' tap structure).
 // ---------------------------------------------------------------------------
-template <int TX, typename T>
+template <int TX, int R, typename T>
 __global__ void __launch_bounds__(256) k_apply_xy(const T* __restrict__ c, T* __restrict__ P,
-                                                  T* __restrict__ Q, T* __restrict__ R, int nx, int ny,
+                                                  T* __restrict__ Q, T* __restrict__ Rr, int nx, int ny, int rows,
                                                   const int* __restrict__ bx, const T* __restrict__ Sx,
                                                   const T* __restrict__ D2x, const int* __restrict__ by,
                                                   const T* __restrict__ Sy, const T* __restrict__ D2y,
                                                   bool only_S) {
   extern __shared__ unsigned char smraw_xy[];
   T* sm = reinterpret_cast<T*>(smraw_xy);
-  const int rows = TX + 2;
   T* cs = sm;                 // [rows][ny]
   T* As = sm + rows * ny;     // [rows][ny]  S_y pass
   T* Bs = As + rows * ny;     // [rows][ny]  D2_y pass
   const int64_t plane = (int64_t)blockIdx.y * nx * ny;
   const int xi0 = blockIdx.x * TX;
-  const int r0 = xi0 - 1;
+  const int r0 = bx[xi0];
   for (int idx = threadIdx.x; idx < rows * ny; idx += blockDim.x) {
     const int r = r0 + idx / ny;
     cs[idx] = (r >= 0 && r < nx) ? c[plane + (int64_t)r * ny + (idx % ny)] : (T)0;
@@ -53,12 +54,12 @@ __global__ void __launch_bounds__(256) k_apply_xy(const T* __restrict__ c, T* __
     const int b = by[eta];
     T a = 0, d = 0;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < R; ++t) {
       const int j = b + t;
       if (j >= 0 && j < ny) {
         const T v = cs[r * ny + j];
-        a = fma(Sy[eta * 4 + t], v, a);
-        d = fma(D2y[eta * 4 + t], v, d);
+        a = fma(Sy[eta * R + t], v, a);
+        d = fma(D2y[eta * R + t], v, d);
       }
     }
     As[idx] = a;
@@ -71,20 +72,20 @@ __global__ void __launch_bounds__(256) k_apply_xy(const T* __restrict__ c, T* __
     const int b = bx[xi] - r0;
     T p = 0, q = 0, rr = 0;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < R; ++t) {
       const int lr = b + t;
       if (lr >= 0 && lr < rows) {
         const T a = As[lr * ny + eta];
-        p = fma(Sx[xi * 4 + t], a, p);
-        q = fma(D2x[xi * 4 + t], a, q);
-        rr = fma(Sx[xi * 4 + t], Bs[lr * ny + eta], rr);
+        p = fma(Sx[xi * R + t], a, p);
+        q = fma(D2x[xi * R + t], a, q);
+        rr = fma(Sx[xi * R + t], Bs[lr * ny + eta], rr);
       }
     }
     const int64_t o = plane + (int64_t)xi * ny + eta;
     P[o] = p;
     if (!only_S) {
       Q[o] = q;
-      R[o] = rr;
+      Rr[o] = rr;
     }
   }
 }
@@ -110,8 +111,8 @@ struct ZPassArgs {
   T lamm[kMaxM];    // lambda-hat^{J, -M'} for M'-1 coupling
 };
 
-// apply, pass 2: one thread per output point (M', zeta, xi, eta) of a component.
-template <typename T>
+// apply, pass 2: one thread per output point (M', zeta, xi, eta) of a component (R taps in z).
+template <int R, typename T>
 __global__ void __launch_bounds__(256) k_apply_z(ZPassArgs<T> a, bool only_S) {
   const int64_t npts = (int64_t)a.nz * a.nx * a.ny;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -124,17 +125,17 @@ __global__ void __launch_bounds__(256) k_apply_z(ZPassArgs<T> a, bool only_S) {
   const int64_t blk = (int64_t)iM * npts;
   T U = 0, Uz = 0, Uzz = 0, Uxx = 0, Uyy = 0;
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
+  for (int t = 0; t < R; ++t) {
     const int k = b + t;
     if (k >= 0 && k < a.nz) {
       const int64_t o = blk + (int64_t)k * a.nx * a.ny + xy;
       const T p = a.P[o];
-      U = fma(a.Sz[zeta * 4 + t], p, U);
+      U = fma(a.Sz[zeta * R + t], p, U);
       if (!only_S) {
-        Uz = fma(a.D1z[zeta * 4 + t], p, Uz);
-        Uzz = fma(a.D2z[zeta * 4 + t], p, Uzz);
-        Uxx = fma(a.Sz[zeta * 4 + t], a.Q[o], Uxx);
-        Uyy = fma(a.Sz[zeta * 4 + t], a.R[o], Uyy);
+        Uz = fma(a.D1z[zeta * R + t], p, Uz);
+        Uzz = fma(a.D2z[zeta * R + t], p, Uzz);
+        Uxx = fma(a.Sz[zeta * R + t], a.Q[o], Uxx);
+        Uyy = fma(a.Sz[zeta * R + t], a.R[o], Uyy);
       }
     }
   }
@@ -156,12 +157,12 @@ __global__ void __launch_bounds__(256) k_apply_z(ZPassArgs<T> a, bool only_S) {
   if (iM + 1 < a.nM) {  // lambda-hat^{J,M'}/y^2 [-(1-z^2) d/dz + 2(M'+1) z] psi_{M'+1}
     T Up = 0, Uzp = 0;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < R; ++t) {
       const int k = b + t;
       if (k >= 0 && k < a.nz) {
         const T p = a.P[blk + npts + (int64_t)k * a.nx * a.ny + xy];
-        Up = fma(a.Sz[zeta * 4 + t], p, Up);
-        Uzp = fma(a.D1z[zeta * 4 + t], p, Uzp);
+        Up = fma(a.Sz[zeta * R + t], p, Up);
+        Uzp = fma(a.D1z[zeta * R + t], p, Uzp);
       }
     }
     out += a.lamp[iM] * iy2 * (-((T)1 - z * z) * Uzp + (T)(2 * (Mp + 1)) * z * Up);
@@ -169,9 +170,9 @@ __global__ void __launch_bounds__(256) k_apply_z(ZPassArgs<T> a, bool only_S) {
   if (iM >= 1) {  // lambda-hat^{J,-M'}/y^2 d/dz psi_{M'-1}
     T Uzm = 0;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < R; ++t) {
       const int k = b + t;
-      if (k >= 0 && k < a.nz) Uzm = fma(a.D1z[zeta * 4 + t], a.P[blk - npts + (int64_t)k * a.nx * a.ny + xy], Uzm);
+      if (k >= 0 && k < a.nz) Uzm = fma(a.D1z[zeta * R + t], a.P[blk - npts + (int64_t)k * a.nx * a.ny + xy], Uzm);
     }
     out += a.lamm[iM] * iy2 * Uzm;
   }
@@ -194,10 +195,16 @@ struct CouplingArgs {
   int64_t src_npts[3];
   int snx[3], sny[3], snz[3];
   int nM;
+  // staged source (float32 path): per source, the y coefficients regrouped by y interval
+  const T* stage[3];    // [nM][nz][nx][nint_y][R] of the source component
+  int snint[3];         // y intervals of the source
+  int sdir;             // 1: Dirichlet y basis (base = q m - 1), so interval m = (base + 1) / q
+  int sq;               // functions per node
 };
 
-// V^(s) coupling: one thread per active collocation point of a component.
-template <typename T>
+// V^(s) coupling: one thread per active collocation point of a component; R x R x R taps of the source
+// expansion at the rotated point.
+template <int R, typename T>
 __global__ void __launch_bounds__(128) k_apply_coupling(CouplingArgs<T> a) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.n_act) return;
@@ -206,13 +213,13 @@ __global__ void __launch_bounds__(128) k_apply_coupling(CouplingArgs<T> a) {
   for (int m = 0; m < kMaxM; ++m) acc[m] = (T)0;
   for (int s = 0; s < a.ns; ++s) {
     const int bz = a.base[s][p], bx = a.base[s][a.n_act + p], by = a.base[s][2 * a.n_act + p];
-    T vz[4], vx[4], vy[4];
-    int iz[4], ix[4], iy[4];
+    T vz[R], vx[R], vy[R];
+    int iz[R], ix[R], iy[R];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      vz[t] = a.val[s][(0 + t) * (int64_t)a.n_act + p];
-      vx[t] = a.val[s][(4 + t) * (int64_t)a.n_act + p];
-      vy[t] = a.val[s][(8 + t) * (int64_t)a.n_act + p];
+    for (int t = 0; t < R; ++t) {
+      vz[t] = a.val[s][(0 * R + t) * (int64_t)a.n_act + p];
+      vx[t] = a.val[s][(1 * R + t) * (int64_t)a.n_act + p];
+      vy[t] = a.val[s][(2 * R + t) * (int64_t)a.n_act + p];
       iz[t] = min(max(bz + t, 0), a.snz[s] - 1);
       ix[t] = min(max(bx + t, 0), a.snx[s] - 1);
       iy[t] = min(max(by + t, 0), a.sny[s] - 1);
@@ -221,21 +228,106 @@ __global__ void __launch_bounds__(128) k_apply_coupling(CouplingArgs<T> a) {
       const T* cb = a.x + a.src_off[s] + (int64_t)jM * a.src_npts[s];
       T sz = 0;
 #pragma unroll
-      for (int tz = 0; tz < 4; ++tz) {
+      for (int tz = 0; tz < R; ++tz) {
         T sx = 0;
 #pragma unroll
-        for (int tx = 0; tx < 4; ++tx) {
+        for (int tx = 0; tx < R; ++tx) {
           const T* row = cb + ((int64_t)iz[tz] * a.snx[s] + ix[tx]) * a.sny[s];
           T sy = vy[0] * row[iy[0]];
-          sy = fma(vy[1], row[iy[1]], sy);
-          sy = fma(vy[2], row[iy[2]], sy);
-          sy = fma(vy[3], row[iy[3]], sy);
+#pragma unroll
+          for (int ty = 1; ty < R; ++ty) sy = fma(vy[ty], row[iy[ty]], sy);
           sx = fma(vx[tx], sy, sx);
         }
         sz = fma(vz[tz], sx, sz);
       }
       for (int iM = 0; iM < a.nM; ++iM)
         acc[iM] = fma(a.w[s][(int64_t)(iM * a.nM + jM) * a.n_act + p], sz, acc[iM]);
+    }
+  }
+  const int pt = a.act_pt[p];
+  for (int iM = 0; iM < a.nM; ++iM) a.y[a.row_off + (int64_t)iM * a.npts + pt] += acc[iM];
+}
+
+// The y coefficients of a component regrouped by y interval: T[row][m][t] = c[row][q m - d + t] for every
+// (M', k, i) row, interval m and tap t (0 outside the basis), so that the R taps a point of interval m
+// reads are contiguous and aligned.  One thread per (row, interval).
+template <int R>
+__global__ void __launch_bounds__(256) k_stage_ytaps(const float* __restrict__ c, float* __restrict__ T, int64_t rows,
+                                                     int ny, int nint, int q, int d) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= rows * nint) return;
+  const int64_t row = gid / nint;
+  const int m = (int)(gid - row * nint);
+  const float* cr = c + row * ny;
+  float v[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int j = q * m - d + t;
+    v[t] = (j >= 0 && j < ny) ? cr[j] : 0.f;
+  }
+  float* o = T + gid * R;
+  if constexpr (R == 4) {
+    *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int t = 0; t < R; t += 2) *reinterpret_cast<float2*>(o + t) = make_float2(v[t], v[t + 1]);
+  }
+}
+
+// The float32 V^(s) coupling on staged sources: the R y taps of a source row are one aligned vector load
+// (float4 for R = 4, three float2 for R = 6) instead of R scattered 4-byte loads.
+template <int R>
+__global__ void __launch_bounds__(128) k_apply_coupling_staged(CouplingArgs<float> a) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.n_act) return;
+  float acc[kMaxM];
+#pragma unroll
+  for (int m = 0; m < kMaxM; ++m) acc[m] = 0.f;
+  for (int s = 0; s < a.ns; ++s) {
+    const int bz = a.base[s][p], bx = a.base[s][a.n_act + p], by = a.base[s][2 * a.n_act + p];
+    float vz[R], vx[R], vy[R];
+    int iz[R], ix[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      vz[t] = a.val[s][(0 * R + t) * (int64_t)a.n_act + p];
+      vx[t] = a.val[s][(1 * R + t) * (int64_t)a.n_act + p];
+      vy[t] = a.val[s][(2 * R + t) * (int64_t)a.n_act + p];
+      iz[t] = min(max(bz + t, 0), a.snz[s] - 1);
+      ix[t] = min(max(bx + t, 0), a.snx[s] - 1);
+    }
+    // y interval of the point (a point outside the source box has base 0 and zero values)
+    const int my = min(max((by + a.sdir) / a.sq, 0), a.snint[s] - 1);
+    for (int jM = 0; jM < a.nM; ++jM) {
+      const float* tb = a.stage[s] + (int64_t)jM * a.snz[s] * a.snx[s] * a.snint[s] * R;
+      float sz = 0.f;
+#pragma unroll
+      for (int tz = 0; tz < R; ++tz) {
+        float sx = 0.f;
+#pragma unroll
+        for (int tx = 0; tx < R; ++tx) {
+          const float* row = tb + (((int64_t)iz[tz] * a.snx[s] + ix[tx]) * a.snint[s] + my) * R;
+          float sy;
+          if constexpr (R == 4) {
+            const float4 c4 = __ldg(reinterpret_cast<const float4*>(row));
+            sy = vy[0] * c4.x;
+            sy = fmaf(vy[1], c4.y, sy);
+            sy = fmaf(vy[2], c4.z, sy);
+            sy = fmaf(vy[3], c4.w, sy);
+          } else {
+            sy = 0.f;
+#pragma unroll
+            for (int t = 0; t < R; t += 2) {
+              const float2 c2 = __ldg(reinterpret_cast<const float2*>(row + t));
+              sy = fmaf(vy[t], c2.x, sy);
+              sy = fmaf(vy[t + 1], c2.y, sy);
+            }
+          }
+          sx = fmaf(vx[tx], sy, sx);
+        }
+        sz = fmaf(vz[tz], sx, sz);
+      }
+      for (int iM = 0; iM < a.nM; ++iM)
+        acc[iM] = fmaf(a.w[s][(int64_t)(iM * a.nM + jM) * a.n_act + p], sz, acc[iM]);
     }
   }
   const int pt = a.act_pt[p];
@@ -372,6 +464,8 @@ __global__ void __launch_bounds__(256) k_mix(const T* __restrict__ Wall, const T
 // the M'-chain of y-vectors t[iM][l - M'][i_x][:] interleaved as r = j * nc + c.
 struct YArgs {
   int nx, ny, nz, M0, nl, maxn;
+  int kq;                   // band half-width of the 1D y matrices (2 cubic, 4 quintic)
+  int pb;                   // cp.async piece bytes: 16, 8 or 4, dividing n_x and the component offset in bytes
   int64_t comp_off;
   const int* chain_lo;   // [nl]
   const int* chain_n;    // [nl]
@@ -390,7 +484,8 @@ struct YArgs {
 __device__ __forceinline__ void cp_async_pb(void* dst, const void* src, int pb) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
   if (pb == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  else if (pb == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
@@ -410,17 +505,21 @@ __device__ __forceinline__ void copy_segments(int nseg, int valid, int pb, SrcF 
   for (int sg = t / pps; sg < nseg; sg += spr) cp_async_pb(dst(sg) + k * ep, src(sg) + k * ep, pb);
 }
 
-// One line through the banded LU factors.  The forward sweep keeps x[r .. r+KL] in a register
-// window (the pivot swap is a select over the window), the backward sweep keeps the KL+KU solved
-// values x[r+1 ..] in registers and adds the newest one last, so the row-to-row dependency is a
-// couple of FMAs instead of a shared-memory round trip.
-template <typename T, int LPB, int KL>
+// One line through the banded LU factors, in place on the line's entries in global memory: seg(r) is the
+// entry of row r of the CTA's first line, and this thread's line is tid entries further.  Every row of both sweeps streams through a shared-memory
+// ring filled a chunk ahead by cooperative cp.async: a ring row holds the row's factor slots and, in its
+// last slot, one line value -- the right-hand side entry x[r + KL + 1] that enters the forward window at
+// row r, or the forward result z[r] the backward sweep starts from.  The forward sweep keeps x[r .. r+KL]
+// in a register window (the pivot swap is a select over the window) and writes z[r] back; the backward
+// sweep keeps the KL+KU solved values x[r+1 ..] in registers, adds the newest one last and writes x[r].
+template <typename T, int LPB, int KL, typename SegF>
 __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* __restrict__ Ub, int64_t nx, int n,
-                                            int R, T* xs, T* ring, int Wring, int tid, bool live, int valid,
+                                            int R, SegF seg, T* ring, int Wring, int tid, bool live, int valid,
                                             int pb) {
   constexpr int W = 2 * KL + 1;
   const int nch = (n + R - 1) / R;
-  const size_t half = (size_t)R * Wring * LPB;
+  const int RS = Wring + 1;  // slots per ring row (factor slots + the line value)
+  const size_t half = (size_t)R * RS * LPB;
   // forward: L z = P b, row r uses L[r][0] (pivot offset) and L[r][1..KL]
   auto issue_f = [&](int ch) {
     T* buf = ring + (ch & 1) * half;
@@ -428,12 +527,15 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
     copy_segments<T, LPB>(
         rows * (KL + 1), valid, pb,
         [&](int sg) { return Lb + ((int64_t)(r0 + sg / (KL + 1)) * (KL + 1) + sg % (KL + 1)) * nx; },
-        [&](int sg) { return buf + ((size_t)(sg / (KL + 1)) * Wring + sg % (KL + 1)) * LPB; });
+        [&](int sg) { return buf + ((size_t)(sg / (KL + 1)) * RS + sg % (KL + 1)) * LPB; });
+    const int lo = r0 + KL + 1, cnt = max(0, min(rows, n - lo));  // window refills of rows r0 .. r0 + cnt - 1
+    copy_segments<T, LPB>(cnt, valid, pb, [&](int sg) { return (const T*)seg(lo + sg); },
+                          [&](int sg) { return buf + ((size_t)sg * RS + Wring) * LPB; });
     cp_commit();
   };
   T w[KL + 1];
 #pragma unroll
-  for (int i = 0; i <= KL; ++i) w[i] = (live && i < n) ? xs[i * LPB + tid] : (T)0;
+  for (int i = 0; i <= KL; ++i) w[i] = (live && i < n) ? seg(i)[tid] : (T)0;
   issue_f(0);
   for (int ch = 0; ch < nch; ++ch) {
     if (ch + 1 < nch) {
@@ -448,7 +550,7 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
       const int r0 = ch * R, rows = min(R, n - r0);
       for (int q = 0; q < rows; ++q) {
         const int r = r0 + q;
-        const T* f = buf + (size_t)q * Wring * LPB + tid;
+        const T* f = buf + (size_t)q * RS * LPB + tid;
         const int p = (int)f[0];
         T xr = w[0];
 #pragma unroll
@@ -458,14 +560,17 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
           if (p == i) w[i] = w[0];
 #pragma unroll
         for (int d = 1; d <= KL; ++d) w[d] -= f[d * LPB] * xr;
-        xs[r * LPB + tid] = xr;
+        seg(r)[tid] = xr;
 #pragma unroll
         for (int i = 0; i < KL; ++i) w[i] = w[i + 1];
-        w[KL] = (r + KL + 1 < n) ? xs[(r + KL + 1) * LPB + tid] : (T)0;
+        w[KL] = (r + KL + 1 < n) ? f[Wring * LPB] : (T)0;
       }
     }
     __syncthreads();
   }
+  // the forward results must be in memory before the backward sweep reads them back through the ring
+  __threadfence();
+  __syncthreads();
   // backward: U x = z, rows descending, U[r][0] the reciprocal of the pivot, U[r][d] the coefficient
   // of x[r + d]; v[i] = x[r + 1 + i] (0 beyond the line, where the band entries are 0)
   auto issue_b = [&](int ch) {
@@ -473,7 +578,9 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
     const int rtop = n - 1 - ch * R, rows = min(R, rtop + 1);
     copy_segments<T, LPB>(
         rows * W, valid, pb, [&](int sg) { return Ub + ((int64_t)(rtop - sg / W) * W + sg % W) * nx; },
-        [&](int sg) { return buf + ((size_t)(sg / W) * Wring + sg % W) * LPB; });
+        [&](int sg) { return buf + ((size_t)(sg / W) * RS + sg % W) * LPB; });
+    copy_segments<T, LPB>(rows, valid, pb, [&](int sg) { return (const T*)seg(rtop - sg); },
+                          [&](int sg) { return buf + ((size_t)sg * RS + Wring) * LPB; });
     cp_commit();
   };
   T v[W - 1];
@@ -493,14 +600,14 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
       const int rows = min(R, n - ch * R);
       for (int q = 0; q < rows; ++q) {
         const int r = n - 1 - (ch * R + q);
-        const T* f = buf + (size_t)q * Wring * LPB + tid;
-        T s0 = xs[r * LPB + tid], s1 = 0;
+        const T* f = buf + (size_t)q * RS * LPB + tid;
+        T s0 = f[Wring * LPB], s1 = 0;
 #pragma unroll
         for (int d = 2; d < W; d += 2) s0 -= f[d * LPB] * v[d - 1];
 #pragma unroll
         for (int d = 3; d < W; d += 2) s1 -= f[d * LPB] * v[d - 1];
         const T x = ((s0 + s1) - f[LPB] * v[0]) * f[0];
-        xs[r * LPB + tid] = x;
+        seg(r)[tid] = x;
 #pragma unroll
         for (int i = W - 2; i > 0; --i) v[i] = v[i - 1];
         v[0] = x;
@@ -529,41 +636,42 @@ __global__ void __launch_bounds__(LPB) k_ysolve(const YBatch<T> yb, int R, int W
   if (il >= a.nl || ix0 >= a.nx) return;  // grid sized for the largest component (uniform per CTA)
   const int nc = a.chain_n[il], lo = a.chain_lo[il];
   const int n = nc * a.ny;
-  T* xs = reinterpret_cast<T*>(smraw);   // [n][LPB]
-  T* ring = xs + (size_t)maxn * LPB;     // [2][R][Wring][LPB]
+  T* ring = reinterpret_cast<T*>(smraw);  // [2][R][Wring + 1][LPB]
   const int tid = threadIdx.x;
   const int valid = min(LPB, a.nx - ix0);
   const bool live = tid < valid;
-  // 16-byte pieces when every segment start is 16-byte aligned, else 8-byte (n_x is even)
-  const int pb = ((a.nx * (int)sizeof(T)) % 16 == 0) ? 16 : 8;
+  // piece size chosen on the host so that every segment start (line rows and factor rows) is aligned to it
+  // and every CTA's valid line count is a whole number of pieces
+  const int pb = a.pb;
   const int l = a.M0 + il;
-  auto xrow = [&](int r) -> int64_t {
+  // entry of row r of the CTA's first line (the line of thread tid is tid elements further)
+  auto seg = [&](int r) -> T* {
     const int j = r / nc, c = r - j * nc;
     const int iM = lo + c, k = l - a.M0 - iM;
-    return a.comp_off + (((int64_t)iM * a.nz + k) * a.ny + j) * a.nx + ix0;
+    return t + a.comp_off + (((int64_t)iM * a.nz + k) * a.ny + j) * a.nx + ix0;
   };
-  copy_segments<T, LPB>(n, valid, pb, [&](int r) { return t + xrow(r); }, [&](int r) { return xs + (size_t)r * LPB; });
-  cp_commit();
-  cp_wait_all();
-  __syncthreads();
+  (void)maxn;
   const T* Lb = L + a.lmul_off[il] + ix0;
   const T* Ub = U + a.band_off[il] + ix0;
-  switch (nc) {
-    case 1: ysolve_line<T, LPB, 2>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    case 2: ysolve_line<T, LPB, 5>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    case 3: ysolve_line<T, LPB, 7>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    case 4: ysolve_line<T, LPB, 9>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    case 5: ysolve_line<T, LPB, 11>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    case 6: ysolve_line<T, LPB, 13>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    case 7: ysolve_line<T, LPB, 15>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    case 8: ysolve_line<T, LPB, 17>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    case 9: ysolve_line<T, LPB, 19>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    case 10: ysolve_line<T, LPB, 21>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    case 11: ysolve_line<T, LPB, 23>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
-    default: ysolve_line<T, LPB, 25>(Lb, Ub, a.nx, n, R, xs, ring, Wring, tid, live, valid, pb); break;
+  // band half-width of this chain (band_kl on the host; at most kMaxBandKL there)
+  const int KLc = (nc == 1) ? a.kq : a.kq * nc + 1;
+#define FM_YS(KLV) ysolve_line<T, LPB, KLV>(Lb, Ub, a.nx, n, R, seg, ring, Wring, tid, live, valid, pb)
+  switch (KLc) {
+    case 2: FM_YS(2); break;
+    case 4: FM_YS(4); break;
+    case 5: FM_YS(5); break;
+    case 7: FM_YS(7); break;
+    case 9: FM_YS(9); break;
+    case 11: FM_YS(11); break;
+    case 13: FM_YS(13); break;
+    case 15: FM_YS(15); break;
+    case 17: FM_YS(17); break;
+    case 19: FM_YS(19); break;
+    case 21: FM_YS(21); break;
+    case 23: FM_YS(23); break;
+    default: FM_YS(25); break;
   }
-  if (live)
-    for (int r = 0; r < n; ++r) t[xrow(r) + tid] = xs[r * LPB + tid];
+#undef FM_YS
 }
 
 // ---------------------------------------------------------------------------
@@ -693,6 +801,60 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_many(const double* __restri
           const double* vv = reinterpret_cast<const double*>(vp[u]);
           if (LOWP) accf[u] = fmaf(f64_lead_f32(vv[e]), f64_lead_f32(w[e]), accf[u]);
           else acc[u] = fma(vv[e], w[e], acc[u]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < JT; ++u) {
+      double v = LOWP ? (double)accf[u] : acc[u];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[u][wid] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nj) {
+      double r = 0.0;
+      for (int q = 0; q < kRedThreads / 32; ++q) r += sh[threadIdx.x][q];
+      partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = r;
+    }
+    __syncthreads();
+  }
+  last_block_reduce(partial, nt, counter, out);
+}
+
+// k_dot_many with scalar loads: for vectors that do not all start on 16-byte boundaries (odd strides)
+template <bool LOWP>
+__global__ void __launch_bounds__(kRedThreads) k_dot_many_s(const double* __restrict__ V, int64_t ldv, int nv,
+                                                           const double* __restrict__ w, int64_t n,
+                                                           double* __restrict__ partial, const double* __restrict__ extra,
+                                                           unsigned* counter, double* __restrict__ out) {
+  constexpr int JT = 8;
+  __shared__ double sh[JT][kRedThreads / 32];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  const int nt = nv + (extra ? 1 : 0);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j0 = 0; j0 < nt; j0 += JT) {
+    const int nj = min(JT, nt - j0);
+    const double* vp[JT];
+#pragma unroll
+    for (int u = 0; u < JT; ++u) {
+      const int j = j0 + min(u, nj - 1);
+      vp[u] = (j < nv) ? V + (int64_t)j * ldv : extra;
+    }
+    double acc[JT];
+    float accf[JT];
+#pragma unroll
+    for (int u = 0; u < JT; ++u) {
+      acc[u] = 0.0;
+      accf[u] = 0.f;
+    }
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int u = 0; u < JT; ++u)
+        if (u < nj) {
+          if (LOWP) accf[u] = fmaf(f64_lead_f32(vp[u][i]), f64_lead_f32(wi), accf[u]);
+          else acc[u] = fma(vp[u][i], wi, acc[u]);
         }
     }
 #pragma unroll
@@ -1094,13 +1256,19 @@ static int apply_t(fm_ctx* c, double E, const T* x, T* y, bool only_S, T* P, T* 
     const ApplyTabs<T> tb = tabs_of<T>(cp);
     const int64_t off = cp.off;
     constexpr int TX = 8;
-    const size_t smem = (size_t)3 * (TX + 2) * cp.ny * sizeof(T);
+    const int rows = cp.ax.tile_rows(TX), RT = cp.r;
+    const size_t smem = (size_t)3 * rows * cp.ny * sizeof(T);
     dim3 g1((cp.nx + TX - 1) / TX, cp.nz * c->nM);
     {
       const int tk_ = timed ? prof_begin(c, FM_KERNEL_APPLY_XY) : -1;
-      k_apply_xy<TX, T><<<g1, 256, smem, c->stream>>>(x + off, P + off, Q + off, R + off, cp.nx, cp.ny, cp.dx.base, tb.Sx,
-                                                      tb.D2x, cp.dy.base, tb.Sy, tb.D2y, only_S);
-      prof_end(c, tk_, fscale * cp.npts * c->nM * (only_S ? 16.0 : 40.0), (double)cp.npts * c->nM * (only_S ? 2.0 : 4.0) * sizeof(T));
+      if (RT == 6)
+        k_apply_xy<TX, 6, T><<<g1, 256, smem, c->stream>>>(x + off, P + off, Q + off, R + off, cp.nx, cp.ny, rows,
+                                                           cp.dx.base, tb.Sx, tb.D2x, cp.dy.base, tb.Sy, tb.D2y, only_S);
+      else
+        k_apply_xy<TX, 4, T><<<g1, 256, smem, c->stream>>>(x + off, P + off, Q + off, R + off, cp.nx, cp.ny, rows,
+                                                           cp.dx.base, tb.Sx, tb.D2x, cp.dy.base, tb.Sy, tb.D2y, only_S);
+      prof_end(c, tk_, fscale * cp.npts * c->nM * RT * (only_S ? 4.0 : 10.0),
+               (double)cp.npts * c->nM * (only_S ? 2.0 : 4.0) * sizeof(T));
     }
     c->launches++;
     ZPassArgs<T> a;
@@ -1117,11 +1285,25 @@ static int apply_t(fm_ctx* c, double E, const T* x, T* y, bool only_S, T* P, T* 
     const int64_t tot = cp.npts * c->nM;
     {
       const int tk_ = timed ? prof_begin(c, FM_KERNEL_APPLY_Z) : -1;
-      k_apply_z<T><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(a, only_S);
-      prof_end(c, tk_, (double)tot * (only_S ? 8.0 : (10.0 + (c->nM > 1 ? 32.0 : 0.0) + 40.0)),
+      if (RT == 6) k_apply_z<6, T><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(a, only_S);
+      else k_apply_z<4, T><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(a, only_S);
+      prof_end(c, tk_, (double)tot * (only_S ? 2.0 * RT : (10.0 + (c->nM > 1 ? 8.0 * RT : 0.0) + 10.0 * RT)),
                (double)tot * (only_S ? 2.0 : 7.0) * sizeof(T));
     }
     c->launches++;
+  }
+  const bool staged = std::is_same<T, float>::value && c->ystage32 != nullptr;
+  if (!only_S && staged) {  // float32: regroup every source component's y coefficients by y interval
+    for (auto& cp : c->comps) {
+      const int64_t rows = (int64_t)c->nM * cp.nz * cp.nx, items = rows * cp.ay.nint;
+      const int tk_ = timed ? prof_begin(c, FM_KERNEL_COUPLING) : -1;
+      const float* xs = reinterpret_cast<const float*>(x) + cp.off;
+      float* ts = c->ystage32 + cp.ystage_off;
+      if (cp.r == 6) k_stage_ytaps<6><<<(unsigned)((items + 255) / 256), 256, 0, c->stream>>>(xs, ts, rows, cp.ny, cp.ay.nint, cp.ay.q, 1);
+      else k_stage_ytaps<4><<<(unsigned)((items + 255) / 256), 256, 0, c->stream>>>(xs, ts, rows, cp.ny, cp.ay.nint, cp.ay.q, 1);
+      prof_end(c, tk_, 0.0, (double)rows * cp.ny * 4.0 + (double)items * cp.r * 4.0);
+      c->launches++;
+    }
   }
   if (!only_S) {
     for (auto& cp : c->comps) {
@@ -1130,19 +1312,40 @@ static int apply_t(fm_ctx* c, double E, const T* x, T* y, bool only_S, T* P, T* 
       CouplingArgs<T> a{};
       a.x = x; a.y = y; a.row_off = cp.off; a.npts = cp.npts; a.n_act = cp.n_act; a.act_pt = cp.act_pt;
       a.ns = (int)cp.sources.size(); a.nM = c->nM;
+      const int RT = cp.r;
       for (int s = 0; s < a.ns; ++s) {
         const auto& src = c->comps[cp.sources[s].src];
         a.base[s] = cp.cpl_base + (int64_t)s * 3 * cp.n_act;
-        a.val[s] = tb.cval + (int64_t)s * 12 * cp.n_act;
+        a.val[s] = tb.cval + (int64_t)s * 3 * RT * cp.n_act;
         a.w[s] = tb.cw + (int64_t)s * c->nM * c->nM * cp.n_act;
         a.src_off[s] = src.off; a.src_npts[s] = src.npts;
         a.snx[s] = src.nx; a.sny[s] = src.ny; a.snz[s] = src.nz;
+        if (staged) {
+          a.stage[s] = reinterpret_cast<const T*>(c->ystage32 + src.ystage_off);
+          a.snint[s] = src.ay.nint;
+        }
       }
+      a.sdir = 1;
+      a.sq = cp.ay.q;
       {
         const int tk_ = timed ? prof_begin(c, FM_KERNEL_COUPLING) : -1;
-        k_apply_coupling<T><<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
-        prof_end(c, tk_, (double)cp.n_act * a.ns * (168.0 * c->nM + 2.0 * c->nM * c->nM),
-                 (double)cp.n_act * (4.0 + 2.0 * c->nM * sizeof(T) + a.ns * (12.0 + (12.0 + c->nM * c->nM) * sizeof(T))));
+        if constexpr (std::is_same<T, float>::value) {
+          if (staged) {
+            if (RT == 6) k_apply_coupling_staged<6><<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
+            else k_apply_coupling_staged<4><<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
+          } else if (RT == 6) {
+            k_apply_coupling<6, T><<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
+          } else {
+            k_apply_coupling<4, T><<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
+          }
+        } else {
+          if (RT == 6) k_apply_coupling<6, T><<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
+          else k_apply_coupling<4, T><<<(cp.n_act + 127) / 128, 128, 0, c->stream>>>(a);
+        }
+        // per (point, source): 2 (R^3 + R^2 + R) contraction flops per M'' and 2 n_M^2 for the weights
+        const double cfl = 2.0 * (RT * RT * RT + RT * RT + RT);
+        prof_end(c, tk_, (double)cp.n_act * a.ns * (cfl * c->nM + 2.0 * c->nM * c->nM),
+                 (double)cp.n_act * (4.0 + 2.0 * c->nM * sizeof(T) + a.ns * (12.0 + (3.0 * RT + c->nM * c->nM) * sizeof(T))));
       }
       c->launches++;
     }
@@ -1179,12 +1382,23 @@ static int ysolve_banded(fm_ctx* c, const std::vector<fmi::Comp*>& comps, T* u) 
   for (size_t q = 0; q < comps.size(); ++q) {
     const fmi::Comp& cp = *comps[q];
     for (int il = 0; il < cp.nl; ++il) {
-      const int nc = cp.chain_n[il], n = nc * cp.ny, kl = (nc == 1) ? 2 : 2 * nc + 1;
+      const int nc = cp.chain_n[il], n = nc * cp.ny, kl = band_kl(cp.ay, nc);
       yfl += (double)cp.nx * (2.0 * n * (3.0 * kl) + n);
       yby += (double)cp.nx * ((double)n * (3.0 * kl + 2.0) * ts + 2.0 * n * ts);
     }
     YArgs& ya = yb.a[q];
     ya.nx = cp.nx; ya.ny = cp.ny; ya.nz = cp.nz; ya.M0 = c->M0; ya.nl = cp.nl; ya.comp_off = cp.off;
+    ya.kq = std::max(cp.ay.kl, cp.ay.ku);
+    // the largest piece dividing the byte length of an x row and the component's byte offset (line rows
+    // start at comp_off + multiple of n_x; factor rows at multiples of n_x); at least one element
+    ya.pb = (int)sizeof(T);
+    for (int pcand : {16, 8}) {
+      if (pcand <= (int)sizeof(T)) break;
+      if (((int64_t)cp.nx * (int64_t)sizeof(T)) % pcand == 0 && ((int64_t)cp.off * (int64_t)sizeof(T)) % pcand == 0) {
+        ya.pb = pcand;
+        break;
+      }
+    }
     ya.chain_lo = (const int*)cp.d_chain_lo; ya.chain_n = (const int*)cp.d_chain_n;
     ya.band_off = cp.d_band_off; ya.lmul_off = cp.d_lmul_off;
     int maxnc = 1;
@@ -1192,31 +1406,29 @@ static int ysolve_banded(fm_ctx* c, const std::vector<fmi::Comp*>& comps, T* u) 
     ya.maxn = maxnc * cp.ny;
     yb.U[q] = std::is_same<T, double>::value ? (const T*)cp.yU : (const T*)cp.yU32;
     yb.L[q] = std::is_same<T, double>::value ? (const T*)cp.yL : (const T*)cp.yL32;
-    const int klmax = (maxnc == 1) ? 2 : 2 * maxnc + 1;
+    int klmax = 2;
+    for (int v : cp.chain_n) klmax = std::max(klmax, band_kl(cp.ay, v));
     maxn = std::max(maxn, ya.maxn);
     wring = std::max(wring, 2 * klmax + 1);
     gy = std::max(gy, cp.nl);
   }
   int maxnx = 1;
   for (auto* cp : comps) maxnx = std::max(maxnx, cp->nx);
-  // Lines per CTA, and factor rows per ring half: the CTAs are latency-bound, so the ring is sized
-  // for as many resident CTAs per SM as the grid can use (228 KB of shared memory per SM), with at
-  // least 8 rows of prefetch; failing that, the largest ring that fits 200 KB.
+  // Lines per CTA, and rows per ring half (factor slots plus the line value): the CTAs are latency-bound,
+  // so the ring is sized for as many resident CTAs per SM as the grid can use (228 KB of shared memory per
+  // SM), between 4 and 32 rows a half.
   auto plan = [&](int lpb, int* R, size_t* sm) -> bool {
-    const size_t line = (size_t)maxn * lpb * sizeof(T), per_row = 2 * (size_t)wring * lpb * sizeof(T);
+    const size_t per_row = 2 * (size_t)(wring + 1) * lpb * sizeof(T);
     const int ctas = ((maxnx + lpb - 1) / lpb) * gy * (int)comps.size();
-    const int per_sm = std::max(1, std::min(8, (ctas + 151) / 152));
+    const int per_sm = std::max(1, std::min(16, (ctas + 151) / 152));
     for (int want = per_sm; want >= 1; --want) {
       const size_t cap = std::min<size_t>(200 * 1024, 233472 / want - 1024);
-      if (line + 8 * per_row > cap) continue;
-      *R = (int)std::min<size_t>(32, (cap - line) / per_row);
-      *sm = line + (size_t)*R * per_row;
+      if (4 * per_row > cap) continue;
+      *R = (int)std::min<size_t>(32, cap / per_row);
+      *sm = (size_t)*R * per_row;
       return true;
     }
-    if (line + 2 * per_row > 200 * 1024) return false;
-    *R = (int)std::min<size_t>(32, (200 * 1024 - line) / per_row);
-    *sm = line + (size_t)*R * per_row;
-    return true;
+    return false;
   };
   const int tk_ = prof_begin(c, FM_KERNEL_YSOLVE);
   int R;
@@ -1228,7 +1440,7 @@ static int ysolve_banded(fm_ctx* c, const std::vector<fmi::Comp*>& comps, T* u) 
     gx = (maxnx + 7) / 8;
     k_ysolve<T, 8><<<dim3(gx, gy, (unsigned)comps.size()), 8, sm, c->stream>>>(yb, R, wring, maxn, u);
   } else {
-    return FM_ERR_ARG;  // M' chains too long for one line in shared memory
+    return FM_ERR_ARG;  // band too wide for the ring
   }
   prof_end(c, tk_, yfl, yby);
   c->launches++;
@@ -1246,13 +1458,16 @@ static int precond_impl(fm_ctx* c, const TIO* x, TIO* y, T* t) {
   T* u = is32 ? (T*)c->u32 : (T*)c->u64;
   std::vector<fmi::Comp*> banded;
   int rc;
+  if (tc) {  // z, x and y stages on the tensor cores
+    if ((rc = fmi::precond_tc_front<TIO>(c, x, &banded))) return rc;
+    if ((rc = ysolve_banded<T>(c, banded, u))) return rc;
+    if ((rc = fmi::precond_tc_back<TIO>(c, y))) return rc;
+    FM_CUDA(cudaGetLastError());
+    return FM_OK;
+  }
   for (auto& cp : c->comps) {
     const bool ymda = cp.ydiag_ok && (c->opts.y_solver == 2 || (c->opts.y_solver == 0 && is32));
     if (!ymda) banded.push_back(&cp);
-    if (tc) {  // x and y stages on the tensor cores
-      if ((rc = fmi::precond_tc_front<TIO>(c, cp, x, ymda))) return rc;
-      continue;
-    }
     const int64_t nxy = (int64_t)cp.nx * cp.ny;
     const T* Wzb = std::is_same<T, double>::value ? (const T*)cp.Wzb : (const T*)cp.Wzb32;
     const T* Wxb = std::is_same<T, double>::value ? (const T*)cp.Wxb : (const T*)cp.Wxb32;
@@ -1294,10 +1509,6 @@ static int precond_impl(fm_ctx* c, const TIO* x, TIO* y, T* t) {
   }
   if ((rc = ysolve_banded<T>(c, banded, u))) return rc;
   for (auto& cp : c->comps) {
-    if (tc) {
-      if ((rc = fmi::precond_tc_back<TIO>(c, cp, y))) return rc;
-      continue;
-    }
     const int64_t nxy = (int64_t)cp.nx * cp.ny;
     const T* Wz = std::is_same<T, double>::value ? (const T*)cp.Wz : (const T*)cp.Wz32;
     const T* Wx = std::is_same<T, double>::value ? (const T*)cp.Wx : (const T*)cp.Wx32;
@@ -1349,13 +1560,16 @@ int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* 
   const int nb = c->red_blocks;
   const int nt = nv + (extra ? 1 : 0);
   if (nt > kGsMaxVec) return FM_ERR_ARG;
-  // 16-byte element pairs: every vector must start on a 16-byte boundary (n_x is even, so N is)
+  // 16-byte element pairs when every vector starts on a 16-byte boundary, scalar loads otherwise (an odd
+  // vector length puts every other basis vector on an 8-byte boundary)
   const uintptr_t al = reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w) |
                        reinterpret_cast<uintptr_t>(extra) | (uintptr_t)(ldv * 8);
-  if (al & 15u) return FM_ERR_ARG;
+  const bool pairs = (al & 15u) == 0;
   const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-  if (lowp) k_dot_many<true><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
-  else k_dot_many<false><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
+  if (pairs && lowp) k_dot_many<true><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
+  else if (pairs) k_dot_many<false><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
+  else if (lowp) k_dot_many_s<true><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
+  else k_dot_many_s<false><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, extra, c->gs_cnt, h_dev);
   prof_end(c, tk_, 2.0 * nt * (double)c->N, (nt + 1.0) * 8.0 * (double)c->N);
   c->launches++;
   FM_CUDA(cudaGetLastError());
@@ -1429,15 +1643,17 @@ int gs_cgs2(fm_ctx* c, const double* V, int nv, double* w, double* vout, double*
 int gs_cgs2_32(fm_ctx* c, const float* V, int nv, float* w, float* vout, double* h, double* hn) {
   if (nv < 1 || nv > kGsMaxVec) return FM_ERR_ARG;
   const int64_t N = c->N;
+  // 16-byte quads when every vector starts on a 16-byte boundary (N a multiple of 4), scalar loads otherwise
   const uintptr_t al = reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w) | (uintptr_t)(N * 4);
-  if (al & 15u) return FM_ERR_ARG;
+  const bool quads = (al & 15u) == 0;
   double* h1 = c->gsd;
   double* h2 = c->gsd + kGsMaxVec;
   double* sc = c->gsd + 3 * kGsMaxVec;
   const int nb = c->red_blocks, nb2 = 4 * c->red_blocks;
   {
     const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_many32v<<<nb, kRedThreads, 0, c->stream>>>(V, N, nv, w, N, c->red, c->gs_cnt, h1);
+    if (quads) k_dot_many32v<<<nb, kRedThreads, 0, c->stream>>>(V, N, nv, w, N, c->red, c->gs_cnt, h1);
+    else k_dot_many32<<<nb, kRedThreads, 0, c->stream>>>(V, N, nv, w, N, c->red, c->gs_cnt, h1);
     prof_end(c, tk_, 2.0 * nv * (double)N, (nv + 1.0) * 4.0 * (double)N);
   }
   {
@@ -1447,7 +1663,8 @@ int gs_cgs2_32(fm_ctx* c, const float* V, int nv, float* w, float* vout, double*
   }
   {
     const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-    k_dot_many32v<<<nb, kRedThreads, 0, c->stream>>>(V, N, nv, w, N, c->red, c->gs_cnt, h2);
+    if (quads) k_dot_many32v<<<nb, kRedThreads, 0, c->stream>>>(V, N, nv, w, N, c->red, c->gs_cnt, h2);
+    else k_dot_many32<<<nb, kRedThreads, 0, c->stream>>>(V, N, nv, w, N, c->red, c->gs_cnt, h2);
     prof_end(c, tk_, 2.0 * nv * (double)N, (nv + 1.0) * 4.0 * (double)N);
   }
   {
@@ -1669,8 +1886,10 @@ int axpby32(fm_ctx* c, float a, const float* x, float b, float* y) {
 
 int kernels_init(fm_ctx* c) {
   (void)c;
-  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, 4, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, 4, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, 6, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, 6, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<double, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<float, double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));

@@ -5,6 +5,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <thread>
 #include <vector>
@@ -15,29 +18,59 @@
 namespace fmi {
 
 // ---------------------------------------------------------------------------
-// cubic Hermite shape functions on [t_m, t_m + h], local coordinate s in [0, 1]:
-// order (value left, slope left, value right, slope right)
+// Hermite shape functions on [t_m, t_m + h], local coordinate s in [0, 1].
+// Cubic (q = 2): value left, slope left, value right, slope right.
+// Quintic (q = 3, S_5^3 of Section 4): value, first and second derivative at the left node, then at the
+// right node -- the degree-5 polynomials with one unit condition among those six; derivative dofs are
+// with respect to t, hence the powers of h.  deriv = order of the t-derivative returned.
 // ---------------------------------------------------------------------------
-static void shapes(double s, double h, int deriv, double v[4]) {
+static void shapes(double s, double h, int deriv, int q, double* v) {
   const double u = 1.0 - s;
+  if (q == 2) {
+    if (deriv == 0) {
+      v[0] = (1.0 + 2.0 * s) * u * u;
+      v[1] = s * u * u * h;
+      v[2] = s * s * (3.0 - 2.0 * s);
+      v[3] = s * s * (s - 1.0) * h;
+    } else if (deriv == 1) {
+      v[0] = 6.0 * s * (s - 1.0) / h;
+      v[1] = u * (1.0 - 3.0 * s);
+      v[2] = 6.0 * s * u / h;
+      v[3] = s * (3.0 * s - 2.0);
+    } else {
+      v[0] = (12.0 * s - 6.0) / (h * h);
+      v[1] = (6.0 * s - 4.0) / h;
+      v[2] = (6.0 - 12.0 * s) / (h * h);
+      v[3] = (6.0 * s - 2.0) / h;
+    }
+    return;
+  }
+  const double s2 = s * s, s3 = s2 * s, s4 = s3 * s, s5 = s4 * s;
   if (deriv == 0) {
-    v[0] = (1.0 + 2.0 * s) * u * u;
-    v[1] = s * u * u * h;
-    v[2] = s * s * (3.0 - 2.0 * s);
-    v[3] = s * s * (s - 1.0) * h;
+    v[0] = 1.0 - 10.0 * s3 + 15.0 * s4 - 6.0 * s5;
+    v[1] = (s - 6.0 * s3 + 8.0 * s4 - 3.0 * s5) * h;
+    v[2] = 0.5 * s2 * u * u * u * h * h;
+    v[3] = 10.0 * s3 - 15.0 * s4 + 6.0 * s5;
+    v[4] = (-4.0 * s3 + 7.0 * s4 - 3.0 * s5) * h;
+    v[5] = 0.5 * s3 * u * u * h * h;
   } else if (deriv == 1) {
-    v[0] = 6.0 * s * (s - 1.0) / h;
-    v[1] = u * (1.0 - 3.0 * s);
-    v[2] = 6.0 * s * u / h;
-    v[3] = s * (3.0 * s - 2.0);
+    v[0] = (-30.0 * s2 + 60.0 * s3 - 30.0 * s4) / h;
+    v[1] = 1.0 - 18.0 * s2 + 32.0 * s3 - 15.0 * s4;
+    v[2] = 0.5 * (2.0 * s - 9.0 * s2 + 12.0 * s3 - 5.0 * s4) * h;
+    v[3] = (30.0 * s2 - 60.0 * s3 + 30.0 * s4) / h;
+    v[4] = -12.0 * s2 + 28.0 * s3 - 15.0 * s4;
+    v[5] = 0.5 * (3.0 * s2 - 8.0 * s3 + 5.0 * s4) * h;
   } else {
-    v[0] = (12.0 * s - 6.0) / (h * h);
-    v[1] = (6.0 * s - 4.0) / h;
-    v[2] = (6.0 - 12.0 * s) / (h * h);
-    v[3] = (6.0 * s - 2.0) / h;
+    v[0] = (-60.0 * s + 180.0 * s2 - 120.0 * s3) / (h * h);
+    v[1] = (-36.0 * s + 96.0 * s2 - 60.0 * s3) / h;
+    v[2] = 0.5 * (2.0 - 18.0 * s + 36.0 * s2 - 20.0 * s3);
+    v[3] = (60.0 * s - 180.0 * s2 + 120.0 * s3) / (h * h);
+    v[4] = (-24.0 * s + 84.0 * s2 - 60.0 * s3) / h;
+    v[5] = 0.5 * (6.0 * s - 24.0 * s2 + 20.0 * s3);
   }
 }
 
+// q Gauss-Legendre nodes on [-1, 1], ascending: closed forms for q <= 4, Newton on P_q otherwise
 static void gauss(int q, double* g) {
   if (q == 2) {
     const double a = 1.0 / std::sqrt(3.0);
@@ -45,35 +78,53 @@ static void gauss(int q, double* g) {
   } else if (q == 3) {
     const double a = std::sqrt(0.6);
     g[0] = -a; g[1] = 0.0; g[2] = a;
-  } else {  // 4
+  } else if (q == 4) {
     const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(1.2));
     const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(1.2));
     g[0] = -b; g[1] = -a; g[2] = a; g[3] = b;
+  } else {
+    for (int i = 0; i < q; ++i) {
+      double x = std::cos(M_PI * (i + 0.75) / (q + 0.5));  // the i-th largest root, approximately
+      for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = x;  // Legendre recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}
+        for (int k = 1; k < q; ++k) {
+          const double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+          p0 = p1;
+          p1 = p2;
+        }
+        const double dp = q * (x * p1 - p0) / (x * x - 1.0);
+        const double dx = p1 / dp;
+        x -= dx;
+        if (std::fabs(dx) < 1e-16) break;
+      }
+      g[q - 1 - i] = x;
+    }
   }
 }
 
-// taps for interval m: the Dirichlet basis drops the value functions of the end nodes;
-// the slope function of the last node then sits at tap 2.
-static void place(const Axis& A, int m, const double sh[4], int* base, double v[4]) {
+// taps for interval m: base q m (- 1 with the Dirichlet basis, which drops the value functions of the
+// end nodes: the first interval's tap 0 is then outside the basis, and in the last interval the taps
+// after the dropped value function move down one place so that the r taps stay contiguous).
+static void place(const Axis& A, int m, const double* sh, int* base, double* v) {
+  const int q = A.q, r = A.r;
   if (!A.dirichlet) {
-    *base = 2 * m;
-    for (int t = 0; t < 4; ++t) v[t] = sh[t];
+    *base = q * m;
+    for (int t = 0; t < r; ++t) v[t] = sh[t];
     return;
   }
-  *base = 2 * m - 1;
-  v[0] = (m == 0) ? 0.0 : sh[0];
-  v[1] = sh[1];
+  *base = q * m - 1;
+  for (int t = 0; t < r; ++t) v[t] = sh[t];
+  if (m == 0) v[0] = 0.0;
   if (m == A.nint - 1) {
-    v[2] = sh[3];
-    v[3] = 0.0;
-  } else {
-    v[2] = sh[2];
-    v[3] = sh[3];
+    for (int t = q; t < r - 1; ++t) v[t] = sh[t + 1];
+    v[r - 1] = 0.0;
   }
 }
 
-void Axis::build(int kind_, int nint_, double a_, double b_, bool dirichlet_) {
+void Axis::build(int kind_, int nint_, double a_, double b_, bool dirichlet_, int basis) {
   kind = kind_; nint = nint_; a = a_; b = b_; dirichlet = dirichlet_;
+  q = (basis == 1) ? 3 : 2;
+  r = 2 * q;
   nodes.resize(nint + 1);
   for (int i = 0; i <= nint; ++i) {
     const double u = (double)i / nint;
@@ -83,29 +134,60 @@ void Axis::build(int kind_, int nint_, double a_, double b_, bool dirichlet_) {
   }
   nodes[0] = a;
   nodes[nint] = b;
-  n = 2 * (nint + 1) - (dirichlet ? 2 : 0);
+  n = q * (nint + 1) - (dirichlet ? 2 : 0);
   pts.clear(); base.clear(); S.clear(); D1.clear(); D2.clear();
+  // Gauss points per interval, as many in all as functions: cubic 2 (closed z: 3 in the first and last
+  // intervals); quintic 3 (x, y: 4 in the first interval; closed z: one more in the first, the last and
+  // the middle interval nint / 2; a single interval takes all)
+  std::vector<int> cnt(nint, q);
+  if (q == 2) {
+    if (!dirichlet) {
+      if (nint == 1) cnt[0] = 4;
+      else cnt[0] = cnt[nint - 1] = 3;
+    }
+  } else if (dirichlet) {
+    cnt[0] += 1;
+  } else if (nint == 1) {
+    cnt[0] = 6;
+  } else {
+    cnt[0] += 1;
+    cnt[nint - 1] += 1;
+    cnt[nint / 2] += 1;
+  }
   for (int m = 0; m < nint; ++m) {
-    int q = 2;
-    if (!dirichlet) q = (nint == 1) ? 4 : ((m == 0 || m == nint - 1) ? 3 : 2);
-    double g[4];
-    gauss(q, g);
+    double g[8];
+    gauss(cnt[m], g);
     const double h = nodes[m + 1] - nodes[m];
-    for (int e = 0; e < q; ++e) {
+    for (int e = 0; e < cnt[m]; ++e) {
       const double s = 0.5 * (1.0 + g[e]);
       const double p = nodes[m] + h * s;
       pts.push_back(p);
-      double sh[4], v[4];
+      double sh[kMaxTaps], v[kMaxTaps];
       int bb;
       for (int d = 0; d < 3; ++d) {
-        shapes(s, h, d, sh);
+        shapes(s, h, d, q, sh);
         place(*this, m, sh, &bb, v);
         std::vector<double>& dst = d == 0 ? S : (d == 1 ? D1 : D2);
-        for (int t = 0; t < 4; ++t) dst.push_back(v[t]);
+        for (int t = 0; t < r; ++t) dst.push_back(v[t]);
       }
       base.push_back(bb);
     }
   }
+  kl = ku = 0;
+  for (int e = 0; e < (int)pts.size(); ++e) {
+    const int lo = std::max(base[e], 0), hi = std::min(base[e] + r - 1, n - 1);
+    kl = std::max(kl, e - lo);
+    ku = std::max(ku, hi - e);
+  }
+}
+
+int Axis::tile_rows(int tx) const {
+  int rows = 1;
+  for (int e0 = 0; e0 < (int)pts.size(); e0 += tx) {
+    const int e1 = std::min((int)pts.size(), e0 + tx) - 1;
+    rows = std::max(rows, base[e1] + r - base[e0]);
+  }
+  return rows;
 }
 
 int Axis::locate(double p) const {
@@ -113,16 +195,16 @@ int Axis::locate(double p) const {
   return std::min(std::max(m, 0), nint - 1);
 }
 
-void Axis::eval(double p, int deriv, int* base_out, double v[4]) const {
+void Axis::eval(double p, int deriv, int* base_out, double v[kMaxTaps]) const {
   if (!(p >= a && p <= b)) {
     *base_out = 0;
-    v[0] = v[1] = v[2] = v[3] = 0.0;
+    for (int t = 0; t < kMaxTaps; ++t) v[t] = 0.0;
     return;
   }
   const int m = locate(p);
   const double h = nodes[m + 1] - nodes[m];
-  double sh[4];
-  shapes((p - nodes[m]) / h, h, deriv, sh);
+  double sh[kMaxTaps];
+  shapes((p - nodes[m]) / h, h, deriv, q, sh);
   place(*this, m, sh, base_out, v);
 }
 
@@ -261,6 +343,18 @@ static void parallel_for(int n, F f) {
   for (auto& t : th) t.join();
 }
 
+// Wall-clock phases of the set-up, printed to stderr when FM_VERBOSE is set.
+struct PhaseTimer {
+  bool on = getenv("FM_VERBOSE") != nullptr;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  void mark(const char* what) {
+    if (!on) return;
+    const auto now = std::chrono::steady_clock::now();
+    fprintf(stderr, "[fm_setup] %-28s %8.1f ms\n", what, std::chrono::duration<double, std::milli>(now - t).count());
+    t = now;
+  }
+};
+
 static int upload_axis(fm_ctx* c, const Axis& A, AxisDev& D) {
   int rc;
   if ((rc = upload(c, (void**)&D.base, A.base.data(), A.base.size() * sizeof(int)))) return rc;
@@ -274,14 +368,33 @@ static int upload_axis(fm_ctx* c, const Axis& A, AxisDev& D) {
 static std::vector<double> dense_of(const Axis& A, const std::vector<double>& vals) {
   std::vector<double> M((size_t)A.n * A.n, 0.0);
   for (int q = 0; q < A.n; ++q)
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < A.r; ++t) {
       const int j = A.base[q] + t;
-      if (j >= 0 && j < A.n) M[(size_t)q * A.n + j] += vals[q * 4 + t];
+      if (j >= 0 && j < A.n) M[(size_t)q * A.n + j] += vals[q * A.r + t];
     }
   return M;
 }
 
 static std::vector<float> to_f32(const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); }
+
+// bfloat16 bits of v: the high half of the float32 pattern, rounded to nearest even
+uint16_t f2bf(float v) {
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);  // NaN stays NaN
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+static std::vector<uint16_t> to_bf16(const std::vector<double>& v) {
+  std::vector<uint16_t> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = f2bf((float)v[i]);
+  return o;
+}
+
+static bool tc_requested(const fm_ctx* c) {
+  return c->opts.precision != FM_PREC_FP64 && c->opts.mma != FM_MMA_SIMT;
+}
 
 int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
   const fm_system& S = c->sys;
@@ -304,12 +417,15 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
   for (size_t ic = 0; ic < labels.size(); ++ic) {
     Comp& cp = c->comps[ic];
     const fm_grid& g = grids[n_grids == 1 ? 0 : ic];
-    if (g.nint_x < 1 || g.nint_y < 1 || g.nint_z < 1 || !(g.Rx > 0) || !(g.Ry > 0) || g.basis != 0) return FM_ERR_ARG;
+    if (g.nint_x < 1 || g.nint_y < 1 || g.nint_z < 1 || !(g.Rx > 0) || !(g.Ry > 0) || g.basis < 0 || g.basis > 1)
+      return FM_ERR_ARG;
     if (g.zmap == FM_MAP_POW || g.xmap == FM_MAP_SIN || g.ymap == FM_MAP_SIN) return FM_ERR_ARG;
     cp.label = labels[ic];
-    cp.ax.build(g.xmap, g.nint_x, 0.0, g.Rx, true);
-    cp.ay.build(g.ymap, g.nint_y, 0.0, g.Ry, true);
-    cp.az.build(g.zmap, g.nint_z, -1.0, 1.0, false);
+    cp.ax.build(g.xmap, g.nint_x, 0.0, g.Rx, true, g.basis);
+    cp.ay.build(g.ymap, g.nint_y, 0.0, g.Ry, true, g.basis);
+    cp.az.build(g.zmap, g.nint_z, -1.0, 1.0, false, g.basis);
+    cp.r = cp.ax.r;
+    if (ic > 0 && cp.r != c->comps[0].r) return FM_ERR_ARG;  // one basis for every solved component
     cp.nx = cp.ax.n; cp.ny = cp.ay.n; cp.nz = cp.az.n;
     cp.Rx = g.Rx; cp.Ry = g.Ry;
     cp.npts = (int64_t)cp.nz * cp.nx * cp.ny;
@@ -342,7 +458,47 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
   }
   const int J = S.J, nM = c->nM;
   int rc;
+  PhaseTimer tm;
+  // x decompositions of every component in one thread pool (they need only the x axis, unless the computed
+  // z eigenvalues replace l(l+1): then they follow the z decompositions below)
+  struct XD {
+    std::vector<double> Wx, Wxb;
+    std::vector<int> err;
+  };
+  std::vector<XD> xd(c->comps.size());
+  auto x_task = [&](const Comp& cp, int il, XD& d) {
+    const int nx = cp.nx, l = c->M0 + il;
+    const double ll1 = (c->opts.z_eigs == 1) ? -cp.Lz[il] : (double)l * (l + 1);
+    static thread_local std::vector<double> Sxd, D2xd;
+    Sxd = dense_of(cp.ax, cp.ax.S);
+    D2xd = dense_of(cp.ax, cp.ax.D2);
+    std::vector<double> A1((size_t)nx * nx);
+    for (int q = 0; q < nx; ++q) {
+      const double x = cp.ax.pts[q];
+      const double f = ll1 / (x * x) + coulomb(c, cp.label, x);
+      for (int j = 0; j < nx; ++j) A1[(size_t)q * nx + j] = -D2xd[(size_t)q * nx + j] + f * Sxd[(size_t)q * nx + j];
+    }
+    Comp& cw = const_cast<Comp&>(cp);
+    d.err[il] = fmh::decompose(nx, A1.data(), Sxd.data(), false, &d.Wxb[(size_t)il * nx * nx],
+                               &d.Wx[(size_t)il * nx * nx], &cw.Lx[(size_t)il * nx]);
+  };
+  const bool x_first = c->opts.z_eigs != 1;
+  if (x_first) {
+    std::vector<std::pair<int, int>> tasks;
+    for (size_t q = 0; q < c->comps.size(); ++q) {
+      Comp& cp = c->comps[q];
+      cp.nl = nM + cp.nz - 1;
+      xd[q].Wx.resize((size_t)cp.nl * cp.nx * cp.nx);
+      xd[q].Wxb.resize((size_t)cp.nl * cp.nx * cp.nx);
+      xd[q].err.assign(cp.nl, 0);
+      cp.Lx.assign((size_t)cp.nl * cp.nx, 0.0);
+      for (int il = 0; il < cp.nl; ++il) tasks.push_back({(int)q, il});
+    }
+    parallel_for((int)tasks.size(), [&](int t) { x_task(c->comps[tasks[t].first], tasks[t].second, xd[tasks[t].first]); });
+    tm.mark("x decompositions");
+  }
   for (auto& cp : c->comps) {
+    tm.mark("(previous component)");
     if ((rc = upload_axis(c, cp.ax, cp.dx))) return rc;
     if ((rc = upload_axis(c, cp.ay, cp.dy))) return rc;
     if ((rc = upload_axis(c, cp.az, cp.dz))) return rc;
@@ -350,30 +506,36 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
     // folded with the M'-dependent diagonal terms, and the coefficients of the z derivatives
     std::vector<double> W((size_t)nM * cp.npts), Atab((size_t)cp.npts), Btab((size_t)nM * cp.npts), iy2(cp.ny);
     for (int j = 0; j < cp.ny; ++j) iy2[j] = 1.0 / (cp.ay.pts[j] * cp.ay.pts[j]);
-    for (int k = 0; k < cp.nz; ++k)
-      for (int i = 0; i < cp.nx; ++i)
-        for (int j = 0; j < cp.ny; ++j) {
-          const double z = cp.az.pts[k], x = cp.ax.pts[i], y = cp.ay.pts[j];
-          double tot = coulomb(c, cp.label, x);
+    std::vector<int> bad_plane(cp.nz, 0);
+    const Comp* cq = &cp;
+    parallel_for(cp.nz, [&](int k) {  // one z plane per task
+      for (int i = 0; i < cq->nx; ++i)
+        for (int j = 0; j < cq->ny; ++j) {
+          const double z = cq->az.pts[k], x = cq->ax.pts[i], y = cq->ay.pts[j];
+          double tot = coulomb(c, cq->label, x);
           for (int beta = 1; beta <= 3; ++beta) {
-            if (beta == cp.label) continue;
+            if (beta == cq->label) continue;
             double cc, ss, xb, yb, zb;
-            rotation(m, beta, cp.label, &cc, &ss);
+            rotation(m, beta, cq->label, &cc, &ss);
             rotate(cc, ss, x, y, z, &xb, &yb, &zb);
             const double vc = coulomb(c, beta, xb);
             if (c->split.mode == FM_SPLIT_SCHRODINGER) tot += vc;
             else if (c->split.mode == FM_SPLIT_MERKURIEV) tot += (1.0 - chi(c->split, xb, yb)) * vc;
           }
-          if (!std::isfinite(tot)) return FM_ERR_NUMERIC;
-          const size_t pt = ((size_t)k * cp.nx + i) * cp.ny + j;
+          if (!std::isfinite(tot)) bad_plane[k] = 1;
+          const size_t pt = ((size_t)k * cq->nx + i) * cq->ny + j;
           const double q = 1.0 / (x * x) + iy2[j];
           Atab[pt] = q * (1.0 - z * z);
           for (int iM = 0; iM < nM; ++iM) {
             const int Mp = c->Mps[iM];
-            W[(size_t)iM * cp.npts + pt] = tot + q * Mp * (Mp + 1.0) + (J * (J + 1.0) - 2.0 * Mp * Mp) * iy2[j];
-            Btab[(size_t)iM * cp.npts + pt] = 2.0 * (Mp + 1) * z * q;
+            W[(size_t)iM * cq->npts + pt] = tot + q * Mp * (Mp + 1.0) + (J * (J + 1.0) - 2.0 * Mp * Mp) * iy2[j];
+            Btab[(size_t)iM * cq->npts + pt] = 2.0 * (Mp + 1) * z * q;
           }
         }
+    });
+    for (int b : bad_plane)
+      if (b) return FM_ERR_NUMERIC;
+    tm.mark("potential tables");
     if ((rc = upload(c, (void**)&cp.W, W.data(), W.size() * sizeof(double)))) return rc;
     if ((rc = upload(c, (void**)&cp.A, Atab.data(), Atab.size() * sizeof(double)))) return rc;
     if ((rc = upload(c, (void**)&cp.B, Btab.data(), Btab.size() * sizeof(double)))) return rc;
@@ -393,24 +555,28 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
     // coupling geometry (Eqs. r-form, s-rot): active points and, per source, taps and weights
     if (!cp.sources.empty()) {
       std::vector<int> act;
+      std::vector<char> on_xy((size_t)cp.nx * cp.ny, 1);  // chi depends on (x, y) only
+      if (c->split.mode == FM_SPLIT_MERKURIEV)
+        for (int i = 0; i < cp.nx; ++i)
+          for (int j = 0; j < cp.ny; ++j) on_xy[(size_t)i * cp.ny + j] = chi(c->split, cp.ax.pts[i], cp.ay.pts[j]) > c->split.vs_cut;
       for (int k = 0; k < cp.nz; ++k)
         for (int i = 0; i < cp.nx; ++i)
-          for (int j = 0; j < cp.ny; ++j) {
-            const double x = cp.ax.pts[i], y = cp.ay.pts[j];
-            bool on = true;
-            if (c->split.mode == FM_SPLIT_MERKURIEV) on = chi(c->split, x, y) > c->split.vs_cut;
-            if (on) act.push_back((int)(((int64_t)k * cp.nx + i) * cp.ny + j));
-          }
+          for (int j = 0; j < cp.ny; ++j)
+            if (on_xy[(size_t)i * cp.ny + j]) act.push_back((int)(((int64_t)k * cp.nx + i) * cp.ny + j));
       cp.n_act = (int)act.size();
       const int ns = (int)cp.sources.size(), na = cp.n_act;
       std::vector<int> base((size_t)ns * 3 * na);
-      std::vector<double> val((size_t)ns * 12 * na), wt((size_t)ns * nM * nM * na);
+      const int R = cp.r, R3 = 3 * cp.r;
+      std::vector<double> val((size_t)ns * R3 * na), wt((size_t)ns * nM * nM * na);
+      std::atomic<int> bad_w{0};
+      const int chunk = 4096, nchunks = (na + chunk - 1) / chunk;
       for (int s = 0; s < ns; ++s) {
         const Source& src = cp.sources[s];
         const Comp& sc = c->comps[src.src];
         double cc, ss;
         rotation(m, src.beta, cp.label, &cc, &ss);
-        for (int p = 0; p < na; ++p) {
+        parallel_for(nchunks, [&](int ch) {
+        for (int p = ch * chunk; p < std::min(na, (ch + 1) * chunk); ++p) {
           const int pt = act[p];
           const int k = pt / (cp.nx * cp.ny), rem = pt % (cp.nx * cp.ny), i = rem / cp.ny, j = rem % cp.ny;
           const double z = cp.az.pts[k], x = cp.ax.pts[i], y = cp.ay.pts[j];
@@ -418,12 +584,12 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
           rotate(cc, ss, x, y, z, &xb, &yb, &zb);
           const double w = w_angle(src.beta, cp.label, cc, ss, x, y, z, yb);
           int b3[3];
-          double v[12];
+          double v[3 * kMaxTaps];
           sc.az.eval(src.zsign * zb, 0, &b3[0], v);
-          sc.ax.eval(xb, 0, &b3[1], v + 4);
-          sc.ay.eval(yb, 0, &b3[2], v + 8);
+          sc.ax.eval(xb, 0, &b3[1], v + R);
+          sc.ay.eval(yb, 0, &b3[2], v + 2 * R);
           for (int d = 0; d < 3; ++d) base[((size_t)s * 3 + d) * na + p] = b3[d];
-          for (int t = 0; t < 12; ++t) val[((size_t)s * 12 + t) * na + p] = v[t];
+          for (int t = 0; t < R3; ++t) val[((size_t)s * R3 + t) * na + p] = v[t];
           // weight V^(s)_a * rho * rho^{M''} * angular(M', M'') * [p (-1)^{M''}]
           const double vc = coulomb(c, cp.label, x);
           const double vs = (c->split.mode == FM_SPLIT_MERKURIEV) ? chi(c->split, x, y) * vc : vc;
@@ -442,11 +608,14 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
               }
               double wv = vs * rho * std::pow(rho, Mpp) * ang;
               if (src.sym) wv *= S.exch_p * ((Mpp % 2 == 0) ? 1.0 : -1.0);
-              if (!std::isfinite(wv)) return FM_ERR_NUMERIC;
+              if (!std::isfinite(wv)) bad_w = 1;
               wt[(((size_t)s * nM * nM) + (size_t)iM * nM + jM) * na + p] = wv;
             }
         }
+        });
       }
+      if (bad_w) return FM_ERR_NUMERIC;
+      tm.mark("coupling geometry");
       if ((rc = upload(c, (void**)&cp.act_pt, act.data(), act.size() * sizeof(int)))) return rc;
       if ((rc = upload(c, (void**)&cp.cpl_base, base.data(), base.size() * sizeof(int)))) return rc;
       if ((rc = upload(c, (void**)&cp.cpl_val, val.data(), val.size() * sizeof(double)))) return rc;
@@ -456,6 +625,7 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       if ((rc = upload(c, (void**)&cp.f32.cw, wt32.data(), wt32.size() * sizeof(float)))) return rc;
     }
 
+    tm.mark("coupling upload");
     // z decompositions per M' (Eq. z-dec), columns normalised to g_l^{M'}(1)
     const int nz = cp.nz, nx = cp.nx;
     std::vector<double> Wz((size_t)nM * nz * nz), Wzb((size_t)nM * nz * nz);
@@ -466,16 +636,17 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       std::vector<double> A1((size_t)nz * nz, 0.0);
       for (int q = 0; q < nz; ++q) {
         const double z = cp.az.pts[q];
-        for (int t = 0; t < 4; ++t) {
+        const int R = cp.az.r;
+        for (int t = 0; t < R; ++t) {
           const int j = cp.az.base[q] + t;
           if (j < 0 || j >= nz) continue;
-          A1[(size_t)q * nz + j] += (1.0 - z * z) * cp.az.D2[q * 4 + t] - 2.0 * (Mp + 1) * z * cp.az.D1[q * 4 + t] -
-                                    Mp * (Mp + 1.0) * cp.az.S[q * 4 + t];
+          A1[(size_t)q * nz + j] += (1.0 - z * z) * cp.az.D2[q * R + t] - 2.0 * (Mp + 1) * z * cp.az.D1[q * R + t] -
+                                    Mp * (Mp + 1.0) * cp.az.S[q * R + t];
         }
       }
       double* Wb = &Wzb[(size_t)iM * nz * nz];
       double* Wr = &Wz[(size_t)iM * nz * nz];
-      const int top = 2 * cp.az.nint;  // value function of the node z = 1
+      const int top = cp.az.q * cp.az.nint;  // value function of the node z = 1
       std::vector<int> kind(nz, 0);
       const int e = fmh::decompose_pairs(nz, A1.data(), Szd.data(), top, Wb, Wr, &cp.Lz[(size_t)iM * nz], kind.data());
       if (e == -1) return FM_ERR_COMPLEX_SPECTRUM;
@@ -503,36 +674,55 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       if ((rc = upload(c, (void**)&cp.Wz32, f.data(), f.size() * 4))) return rc;
       if ((rc = upload(c, (void**)&cp.Wzb32, fb.data(), fb.size() * 4))) return rc;
     }
-    // x decompositions per l = M0 .. J + nz - 1
+    if (tc_requested(c) && nz <= 128) {  // tensor-core z stages: rows padded to 16-byte TMA strides
+      const bool bf = c->opts.mma == FM_MMA_BF16;
+      const int ld = bf ? (nz + 7) / 8 * 8 : (nz + 3) / 4 * 4;
+      cp.ldz = ld;
+      for (int which = 0; which < 2; ++which) {
+        const std::vector<double>& src = which ? Wz : Wzb;
+        std::vector<double> pad((size_t)nM * nz * ld, 0.0);
+        for (int iM = 0; iM < nM; ++iM)
+          for (int r = 0; r < nz; ++r)
+            for (int q = 0; q < nz; ++q) pad[((size_t)iM * nz + r) * ld + q] = src[((size_t)iM * nz + r) * nz + q];
+        void** dst = which ? &cp.Wz_tc : &cp.Wzb_tc;
+        if (bf) {
+          auto h = to_bf16(pad);
+          if ((rc = upload(c, dst, h.data(), h.size() * 2))) return rc;
+        } else {
+          auto h = to_f32(pad);
+          if ((rc = upload(c, dst, h.data(), h.size() * 4))) return rc;
+        }
+      }
+    }
+    // x decompositions per l = M0 .. J + nz - 1 (already done above unless computed z eigenvalues are kept)
+    XD& d = xd[&cp - c->comps.data()];
     cp.nl = nM + nz - 1;
     const int nl = cp.nl;
-    std::vector<double> Wx((size_t)nl * nx * nx), Wxb((size_t)nl * nx * nx);
-    cp.Lx.assign((size_t)nl * nx, 0.0);
-    const std::vector<double> Sxd = dense_of(cp.ax, cp.ax.S), D2xd = dense_of(cp.ax, cp.ax.D2);
-    std::vector<int> errs(nl, 0);
-    const Comp* cpp = &cp;
-    parallel_for(nl, [&](int il) {
-      const int l = c->M0 + il;
-      const double ll1 = (c->opts.z_eigs == 1) ? -cpp->Lz[il] : (double)l * (l + 1);
-      std::vector<double> A1((size_t)nx * nx);
-      for (int q = 0; q < nx; ++q) {
-        const double x = cpp->ax.pts[q];
-        const double f = ll1 / (x * x) + coulomb(c, cpp->label, x);
-        for (int j = 0; j < nx; ++j) A1[(size_t)q * nx + j] = -D2xd[(size_t)q * nx + j] + f * Sxd[(size_t)q * nx + j];
-      }
-      errs[il] = fmh::decompose(nx, A1.data(), Sxd.data(), false, &Wxb[(size_t)il * nx * nx], &Wx[(size_t)il * nx * nx],
-                                &cp.Lx[(size_t)il * nx]);
-    });
-    for (int e : errs) {
+    if (!x_first) {
+      d.Wx.resize((size_t)nl * nx * nx);
+      d.Wxb.resize((size_t)nl * nx * nx);
+      d.err.assign(nl, 0);
+      cp.Lx.assign((size_t)nl * nx, 0.0);
+      parallel_for(nl, [&](int il) { x_task(cp, il, d); });
+    }
+    for (int e : d.err) {
       if (e == -1) return FM_ERR_COMPLEX_SPECTRUM;
       if (e != 0) return FM_ERR_NUMERIC;
     }
+    const std::vector<double>& Wx = d.Wx;
+    const std::vector<double>& Wxb = d.Wxb;
+    tm.mark("z decompositions");
     if ((rc = upload(c, (void**)&cp.Wx, Wx.data(), Wx.size() * 8))) return rc;
     if ((rc = upload(c, (void**)&cp.Wxb, Wxb.data(), Wxb.size() * 8))) return rc;
     {
       auto f = to_f32(Wx), fb = to_f32(Wxb);
       if ((rc = upload(c, (void**)&cp.Wx32, f.data(), f.size() * 4))) return rc;
       if ((rc = upload(c, (void**)&cp.Wxb32, fb.data(), fb.size() * 4))) return rc;
+    }
+    if (tc_requested(c) && c->opts.mma == FM_MMA_BF16) {
+      auto h = to_bf16(Wx), hb = to_bf16(Wxb);
+      if ((rc = upload(c, (void**)&cp.Wx16, h.data(), h.size() * 2))) return rc;
+      if ((rc = upload(c, (void**)&cp.Wxb16, hb.data(), hb.size() * 2))) return rc;
     }
     // M' chains per l and the storage plan of the banded y factors
     cp.chain_lo.assign(nl, 0);
@@ -553,7 +743,8 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       }
       cp.chain_lo[il] = first;
       cp.chain_n[il] = cnt;
-      const int n = cnt * cp.ny, kl = (cnt == 1) ? 2 : 2 * cnt + 1;
+      const int n = cnt * cp.ny, kl = band_kl(cp.ay, cnt);
+      if (kl > kMaxBandKL) return FM_ERR_ARG;  // M' chain too long for the banded y solve of this basis
       cp.band_off[il] = bo;
       cp.lmul_off[il] = lo;
       cp.piv_off[il] = po;
@@ -588,7 +779,12 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       for (size_t q = 0; q < lx2.size(); ++q) lx2[q] = split2(cp.Lx[q]);
       if ((rc = upload(c, (void**)&cp.dLx2, lx2.data(), lx2.size() * sizeof(float2)))) return rc;
       if ((rc = dev_alloc(c, (void**)&cp.dLy2, (size_t)nl * ny * sizeof(float2)))) return rc;
+      if (tc_requested(c) && c->opts.mma == FM_MMA_BF16) {
+        if ((rc = dev_alloc(c, (void**)&cp.Wy16, (size_t)nl * ny * ny * 2))) return rc;
+        if ((rc = dev_alloc(c, (void**)&cp.Wyb16, (size_t)nl * ny * ny * 2))) return rc;
+      }
     }
+    tm.mark("factor uploads");
   }
   return FM_OK;
 }
@@ -609,13 +805,15 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
   for (size_t ic = 0; ic < labels.size(); ++ic) {
     const fm_grid& g = grids[n_grids == 1 ? 0 : ic];
     if (g.nint_x < 1 || g.nint_y < 1 || g.nint_z < 1 || !(g.Rx > 0) || !(g.Ry > 0)) return FM_ERR_ARG;
+    if (g.basis < 0 || g.basis > 1) return FM_ERR_ARG;
     Axis ax, ay, az;
-    ax.build(g.xmap, g.nint_x, 0.0, g.Rx, true);
-    ay.build(g.ymap, g.nint_y, 0.0, g.Ry, true);
-    az.build(g.zmap, g.nint_z, -1.0, 1.0, false);
+    ax.build(g.xmap, g.nint_x, 0.0, g.Rx, true, g.basis);
+    ay.build(g.ymap, g.nint_y, 0.0, g.Ry, true, g.basis);
+    az.build(g.zmap, g.nint_z, -1.0, 1.0, false, g.basis);
+    const double R = ax.r;
     const double nx = ax.n, ny = ay.n, nz = az.n, npts = nx * ny * nz;
     N += (int64_t)(npts * nM);
-    bytes += (nx + ny + nz) * (4 + 3 * 4 * 12 + 8) * 1.5;              // tap tables (float64 + float32)
+    bytes += (nx + ny + nz) * (4 + 3 * R * 12 + 8) * 1.5;              // tap tables (float64 + float32)
     bytes += (2.0 * nM + 1.0) * npts * 12.0 + ny * 12.0;                 // W, B per M'; A; iy2 (+ float32)
     if (split->mode != FM_SPLIT_SCHRODINGER) {                           // coupling geometry
       double act = 0.0;
@@ -624,7 +822,7 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
           if (split->mode != FM_SPLIT_MERKURIEV || chi(*split, ax.pts[i], ay.pts[j]) > split->vs_cut) act += 1.0;
       act *= nz;
       const double ns = 2.0;
-      bytes += act * (4.0 + ns * (12.0 + 12.0 * 12.0 + nM * nM * 12.0));
+      bytes += act * (4.0 + ns * (12.0 + 3.0 * R * 12.0 + nM * nM * 12.0));
     }
     const double nl = nM + nz - 1;
     bytes += 2.0 * nM * nz * nz * 12.0 + 2.0 * nl * nx * nx * 12.0;     // z and x decompositions
@@ -636,17 +834,21 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
         const int Mp = M0 + iM;
         if (Mp <= l && l <= Mp + (int)nz - 1) ++cnt;
       }
-      const double n = cnt * ny, kl = (cnt == 1) ? 2 : 2 * cnt + 1;
+      const double n = cnt * ny, kl = band_kl(ay, cnt);
       bo += n * (2 * kl + 1) * nx;
       lo += n * (kl + 1) * nx;
     }
     bytes += bo * 12.0 + lo * 12.0;
     if (nM == 1) bytes += 2.0 * nl * ny * ny * 12.0 + nl * (nx + ny) * 20.0;  // per-l y diagonalisation
+    if (o->precision != FM_PREC_FP64 && o->mma != FM_MMA_SIMT) {
+      bytes += 2.0 * nM * nz * (nz + 8) * 4.0;                           // padded z factors of the tensor cores
+      if (o->mma == FM_MMA_BF16) bytes += 2.0 * nl * (nx * nx + (nM == 1 ? ny * ny : 0.0)) * 2.0;
+    }
   }
   const double m = o->restart_m, ncv = o->ncv, n = (double)N;
   bytes += n * 8.0 * (5 + 2 + 3 + 16) + n * 4.0 * 2;                    // apply scratch, stage buffers, tuning
   bytes += n * 8.0 * ((m + 1) + std::max(m, ncv) + (ncv + 1));          // FGMRES and Arnoldi bases
-  if (o->precision == FM_PREC_MIXED) bytes += n * 4.0 * ((m + 1) + m + 7);
+  if (o->precision == FM_PREC_MIXED) bytes += n * 4.0 * ((m + 1) + m + 7 + 2.5);  // + y-interval sources
   bytes += (4.0 * 152 * 256 + 8192 + 4096) * 8.0;
   *out = (int64_t)bytes;
   return FM_OK;
@@ -660,6 +862,7 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
 int setup_shift(fm_ctx* c, double Estar) {
   const int J = c->sys.J;
   int rc;
+  PhaseTimer tm;
   for (auto& cp : c->comps) {
     const int nx = cp.nx, ny = cp.ny;
     std::vector<double> U((size_t)cp.band_total), L((size_t)cp.lmul_total);
@@ -671,7 +874,8 @@ int setup_shift(fm_ctx* c, double Estar) {
       const int l = c->M0 + il;
       const double ll1 = (c->opts.z_eigs == 1) ? -cpp->Lz[il] : (double)l * (l + 1);
       const int nc = cpp->chain_n[il], lo = cpp->chain_lo[il];
-      const int n = nc * ny, kl = (nc == 1) ? 2 : 2 * nc + 1, ku = kl, wb = 2 * kl + ku + 1, wu = kl + ku + 1;
+      const int n = nc * ny, kl = band_kl(cpp->ay, nc), ku = kl, wb = 2 * kl + ku + 1, wu = kl + ku + 1;
+      const int R = cpp->ay.r;
       std::vector<double> B((size_t)n * wb), Lm((size_t)n * kl);
       std::vector<int> piv(n);
       for (int ix = 0; ix < nx; ++ix) {
@@ -679,10 +883,10 @@ int setup_shift(fm_ctx* c, double Estar) {
         std::fill(B.begin(), B.end(), 0.0);
         for (int eta = 0; eta < ny; ++eta) {
           const double y = cpp->ay.pts[eta];
-          for (int t = 0; t < 4; ++t) {
+          for (int t = 0; t < R; ++t) {
             const int j = cpp->ay.base[eta] + t;
             if (j < 0 || j >= ny) continue;
-            const double s = cpp->ay.S[eta * 4 + t], d2 = cpp->ay.D2[eta * 4 + t];
+            const double s = cpp->ay.S[eta * R + t], d2 = cpp->ay.D2[eta * R + t];
             const double a1 = -d2 + (vh[eta] - Estar + lx) * s;
             const double a2 = s / (y * y);
             for (int cc = 0; cc < nc; ++cc) {
@@ -713,50 +917,87 @@ int setup_shift(fm_ctx* c, double Estar) {
     });
     for (int b : bad)
       if (b) return FM_ERR_NUMERIC;
+    tm.mark("banded y factors");
     FM_CUDA(cudaMemcpyAsync(cp.yU, U.data(), U.size() * 8, cudaMemcpyHostToDevice, c->stream));
     FM_CUDA(cudaMemcpyAsync(cp.yL, L.data(), L.size() * 8, cudaMemcpyHostToDevice, c->stream));
     std::vector<float> U32(U.begin(), U.end()), L32(L.begin(), L.end());
     FM_CUDA(cudaMemcpyAsync(cp.yU32, U32.data(), U32.size() * 4, cudaMemcpyHostToDevice, c->stream));
     FM_CUDA(cudaMemcpyAsync(cp.yL32, L32.data(), L32.size() * 4, cudaMemcpyHostToDevice, c->stream));
     FM_CUDA(cudaStreamSynchronize(c->stream));
+    tm.mark("banded y upload");
     cp.ydiag_ok = false;
-    if (c->nM == 1 && cp.Wy32) {
-      // (W-bar_y^l, W_y^l, Lambda_y^l) = D(A_l, S_y) with A_l = -D_y + (c_l / y^2 + V^ - E*) S_y; the n_M = 1
-      // block of l is I (x) A_l + Lambda_x^l (x) S_y, inverted line by line as W_y (Lambda_y + lambda_x)^{-1} W-bar_y
-      const std::vector<double> Syd = dense_of(cp.ay, cp.ay.S), D2yd = dense_of(cp.ay, cp.ay.D2);
-      std::vector<double> Wy((size_t)cp.nl * ny * ny), Wyb((size_t)cp.nl * ny * ny), Ly((size_t)cp.nl * ny);
-      std::vector<int> err(cp.nl, 0);
-      const int Mp = c->Mps[0];
-      parallel_for(cp.nl, [&](int il) {
-        const int l = c->M0 + il;
-        const double ll1 = (c->opts.z_eigs == 1) ? -cpp->Lz[il] : (double)l * (l + 1);
-        const double cl = J * (J + 1.0) - 2.0 * Mp * Mp + ll1;
-        std::vector<double> A((size_t)ny * ny);
-        for (int q = 0; q < ny; ++q) {
-          const double y = cpp->ay.pts[q];
-          const double f = cl / (y * y) + vh[q] - Estar;
-          for (int j = 0; j < ny; ++j) A[(size_t)q * ny + j] = -D2yd[(size_t)q * ny + j] + f * Syd[(size_t)q * ny + j];
-        }
-        err[il] = fmh::decompose(ny, A.data(), Syd.data(), false, &Wyb[(size_t)il * ny * ny], &Wy[(size_t)il * ny * ny],
-                                 &Ly[(size_t)il * ny]);
-      });
-      bool ok = true;
-      for (int e : err) ok = ok && (e == 0);
-      if (ok) {
-        std::vector<float> a32(Wy.begin(), Wy.end()), b32(Wyb.begin(), Wyb.end()), l32(Ly.begin(), Ly.end());
-        FM_CUDA(cudaMemcpyAsync(cp.Wy32, a32.data(), a32.size() * 4, cudaMemcpyHostToDevice, c->stream));
-        FM_CUDA(cudaMemcpyAsync(cp.Wyb32, b32.data(), b32.size() * 4, cudaMemcpyHostToDevice, c->stream));
-        FM_CUDA(cudaMemcpyAsync(cp.dLy32, l32.data(), l32.size() * 4, cudaMemcpyHostToDevice, c->stream));
-        FM_CUDA(cudaMemcpyAsync(cp.Wy64, Wy.data(), Wy.size() * 8, cudaMemcpyHostToDevice, c->stream));
-        FM_CUDA(cudaMemcpyAsync(cp.Wyb64, Wyb.data(), Wyb.size() * 8, cudaMemcpyHostToDevice, c->stream));
-        FM_CUDA(cudaMemcpyAsync(cp.dLy64, Ly.data(), Ly.size() * 8, cudaMemcpyHostToDevice, c->stream));
-        std::vector<float2> ly2(Ly.size());
-        for (size_t q = 0; q < ly2.size(); ++q) ly2[q] = split2(Ly[q]);
-        FM_CUDA(cudaMemcpyAsync(cp.dLy2, ly2.data(), ly2.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
-        FM_CUDA(cudaStreamSynchronize(c->stream));
-        cp.ydiag_ok = true;
-      }
+  }
+  // n_M = 1: (W-bar_y^l, W_y^l, Lambda_y^l) = D(A_l, S_y) with A_l = -D_y + (c_l / y^2 + V^ - E*) S_y; the block of
+  // l is I (x) A_l + Lambda_x^l (x) S_y, inverted line by line as W_y (Lambda_y + lambda_x)^{-1} W-bar_y.  The
+  // decompositions of every component run in one thread pool.
+  if (c->nM == 1) {
+    struct YD {
+      Comp* cp;
+      std::vector<double> Syd, D2yd, vh, Wy, Wyb, Ly;
+      std::vector<int> err;
+    };
+    std::vector<YD> yd;
+    for (auto& cp : c->comps) {
+      if (!cp.Wy32) continue;
+      YD d;
+      d.cp = &cp;
+      const int ny = cp.ny;
+      d.Syd = dense_of(cp.ay, cp.ay.S);
+      d.D2yd = dense_of(cp.ay, cp.ay.D2);
+      d.vh.resize(ny);
+      for (int j = 0; j < ny; ++j) d.vh[j] = vhat(c, cp.label, cp.ay.pts[j], cp.Ry);
+      d.Wy.resize((size_t)cp.nl * ny * ny);
+      d.Wyb.resize((size_t)cp.nl * ny * ny);
+      d.Ly.resize((size_t)cp.nl * ny);
+      d.err.assign(cp.nl, 0);
+      yd.push_back(std::move(d));
     }
+    std::vector<std::pair<int, int>> tasks;
+    for (int q = 0; q < (int)yd.size(); ++q)
+      for (int il = 0; il < yd[q].cp->nl; ++il) tasks.push_back({q, il});
+    const int Mp = c->Mps[0];
+    parallel_for((int)tasks.size(), [&](int ti) {
+      YD& d = yd[tasks[ti].first];
+      const Comp* cpp = d.cp;
+      const int il = tasks[ti].second, ny = cpp->ny, l = c->M0 + il;
+      const double ll1 = (c->opts.z_eigs == 1) ? -cpp->Lz[il] : (double)l * (l + 1);
+      const double cl = J * (J + 1.0) - 2.0 * Mp * Mp + ll1;
+      std::vector<double> A((size_t)ny * ny);
+      for (int q = 0; q < ny; ++q) {
+        const double y = cpp->ay.pts[q];
+        const double f = cl / (y * y) + d.vh[q] - Estar;
+        for (int j = 0; j < ny; ++j) A[(size_t)q * ny + j] = -d.D2yd[(size_t)q * ny + j] + f * d.Syd[(size_t)q * ny + j];
+      }
+      d.err[il] = fmh::decompose(ny, A.data(), d.Syd.data(), false, &d.Wyb[(size_t)il * ny * ny],
+                                 &d.Wy[(size_t)il * ny * ny], &d.Ly[(size_t)il * ny]);
+    });
+    tm.mark("y diagonalisations");
+    for (YD& d : yd) {
+      Comp& cp = *d.cp;
+      bool ok = true;
+      for (int e : d.err) ok = ok && (e == 0);
+      if (!ok) continue;  // complex or singular: the banded y solves serve this component
+      std::vector<float> a32(d.Wy.begin(), d.Wy.end()), b32(d.Wyb.begin(), d.Wyb.end()), l32(d.Ly.begin(), d.Ly.end());
+      FM_CUDA(cudaMemcpyAsync(cp.Wy32, a32.data(), a32.size() * 4, cudaMemcpyHostToDevice, c->stream));
+      FM_CUDA(cudaMemcpyAsync(cp.Wyb32, b32.data(), b32.size() * 4, cudaMemcpyHostToDevice, c->stream));
+      FM_CUDA(cudaMemcpyAsync(cp.dLy32, l32.data(), l32.size() * 4, cudaMemcpyHostToDevice, c->stream));
+      FM_CUDA(cudaMemcpyAsync(cp.Wy64, d.Wy.data(), d.Wy.size() * 8, cudaMemcpyHostToDevice, c->stream));
+      FM_CUDA(cudaMemcpyAsync(cp.Wyb64, d.Wyb.data(), d.Wyb.size() * 8, cudaMemcpyHostToDevice, c->stream));
+      FM_CUDA(cudaMemcpyAsync(cp.dLy64, d.Ly.data(), d.Ly.size() * 8, cudaMemcpyHostToDevice, c->stream));
+      std::vector<float2> ly2(d.Ly.size());
+      for (size_t q = 0; q < ly2.size(); ++q) ly2[q] = split2(d.Ly[q]);
+      FM_CUDA(cudaMemcpyAsync(cp.dLy2, ly2.data(), ly2.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+      std::vector<uint16_t> a16, b16;
+      if (cp.Wy16) {
+        a16 = to_bf16(d.Wy);
+        b16 = to_bf16(d.Wyb);
+        FM_CUDA(cudaMemcpyAsync(cp.Wy16, a16.data(), a16.size() * 2, cudaMemcpyHostToDevice, c->stream));
+        FM_CUDA(cudaMemcpyAsync(cp.Wyb16, b16.data(), b16.size() * 2, cudaMemcpyHostToDevice, c->stream));
+      }
+      FM_CUDA(cudaStreamSynchronize(c->stream));
+      cp.ydiag_ok = true;
+    }
+    tm.mark("y diagonalisation upload");
   }
   c->Estar = Estar;
   c->have_shift = true;
@@ -765,3 +1006,24 @@ int setup_shift(fm_ctx* c, double Estar) {
 }
 
 }  // namespace fmi
+
+extern "C" int fm_host_axis(int map, int nint, double a, double b, int dirichlet, int basis, int* n, int* r,
+                            double* pts, int* base, double* S, double* D1, double* D2) {
+  if (nint < 1 || !(b > a) || basis < 0 || basis > 1 || map < 0 || map > 2 || !n || !r || !pts || !base || !S || !D1 ||
+      !D2)
+    return FM_ERR_ARG;
+  fmi::Axis A;
+  A.build(map, nint, a, b, dirichlet != 0, basis);
+  *n = A.n;
+  *r = A.r;
+  for (int e = 0; e < A.n; ++e) {
+    pts[e] = A.pts[e];
+    base[e] = A.base[e];
+    for (int t = 0; t < A.r; ++t) {
+      S[e * A.r + t] = A.S[e * A.r + t];
+      D1[e * A.r + t] = A.D1[e * A.r + t];
+      D2[e * A.r + t] = A.D2[e * A.r + t];
+    }
+  }
+  return FM_OK;
+}

@@ -27,6 +27,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <type_traits>
 
@@ -497,7 +498,8 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 // (K), converted from the input type while it is written into shared memory, D in tensor memory
 // (128 lanes l x 128 columns p).  Persistent CTAs walk the (M', point tile) list.
 //   OUT_JI (forward):  in x[M'][k][i][j] -> out t[slab][j][i]; tiles of 32 i x 4 j, B row = jj * 32 + ii
-//   !OUT_JI (inverse): in u[slab][j][i]  -> out y[M'][k][i][j]; tiles of 8 i x 16 j, B row = ii * 16 + jj
+//   !OUT_JI (inverse): in u[slab][j][i] (IN_JI) or t[slab][i][j] -> out y[M'][k][i][j]; tiles of 8 i x 16 j,
+//                      B row = ii * 16 + jj
 // (slab = M' * n_z + l).  Each thread of the epilogue owns one output plane l and writes runs of 32
 // (forward) or 16 (inverse) consecutive elements of it.
 // ---------------------------------------------------------------------------
@@ -512,8 +514,9 @@ struct TcZArgs {
   int* err;
 };
 
-template <typename TI, typename Op, typename TO, bool OUT_JI>
+template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI>
 __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMap tmW, const TcZArgs a) {
+  static_assert(!(OUT_JI && IN_JI), "the forward stage reads x[M'][k][i][j]");
   using TB = typename Op::T;
   constexpr int TI_ = OUT_JI ? 32 : 8, TJ_ = OUT_JI ? 4 : 16;
   constexpr int kTile = 128 * 128;  // bytes of one K block (128 rows x 128 bytes)
@@ -548,8 +551,8 @@ __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMa
   int cur_iM = -1, a_loads = 0;
   uint32_t a_phase = 0, m_phase = 0;
   // thread -> point of the tile for coalesced loads (the contiguous index runs across lanes)
-  const int ii = OUT_JI ? tid / TJ_ : tid % TI_;
-  const int jj = OUT_JI ? tid % TJ_ : tid / TI_;
+  const int ii = IN_JI ? tid % TI_ : tid / TJ_;
+  const int jj = IN_JI ? tid / TI_ : tid % TJ_;
   const int prow = OUT_JI ? jj * TI_ + ii : ii * TJ_ + jj;
   for (int q = blockIdx.x; q < ntiles * a.nM; q += gridDim.x) {
     const int iM = q / ntiles, t = q - iM * ntiles;
@@ -567,8 +570,8 @@ __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMa
     {
       const int i = i0 + ii, j = j0 + jj;
       const bool ok = i < a.nx && j < a.ny;
-      const int64_t src = OUT_JI ? a.off + ((int64_t)iM * a.nz * a.nx + i) * a.ny + j
-                                 : a.off + ((int64_t)iM * a.nz * a.ny + j) * a.nx + i;
+      const int64_t src = IN_JI ? a.off + ((int64_t)iM * a.nz * a.ny + j) * a.nx + i
+                                : a.off + ((int64_t)iM * a.nz * a.nx + i) * a.ny + j;
       for (int k0 = 0; k0 < kpad; k0 += 8) {
         float v[8];
 #pragma unroll
@@ -952,7 +955,39 @@ bool encode3(CUtensorMap* m, const float* ptr, int d0, int d1, int d2, int box1)
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 3D map of any element type [d2][d1][d0] (d0 contiguous), box box0 x box1 x 1, 128-byte swizzle, zero fill
+bool encode3t(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, int esize, int d0, int d1, int d2, int box0,
+              int box1) {
+  auto fn = encode_fn();
+  if (!fn || !ptr) return false;
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15u) != 0 || ((int64_t)d0 * esize) % 16 != 0 || box0 * esize > 128 ||
+      box1 < 1 || box1 > 256)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+  const cuuint64_t strides[2] = {(cuuint64_t)d0 * esize, (cuuint64_t)d0 * d1 * esize};
+  const cuuint32_t box[3] = {(cuuint32_t)box0, (cuuint32_t)box1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 int round16(int n) { return (n + 15) / 16 * 16; }
+
+// shared memory of the fused x / y kernel: B tile, A ring, the slab's lambda_x pairs, barriers
+size_t fused_smem(int nx, int ny, int row_elems, int stages) {
+  const int n = std::max(nx, ny);
+  const size_t rowsB = (size_t)round16(n), kbB = (size_t)((n + row_elems - 1) / row_elems);
+  return 1024 + kbB * rowsB * 128 + (size_t)stages * 16384 + 256 * 8 + 256;
+}
+
+int fused_stages(int nx, int ny, int row_elems) {
+  for (int st = 4; st >= 2; --st)
+    if (fused_smem(nx, ny, row_elems, st) <= 232448 - 1024) return st;
+  return 0;
+}
+
+size_t tcz_smem(int kblocks) { return 1024 + (size_t)2 * kblocks * 16384 + 64; }
 
 int tmem_cols(int nb) {
   int c = 32;
@@ -975,18 +1010,26 @@ bool tc_component_ok(const Comp& cp) {
   return cp.nx % 4 == 0 && cp.ny % 4 == 0 && cp.nx <= 256 && cp.ny <= 256 && cp.nx >= 16 && cp.ny >= 16;
 }
 
+static bool bf16_component_ok(const Comp& cp) {
+  return tc_component_ok(cp) && cp.nx % 8 == 0 && cp.ny % 8 == 0 && cp.nz <= 128;
+}
+
 int tc_setup(fm_ctx* c) {
   c->tc_active = false;
+  c->bf16 = false;
   if (c->opts.precision == FM_PREC_FP64 || c->opts.mma == FM_MMA_SIMT) return FM_OK;
+  const bool want_bf16 = c->opts.mma == FM_MMA_BF16;
   bool all = true;
-  for (auto& cp : c->comps) all = all && tc_component_ok(cp);
-  if (!all) return c->opts.mma == FM_MMA_TF32 ? FM_ERR_ARG : FM_OK;
-  if (!encode_fn()) return c->opts.mma == FM_MMA_TF32 ? FM_ERR_CUDA : FM_OK;
+  for (auto& cp : c->comps) all = all && (want_bf16 ? bf16_component_ok(cp) : tc_component_ok(cp));
+  if (!all) return (c->opts.mma == FM_MMA_TF32 || want_bf16) ? FM_ERR_ARG : FM_OK;
+  if (!encode_fn()) return c->opts.mma == FM_MMA_AUTO ? FM_OK : FM_ERR_CUDA;
   if (!c->tc_err) {
     int rc = dev_alloc(c, (void**)&c->tc_err, 256);
     if (rc) return rc;
     FM_CUDA(cudaMemsetAsync(c->tc_err, 0, 256, c->stream));
   }
+  const CUtensorMapDataType dt = want_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const int es = want_bf16 ? 2 : 4, E = 128 / es;
   for (auto& cp : c->comps) {
     const int nx = cp.nx, ny = cp.ny, ns = c->nM * cp.nz, nl = cp.nl;
     float* t = c->t32 + cp.off;
@@ -1000,13 +1043,59 @@ int tc_setup(fm_ctx* c) {
            && encode3(&cp.tm[6], cp.Wyb32, ny, ny, nl, round16(ny)) && encode3(&cp.tm[7], cp.Wy32, ny, ny, nl, round16(ny));
     }
     if (!ok) return FM_ERR_CUDA;
+    // z stages on the tensor cores (W_z with padded rows)
+    cp.tcz = cp.Wz_tc && cp.Wzb_tc && cp.nz <= 128;
+    if (cp.tcz) {
+      ok = encode3t(&cp.tmz[0], cp.Wzb_tc, dt, es, cp.ldz, cp.nz, c->nM, E, 128) &&
+           encode3t(&cp.tmz[1], cp.Wz_tc, dt, es, cp.ldz, cp.nz, c->nM, E, 128);
+      if (!ok) return FM_ERR_CUDA;
+    }
+    // n_M = 1: the fused x / y chain (slab in t[slab][j][i], out u[slab][j][i])
+    cp.fused = false;
+    if (c->nM == 1 && cp.Wy32 && cp.tcz && fused_stages(nx, ny, E) > 0) {
+      const void* tin = want_bf16 ? (const void*)(reinterpret_cast<const uint16_t*>(c->t32) + cp.off) : (const void*)t;
+      const void* w[4] = {want_bf16 ? (const void*)cp.Wxb16 : (const void*)cp.Wxb32,
+                          want_bf16 ? (const void*)cp.Wyb16 : (const void*)cp.Wyb32,
+                          want_bf16 ? (const void*)cp.Wy16 : (const void*)cp.Wy32,
+                          want_bf16 ? (const void*)cp.Wx16 : (const void*)cp.Wx32};
+      const int wn[4] = {nx, ny, ny, nx};
+      ok = encode3t(&cp.tmf[0], tin, dt, es, nx, ny, ns, E, round16(ny));
+      for (int g = 0; g < 4 && ok; ++g) ok = encode3t(&cp.tmf[1 + g], w[g], dt, es, wn[g], wn[g], nl, E, 128);
+      if (!ok) return FM_ERR_CUDA;
+      cp.fused = true;
+    }
   }
+  c->bf16 = want_bf16;
   c->tc_active = true;
   return FM_OK;
 }
 
+template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI>
+static cudaError_t tcz_attr() {
+  return cudaFuncSetAttribute(k_tc_z<TI, Op, TO, OUT_JI, IN_JI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 int tc_kernels_init() {
   FM_CUDA(cudaFuncSetAttribute(k_tc_mix, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_tc_fused_xy<OpTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_tc_fused_xy<OpBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  // z forward: x (float64 / float32) -> t (float32, or BF16 ahead of the fused BF16 chain)
+  FM_CUDA((tcz_attr<double, OpTF32, float, true, false>()));
+  FM_CUDA((tcz_attr<float, OpTF32, float, true, false>()));
+  FM_CUDA((tcz_attr<double, OpBF16, float, true, false>()));
+  FM_CUDA((tcz_attr<float, OpBF16, float, true, false>()));
+  FM_CUDA((tcz_attr<double, OpBF16, uint16_t, true, false>()));
+  FM_CUDA((tcz_attr<float, OpBF16, uint16_t, true, false>()));
+  // z inverse: u[slab][j][i] of the fused chain or t[slab][i][j] of the unfused one -> y
+  FM_CUDA((tcz_attr<float, OpTF32, double, false, true>()));
+  FM_CUDA((tcz_attr<float, OpTF32, float, false, true>()));
+  FM_CUDA((tcz_attr<float, OpTF32, double, false, false>()));
+  FM_CUDA((tcz_attr<float, OpTF32, float, false, false>()));
+  FM_CUDA((tcz_attr<float, OpBF16, double, false, false>()));
+  FM_CUDA((tcz_attr<float, OpBF16, float, false, false>()));
+  FM_CUDA((tcz_attr<uint16_t, OpBF16, double, false, true>()));
+  FM_CUDA((tcz_attr<uint16_t, OpBF16, float, false, true>()));
+  FM_CUDA(cudaFuncSetAttribute(k_zmix_rb<float, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix_rb<double, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix_rb<float, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix_rb<float, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
@@ -1066,41 +1155,157 @@ int zstage(fm_ctx* c, const Comp& cp, const float* W, const TI* in, TO* out) {
 
 }  // namespace
 
-// Front half of y = P^{-1} x through the tensor-core chain (float32 stage buffers t32 / u32):
-// z forward, x forward and, for the per-l diagonalised y stage, both y products.  The result is
-// left in u[slab][j][i]; the banded y solves (when not diagonalised) then work in place there.
+// z stages on the tensor cores.  Forward: x -> t[slab][j][i] (BF16 storage when 'to_bf16', ahead of the fused
+// BF16 chain).  Inverse: u[slab][j][i] (fused chain, 'in_ji') or t[slab][i][j] (unfused) -> y.
+template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI>
+static int tcz_launch(fm_ctx* c, const Comp& cp, const CUtensorMap& tm, const void* in, void* out) {
+  TcZArgs a;
+  a.in = in;
+  a.out = out;
+  a.nz = cp.nz;
+  a.nx = cp.nx;
+  a.ny = cp.ny;
+  a.nM = c->nM;
+  a.off = cp.off;
+  const int TI_ = OUT_JI ? 32 : 8, TJ_ = OUT_JI ? 4 : 16;
+  a.tiles_i = (cp.nx + TI_ - 1) / TI_;
+  a.tiles_j = (cp.ny + TJ_ - 1) / TJ_;
+  a.kblocks = (cp.nz + Op::kRow - 1) / Op::kRow;
+  a.ksteps = (cp.nz + Op::kStep - 1) / Op::kStep;
+  a.err = c->tc_err;
+  const size_t smem = tcz_smem(a.kblocks);
+  const int per_sm = std::max(1, std::min(4, (int)(232448 / (smem + 1024))));
+  const int tiles = a.tiles_i * a.tiles_j * c->nM;
+  const int grid = std::max(1, std::min(tiles, 152 * per_sm));
+  const double nun = (double)cp.nx * cp.ny * cp.nz * c->nM;
+  const int tk_ = prof_begin(c, FM_KERNEL_ZMIX);
+  k_tc_z<TI, Op, TO, OUT_JI, IN_JI><<<grid, 128, smem, c->stream>>>(tm, a);
+  prof_end(c, tk_, 2.0 * cp.nz * nun, nun * (double)(sizeof(TI) + sizeof(TO)));
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+bool tc_uses_ydiag(const fm_ctx* c, const Comp& cp) {
+  return cp.ydiag_ok && (c->opts.y_solver == 2 || c->opts.y_solver == 0);
+}
+
+// the fused x / y chain of every component in 'comps' (one launch): t[slab][j][i] -> u[slab][j][i]
+template <typename Op>
+static int fused_launch(fm_ctx* c, const std::vector<Comp*>& comps) {
+  using TB = typename Op::T;
+  if (comps.empty()) return FM_OK;
+  if (comps.size() > 3) return FM_ERR_ARG;
+  FusedArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.ncomp = (int)comps.size();
+  a.total = 0;
+  int nmax = 16, stages = 4;
+  double fl = 0.0, by = 0.0;
+  for (size_t q = 0; q < comps.size(); ++q) {
+    const Comp& cp = *comps[q];
+    FusedComp& f = a.c[q];
+    f.tm_in = cp.tmf[0];
+    for (int g = 0; g < 4; ++g) f.tm_w[g] = cp.tmf[1 + g];
+    f.out = reinterpret_cast<TB*>(c->u32) + cp.off;
+    f.dLx2 = cp.dLx2;
+    f.dLy2 = cp.dLy2;
+    f.nx = cp.nx;
+    f.ny = cp.ny;
+    f.ns = cp.nz;  // n_M = 1: one slab per z mode
+    a.total += f.ns;
+    nmax = std::max(nmax, std::max(cp.nx, cp.ny));
+    stages = std::min(stages, fused_stages(cp.nx, cp.ny, Op::kRow));
+    const double nx = cp.nx, ny = cp.ny, es = (double)sizeof(TB);
+    fl += f.ns * 4.0 * nx * ny * (nx + ny);
+    by += f.ns * (2.0 * es * nx * ny + 2.0 * es * (nx * nx + ny * ny) + 8.0 * (nx + ny));
+  }
+  if (stages < 2) return FM_ERR_ARG;
+  a.rowsB = round16(nmax);
+  a.kbB = (nmax + Op::kRow - 1) / Op::kRow;
+  a.stages = stages;
+  a.ncols = nmax > 128 ? 512 : 256;
+  a.err = c->tc_err;
+  const size_t smem = 1024 + (size_t)a.kbB * a.rowsB * 128 + (size_t)stages * 16384 + 256 * 8 + 256;
+  const int grid = std::min(a.total, 152);
+  const int tk_ = prof_begin(c, FM_KERNEL_XMIX);
+  k_tc_fused_xy<Op><<<grid, kFusedThreads, smem, c->stream>>>(a);
+  prof_end(c, tk_, fl, by);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
 template <typename TIO>
-int precond_tc_front(fm_ctx* c, Comp& cp, const TIO* x, bool ydiag) {
+static int zfwd(fm_ctx* c, Comp& cp, const TIO* x, bool to_bf16) {
+  if (!cp.tcz) return zstage<TIO, float, true>(c, cp, cp.Wzb32, x, c->t32);  // t[slab][j][i]
+  if (!c->bf16) return tcz_launch<TIO, OpTF32, float, true, false>(c, cp, cp.tmz[0], x, c->t32);
+  if (to_bf16) return tcz_launch<TIO, OpBF16, uint16_t, true, false>(c, cp, cp.tmz[0], x, c->t32);
+  return tcz_launch<TIO, OpBF16, float, true, false>(c, cp, cp.tmz[0], x, c->t32);
+}
+
+// Front half of y = P^{-1} x through the tensor-core chain, all components: z forward, then the x (and, for
+// the n_M = 1 y diagonalisation, y) stages -- fused per slab where eligible.  Results: u[slab][j][i] for the
+// fused components and for those left to the banded y solves (returned in 'banded', which work in place
+// there); t[slab][j][i] ... see the layouts at the top of this file for the unfused diagonalised form.
+template <typename TIO>
+int precond_tc_front(fm_ctx* c, const TIO* x, std::vector<Comp*>* banded) {
   int rc;
-  float* t = c->t32 + cp.off;
-  float* u = c->u32 + cp.off;
-  const int nx = cp.nx, ny = cp.ny;
-  if ((rc = zstage<TIO, float, true>(c, cp, cp.Wzb32, x, c->t32))) return rc;  // t[slab][j][i]
-  // x forward: rows j, K = i -> u[slab][i][j] (ydiag) or u[slab][j][i] (banded y)
-  if ((rc = tc_stage(c, cp, cp.tm[0], cp.tm[2], ny, nx, nx, ydiag, u, nullptr, nullptr, FM_KERNEL_XMIX))) return rc;
-  if (ydiag) {
-    // y forward with the diagonal: rows i, K = j -> t[slab][i][j] / (lambda_x,i + lambda_y,j)
-    if ((rc = tc_stage(c, cp, cp.tm[4], cp.tm[6], nx, ny, ny, false, t, cp.dLx2, cp.dLy2, FM_KERNEL_YSOLVE))) return rc;
-    // y inverse: rows i, K = j -> u[slab][j][i]
-    if ((rc = tc_stage(c, cp, cp.tm[5], cp.tm[7], nx, ny, ny, true, u, nullptr, nullptr, FM_KERNEL_YSOLVE))) return rc;
+  std::vector<Comp*> fused;
+  for (auto& cp : c->comps) {
+    const bool ydiag = tc_uses_ydiag(c, cp), fz = ydiag && cp.fused;
+    if (!ydiag) banded->push_back(&cp);
+    if (fz) fused.push_back(&cp);
+    if ((rc = zfwd<TIO>(c, cp, x, fz && c->bf16))) return rc;
+  }
+  if (c->bf16) rc = fused_launch<OpBF16>(c, fused);
+  else rc = fused_launch<OpTF32>(c, fused);
+  if (rc) return rc;
+  for (auto& cp : c->comps) {
+    const bool ydiag = tc_uses_ydiag(c, cp);
+    if (ydiag && cp.fused) continue;
+    float* t = c->t32 + cp.off;
+    float* u = c->u32 + cp.off;
+    const int nx = cp.nx, ny = cp.ny;
+    // x forward: rows j, K = i -> u[slab][i][j] (ydiag) or u[slab][j][i] (banded y)
+    if ((rc = tc_stage(c, cp, cp.tm[0], cp.tm[2], ny, nx, nx, ydiag, u, nullptr, nullptr, FM_KERNEL_XMIX))) return rc;
+    if (ydiag) {
+      // y forward with the diagonal: rows i, K = j -> t[slab][i][j] / (lambda_x,i + lambda_y,j)
+      if ((rc = tc_stage(c, cp, cp.tm[4], cp.tm[6], nx, ny, ny, false, t, cp.dLx2, cp.dLy2, FM_KERNEL_YSOLVE))) return rc;
+      // y inverse: rows i, K = j -> u[slab][j][i]
+      if ((rc = tc_stage(c, cp, cp.tm[5], cp.tm[7], nx, ny, ny, true, u, nullptr, nullptr, FM_KERNEL_YSOLVE))) return rc;
+    }
   }
   return FM_OK;
 }
 
-// Back half: x inverse (rows j, K = i -> t[slab][i][j]) and z inverse into y.
+// Back half: x inverse (rows j, K = i -> t[slab][i][j]) of the unfused components and the z inverse of all.
 template <typename TIO>
-int precond_tc_back(fm_ctx* c, Comp& cp, TIO* y) {
+int precond_tc_back(fm_ctx* c, TIO* y) {
   int rc;
-  float* t = c->t32 + cp.off;
-  const int nx = cp.nx, ny = cp.ny;
-  if ((rc = tc_stage(c, cp, cp.tm[1], cp.tm[3], ny, nx, nx, true, t, nullptr, nullptr, FM_KERNEL_XMIX))) return rc;
-  return zstage<float, TIO, false>(c, cp, cp.Wz32, c->t32, y);
+  for (auto& cp : c->comps) {
+    const bool fz = tc_uses_ydiag(c, cp) && cp.fused;
+    const int nx = cp.nx, ny = cp.ny;
+    if (fz) {  // u[slab][j][i] from the fused chain
+      if (!c->bf16) rc = tcz_launch<float, OpTF32, TIO, false, true>(c, cp, cp.tmz[1], c->u32, y);
+      else rc = tcz_launch<uint16_t, OpBF16, TIO, false, true>(c, cp, cp.tmz[1], c->u32, y);
+      if (rc) return rc;
+      continue;
+    }
+    float* t = c->t32 + cp.off;
+    if ((rc = tc_stage(c, cp, cp.tm[1], cp.tm[3], ny, nx, nx, true, t, nullptr, nullptr, FM_KERNEL_XMIX))) return rc;
+    if (!cp.tcz) rc = zstage<float, TIO, false>(c, cp, cp.Wz32, c->t32, y);
+    else if (!c->bf16) rc = tcz_launch<float, OpTF32, TIO, false, false>(c, cp, cp.tmz[1], c->t32, y);
+    else rc = tcz_launch<float, OpBF16, TIO, false, false>(c, cp, cp.tmz[1], c->t32, y);
+    if (rc) return rc;
+  }
+  return FM_OK;
 }
 
-template int precond_tc_front<double>(fm_ctx*, Comp&, const double*, bool);
-template int precond_tc_front<float>(fm_ctx*, Comp&, const float*, bool);
-template int precond_tc_back<double>(fm_ctx*, Comp&, double*);
-template int precond_tc_back<float>(fm_ctx*, Comp&, float*);
+template int precond_tc_front<double>(fm_ctx*, const double*, std::vector<Comp*>*);
+template int precond_tc_front<float>(fm_ctx*, const float*, std::vector<Comp*>*);
+template int precond_tc_back<double>(fm_ctx*, double*);
+template int precond_tc_back<float>(fm_ctx*, float*);
 
 int tc_check(fm_ctx* c) {
   if (!c->tc_active || !c->tc_err) return FM_OK;

@@ -13,6 +13,8 @@ pytestmark = pytest.mark.gpu
 # the conditioning of the 1D eigenvector bases stay well inside this bound (a layout or index
 # error gives O(1)).
 TF32_REL = 1e-2
+# BF16 keeps 7 (unit roundoff 2^-8, eight times TF32's): the same chain with float32 accumulation
+BF16_REL = 8e-2
 
 CASES = {
     "he_l0_rows132": dict(nint=(66, 34, 3), R=(20.0, 17.0)),      # y stage: 2 row tiles (128 + 4)
@@ -20,6 +22,15 @@ CASES = {
     "he_l1_banded": dict(J=1, nint=(10, 12, 4), R=(20.0, 17.0)),  # n_M = 2: banded y solves between
     "psm_l2": dict(J=2, nint=(8, 10, 4), R=(30.0, 27.0), mass=(1.0, 1.0, 1.0), charge=(-1.0, -1.0, 1.0),
                    shift=-0.27),
+    # n_x = n_y = 256: the float32 slab is too large for the fused per-slab kernel (unfused TF32 chain)
+    "he_l0_wide": dict(nint=(128, 128, 2), R=(20.0, 17.0)),
+}
+# multiples of 8 in n_x and n_y, as the BF16 operands need
+BF16_CASES = {
+    "he_l0_rows136": dict(nint=(68, 36, 3), R=(20.0, 17.0)),      # fused chain, 2 row tiles in x
+    "he_l0_rows136y": dict(nint=(36, 68, 3), R=(20.0, 17.0)),     # fused chain, 2 row tiles in y
+    "he_l0_wide": dict(nint=(128, 128, 2), R=(20.0, 17.0)),       # n = 256: fused in BF16
+    "he_l1_banded": dict(J=1, nint=(12, 8, 4), R=(20.0, 17.0)),   # n_M = 2: banded y, TF32 x stages
 }
 
 
@@ -54,6 +65,8 @@ def test_tc_eligibility(pkg):
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("y_solver", [0, 1])
 def test_tc_precond_close_to_fp64(pkg, name, y_solver):
+    """TF32 tensor-core chain (z stages, fused or unfused x / y stages, banded y solves) against the float64
+    chain, which is itself equal to the paper's literal form (test_gpu_parity)."""
     wl = _wl(name)
     E = wl["shift"] + 0.011
     ref_ctx = pkg.Context(wl, precision=0, y_solver=y_solver)
@@ -133,5 +146,72 @@ def test_tc_eigs_match_oracle(pkg, name, k, precision):
     ctx = pkg.Context(wl, restart_m=40, precision=precision, mma=2)
     ev, info = ctx.fm_eigs(shift, k)
     assert info["converged"] == 1
+    for i in range(k):
+        assert abs(ev[i] - Eo[i]) <= 1e-9 * abs(Eo[i]), (ev, Eo)
+
+
+@pytest.mark.parametrize("name", list(BF16_CASES))
+@pytest.mark.parametrize("y_solver", [0, 1])
+def test_bf16_precond_close_to_fp64(pkg, name, y_solver):
+    """BF16 operands (float32 accumulation) in the z stages and the fused chain, against the float64 chain,
+    and within a few times the TF32 chain's error."""
+    wl = workload("he_l0_24x24x8", **BF16_CASES[name])
+    E = wl["shift"] + 0.011
+    out = {}
+    for key, kw in (("ref", dict(precision=0)), ("tf32", dict(precision=1, mma=2)), ("bf16", dict(precision=1, mma=3))):
+        c = pkg.Context(wl, y_solver=y_solver, **kw)
+        c.fm_set_shift(E)
+        v = _dev(rand_vec(c.n, 24))
+        y = torch.empty_like(v)
+        c.fm_precond_apply(v, y)
+        out[key] = y
+        c.close()
+    nref = torch.linalg.norm(out["ref"]).item()
+    e32 = torch.linalg.norm(out["tf32"] - out["ref"]).item() / nref
+    e16 = torch.linalg.norm(out["bf16"] - out["ref"]).item() / nref
+    print(name, y_solver, "TF32", e32, "BF16", e16)
+    assert e32 < TF32_REL and e16 < BF16_REL, (name, e32, e16)
+
+
+def test_bf16_eligibility(pkg):
+    from paper_2005_05398_gb300._lib import FMError
+    with pytest.raises(FMError) as e:  # n_x = 20: a multiple of 4, not of 8
+        pkg.Context(workload("he_l0_24x24x8", nint=(10, 12, 3)), precision=1, mma=3)
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_bf16_solve_matches_sparse_lu(pkg, precision):
+    """A looser preconditioner, the same float64 solution."""
+    from oracle.system import FMSystem
+    from oracle import solvers
+    wl = workload("he_l0_24x24x8", nint=(12, 8, 4), R=(20.0, 17.0))
+    s = FMSystem(wl)
+    H, S = s.H(), s.S()
+    E = -2.5
+    b = rand_vec(s.N, 25)
+    ref = solvers.solve(H, S, E, b)
+    ctx = pkg.Context(wl, precision=precision, mma=3, restart_m=40)
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    info = ctx.fm_solve(E, _dev(b), x)
+    got = x.cpu().numpy()
+    assert info["converged"] == 1 and info["resid"] <= 1e-12
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8
+
+
+@pytest.mark.parametrize("name,k,precision", [("he_l0_rows136", 2, 1), ("he_l1_banded", 2, 2)])
+def test_bf16_eigs_match_oracle(pkg, name, k, precision):
+    from oracle.system import FMSystem
+    from oracle import solvers
+    wl = workload("he_l0_24x24x8", **BF16_CASES[name])
+    s = FMSystem(wl)
+    H, S = s.H(), s.S()
+    shift = wl["shift"] if name != "he_l1_banded" else -2.12
+    Eo, _ = solvers.eigs_near(H, S, shift, k + 4)
+    real = np.abs(Eo.imag) <= 1e-10 * np.abs(Eo)
+    Eo = Eo[real][:k].real
+    ctx = pkg.Context(wl, restart_m=40, precision=precision, mma=3)
+    ev, info = ctx.fm_eigs(shift, k)
+    assert info["converged"] == 1 and info["resid"] <= 1e-9
     for i in range(k):
         assert abs(ev[i] - Eo[i]) <= 1e-9 * abs(Eo[i]), (ev, Eo)

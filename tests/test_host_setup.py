@@ -83,3 +83,30 @@ def test_y_pencil_and_complex_detection(lib):
     rot = np.array([[0.0, -1.0], [1.0, 0.0]])
     with pytest.raises(lib.FMError):
         lib.fm_host_decompose(rot, np.eye(2))
+
+
+@pytest.mark.parametrize("basis", [0, 1])
+@pytest.mark.parametrize("kind,nint,a,b,dirichlet", [(0, 7, 0.0, 36.0, True), (0, 1, 0.0, 9.0, True),
+                                                    (2, 5, -1.0, 1.0, False), (2, 2, -1.0, 1.0, False),
+                                                    (2, 1, -1.0, 1.0, False), (1, 6, -1.0, 1.0, False)])
+def test_library_axis_equals_oracle_basis(lib, basis, kind, nint, a, b, dirichlet):
+    """The library's spline axis (set-up code, host) against the oracle's basis: the same collocation points,
+    function count and, rebuilt from the taps, the same value / first / second derivative matrices
+    (cubic and quintic Hermite, Dirichlet x / y axes and closed z axes)."""
+    from oracle.splines import Axis
+    ax = lib.fm_host_axis(kind, nint, a, b, dirichlet, basis)
+    ref = Axis(kind, nint, a, b, dirichlet=dirichlet, basis=basis)
+    n, r = ax["n"], ax["r"]
+    assert n == ref.n and r == (4 if basis == 0 else 6)
+    assert np.abs(ax["pts"] - ref.pts).max() < 1e-14 * max(abs(a), abs(b))
+    for d, key in ((0, "S"), (1, "D1"), (2, "D2")):
+        M = np.zeros((n, n))
+        for e in range(n):
+            for t in range(r):
+                j = ax["base"][e] + t
+                if 0 <= j < n:
+                    M[e, j] += ax[key][e, t]
+                else:
+                    assert ax[key][e, t] == 0.0
+        R = ref.mat(d)
+        assert np.abs(M - R).max() < 1e-12 * np.abs(R).max(), (key, np.abs(M - R).max())
