@@ -136,6 +136,12 @@ typedef struct {
                         to tol) given to a returned pair whose backward error is above eig_tol; 0..8, default 2 */
   double inner_tol32; /* FM_PREC_MIXED: relative residual of each float32 inner solve, in [1e-7, 0.5]
                         (default 3e-5; smaller means fewer refinement steps, more float32 iterations each) */
+  int tc_chain;      /* tensor-core preconditioner chain: 0 = z stages on the tensor cores and, for n_M = 1, the
+                        x / y stages of a slab in one fused kernel; 1 = z stages on CUDA cores and one
+                        tensor-core launch per x / y stage (TF32) */
+  int gram_schmidt;  /* float64 FGMRES orthogonalisation: 0 = two classical Gram-Schmidt passes, the first on
+                        the FP32 pipe from the leading bits; 1 = one float64 pass, repeated only when it
+                        cancelled more than half of the vector's norm (DGKS test) */
   int device;        /* CUDA device ordinal */
   void* stream;      /* cudaStream_t, NULL = legacy default stream */
 } fm_opts;

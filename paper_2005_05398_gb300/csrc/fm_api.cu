@@ -122,8 +122,10 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
       if ((rc = launch_precond(c, Vj, Zj))) return rc;
       if ((rc = apply_tuning(c, Zj))) return rc;
       if ((rc = launch_apply(c, E, Zj, c->w, false))) return rc;
-      double hn;  // CGS2 writes the next basis vector V[j+1] = (w - V h) / hn
-      if ((rc = gs_cgs2(c, c->V, j + 1, c->w, c->V + (int64_t)(j + 1) * N, h.data(), &hn))) return rc;
+      double hn;  // Gram-Schmidt writes the next basis vector V[j+1] = (w - V h) / hn
+      if (c->opts.gram_schmidt == 1) rc = gs_cgs1(c, c->V, j + 1, c->w, c->V + (int64_t)(j + 1) * N, h.data(), &hn);
+      else rc = gs_cgs2(c, c->V, j + 1, c->w, c->V + (int64_t)(j + 1) * N, h.data(), &hn);
+      if (rc) return rc;
       if (!std::isfinite(hn)) return FM_ERR_BREAKDOWN;
       for (int i = 0; i < j; ++i) {  // previous Givens rotations
         const double t = cs[i] * h[i] + sn[i] * h[i + 1];
@@ -377,6 +379,8 @@ void fm_default_opts(fm_opts* o) {
   o->start_filter = 8;
   o->refine = 2;
   o->inner_tol32 = 3e-5;
+  o->tc_chain = 0;
+  o->gram_schmidt = 0;
   o->device = 0;
   o->stream = nullptr;
 }
@@ -434,7 +438,8 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
   if (o.restart_m < 1 || o.restart_m > 256 || o.max_iters < 1 || !(o.tol > 0) || o.ncv < 3 || o.ncv > 64 ||
       o.max_restarts < 0 || !(o.eig_tol > 0) || o.precision < 0 || o.precision > 2 || o.y_solver < 0 ||
       o.y_solver > 2 || o.mma < 0 || o.mma > 3 || o.start_filter < 0 || o.start_filter > 16 || o.refine < 0 || o.refine > 8 ||
-      !(o.inner_tol32 >= 1e-7 && o.inner_tol32 <= 0.5))
+      !(o.inner_tol32 >= 1e-7 && o.inner_tol32 <= 0.5) || o.gram_schmidt < 0 || o.gram_schmidt > 1 ||
+      o.tc_chain < 0 || o.tc_chain > 1 || (o.tc_chain == 1 && o.mma == FM_MMA_BF16))
     return FM_ERR_ARG;
   fm_ctx* c = new fm_ctx();
   c->sys = *sys;

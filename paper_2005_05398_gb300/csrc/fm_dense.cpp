@@ -263,35 +263,45 @@ int hess_eigvals(int n, const double* Hin, double* re, double* im) {
         }
       }
     }
-    // clean the entries below the subdiagonal created by rounding
-    for (int i = lo + 2; i <= hi; ++i)
-      for (int j = lo; j < i - 1; ++j) at(A, n, i, j) = 0.0;
+    // clean the entries below the subdiagonal the bulge chase leaves by rounding (the 3-element reflectors
+    // touch only (i, i-2) and (i, i-3))
+    for (int i = lo + 2; i <= hi; ++i) {
+      at(A, n, i, i - 2) = 0.0;
+      if (i - 3 >= lo) at(A, n, i, i - 3) = 0.0;
+    }
   }
   return 0;
 }
 
-// Solve (H - mu I) y = b for upper-Hessenberg H by elimination with adjacent-row pivoting.
-static void hess_shifted_solve(int n, const double* H, double mu, double tiny, double* b, double* work) {
-  double* M = work;  // n*n
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) M[(size_t)i * n + j] = (j >= i - 1) ? H[(size_t)i * n + j] - (i == j ? mu : 0.0) : 0.0;
+// LU factors of (H - mu I) for upper-Hessenberg H by elimination with adjacent-row pivoting: M holds U
+// (rows from their diagonal on), l[k] the multiplier of step k and sw[k] whether rows k, k+1 were swapped.
+static void hess_shifted_factor(int n, const double* H, double mu, double tiny, double* M, double* l, char* sw) {
+  for (int i = 0; i < n; ++i) {
+    const int j0 = std::max(0, i - 1);
+    for (int j = j0; j < n; ++j) M[(size_t)i * n + j] = H[(size_t)i * n + j] - (i == j ? mu : 0.0);
+  }
   for (int k = 0; k + 1 < n; ++k) {
     double* rk = M + (size_t)k * n;
     double* r1 = M + (size_t)(k + 1) * n;
-    if (std::fabs(r1[k]) > std::fabs(rk[k])) {
+    sw[k] = std::fabs(r1[k]) > std::fabs(rk[k]);
+    if (sw[k])
       for (int j = k; j < n; ++j) std::swap(rk[j], r1[j]);
-      std::swap(b[k], b[k + 1]);
-    }
     if (rk[k] == 0.0) rk[k] = tiny;
-    const double l = r1[k] / rk[k];
-    if (l != 0.0) {
-      for (int j = k; j < n; ++j) r1[j] -= l * rk[j];
-      b[k + 1] -= l * b[k];
-    }
+    l[k] = r1[k] / rk[k];
+    if (l[k] != 0.0)
+      for (int j = k + 1; j < n; ++j) r1[j] -= l[k] * rk[j];
+  }
+  if (M[(size_t)(n - 1) * n + n - 1] == 0.0) M[(size_t)(n - 1) * n + n - 1] = tiny;
+}
+
+// y <- (H - mu I)^{-1} y with the factors of hess_shifted_factor
+static void hess_shifted_lu_solve(int n, const double* M, const double* l, const char* sw, double* b) {
+  for (int k = 0; k + 1 < n; ++k) {
+    if (sw[k]) std::swap(b[k], b[k + 1]);
+    b[k + 1] -= l[k] * b[k];
   }
   for (int i = n - 1; i >= 0; --i) {
-    double* ri = M + (size_t)i * n;
-    if (ri[i] == 0.0) ri[i] = tiny;
+    const double* ri = M + (size_t)i * n;
     double s = b[i];
     for (int j = i + 1; j < n; ++j) s -= ri[j] * b[j];
     b[i] = s / ri[i];
@@ -339,7 +349,8 @@ int eig_general2(int n, const double* Ain, double* re, double* im, double* Vr, d
   for (int i = 0; i < n; ++i) maxabs = std::max(maxabs, std::hypot(re[i], im[i]));
   for (size_t i = 0; i < A.size(); ++i) hn = std::max(hn, std::fabs(A[i]));
   int status = 0;
-  std::vector<double> work((size_t)n * n), y(n);
+  std::vector<double> work((size_t)n * n), y(n), lmul(n);
+  std::vector<char> swp(n);
   std::vector<cplx> cwork((size_t)n * n), cy(n);
   const double tiny = 1e-15 * (hn > 0 ? hn : 1.0);
   for (int e = 0; e < n; ++e) {
@@ -347,8 +358,9 @@ int eig_general2(int n, const double* Ain, double* re, double* im, double* Vr, d
     if (!cx) {
       im[e] = 0.0;
       for (int i = 0; i < n; ++i) y[i] = 1.0 + 0.1 * std::sin(1.0 + 3.7 * i + 0.3 * e);
+      hess_shifted_factor(n, A.data(), re[e], tiny, work.data(), lmul.data(), swp.data());
       for (int it = 0; it < 3; ++it) {
-        hess_shifted_solve(n, A.data(), re[e], tiny, y.data(), work.data());
+        hess_shifted_lu_solve(n, work.data(), lmul.data(), swp.data(), y.data());
         double nr = 0.0;
         for (int i = 0; i < n; ++i) nr += y[i] * y[i];
         nr = std::sqrt(nr);

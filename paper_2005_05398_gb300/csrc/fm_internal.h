@@ -228,6 +228,7 @@ int axpy_many(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* h_h
 int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* w, const double* extra, double* h_dev,
                  bool lowp = false);
 int gs_cgs2(fm_ctx* c, const double* V, int nv, double* w, double* vout, double* h, double* hn);
+int gs_cgs1(fm_ctx* c, const double* V, int nv, double* w, double* vout, double* h, double* hn);
 int gs_cgs2_32(fm_ctx* c, const float* V, int nv, float* w, float* vout, double* h, double* hn);
 int tuning_correct(fm_ctx* c, const double* U, const double* WmU, const double* Gdev, int k, double* z);
 int scale_copy(fm_ctx* c, const double* x, double a, double* y);   // y = a x
@@ -246,6 +247,7 @@ bool tc_component_ok(const Comp& cp);
 int tc_setup(fm_ctx* c);       // after the stage buffers exist: encode the TMA maps
 int tc_kernels_init();
 int tc_check(fm_ctx* c);       // FM_ERR_TIMEOUT when a tensor-core kernel gave up a wait
+int* tc_flag_slot(fm_ctx* c);  // the wait flag's place in the Gram-Schmidt result buffer (read every step)
 // tensor-core chain over all components: z and x forward (+ y for the diagonalised n_M = 1 form, fused
 // per slab where eligible); the components left for the banded y solves are returned in 'banded'
 template <typename TIO>

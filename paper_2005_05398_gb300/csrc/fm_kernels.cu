@@ -679,6 +679,10 @@ __global__ void __launch_bounds__(LPB) k_ysolve(const YBatch<T> yb, int R, int W
 // ---------------------------------------------------------------------------
 constexpr int kRedThreads = 256;
 constexpr int kGsMaxVec = 264;  // basis vectors one Gram-Schmidt pass takes (restart length <= 256)
+// gsd layout: [0, kGsMaxVec) first-pass coefficients, [kGsMaxVec, 2 kGsMaxVec) second pass, [3 kGsMaxVec, +4)
+// scalars, [kGsFlag] the tensor-core kernels' wait flag (an int), read back with every Gram-Schmidt result
+constexpr int kGsFlag = 3 * kGsMaxVec + 8;
+constexpr int kGsRead = kGsFlag + 1;
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -963,6 +967,9 @@ __global__ void k_axpby32(float a, const float* __restrict__ x, float b, float* 
 // MODE 0: w <- w', out[0] = ||w'||^2.
 // MODE 1 (closing pass): nu^2 = nrm2_prev - |c|^2 (the norm of w' by Pythagoras, V orthonormal and
 // c = V^T w), vout <- w' / nu (0 when nu^2 <= 0), out[0] = ||vout||^2 (1 up to rounding), out[1] = nu.
+// MODE 2 (single pass with the DGKS test): as MODE 1 when nu^2 >= nrm2_prev / 2 (little cancellation: one
+// float64 projection is enough), out[2] = 0; otherwise as MODE 0 (w <- w', out[0] = ||w'||^2) with
+// out[2] = 1, and the caller re-orthogonalises.  Every block takes the same decision from the same values.
 template <int MODE>
 __global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restrict__ V, int64_t ldv, int nv,
                                                         const double* __restrict__ h, const double* __restrict__ G,
@@ -972,6 +979,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restric
   __shared__ double cs[kGsMaxVec];
   __shared__ double sh[32];
   __shared__ double inv_nu;
+  __shared__ int reorth;
   for (int j = threadIdx.x; j < nv; j += blockDim.x) {
     double cj;
     if (G) {
@@ -983,15 +991,20 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restric
     cs[j] = cj;
   }
   __syncthreads();
-  if (MODE == 1 && threadIdx.x == 0) {
+  if (MODE >= 1 && threadIdx.x == 0) {
     double c2 = 0.0;
     for (int j = 0; j < nv; ++j) c2 = fma(cs[j], cs[j], c2);
     const double nu2 = *nrm2_prev - c2;
     const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
     inv_nu = nu > 0.0 ? 1.0 / nu : 0.0;
-    if (blockIdx.x == 0) out[1] = nu;
+    reorth = (MODE == 2 && !(nu2 >= 0.5 * *nrm2_prev)) ? 1 : 0;
+    if (blockIdx.x == 0) {
+      out[1] = nu;
+      if (MODE == 2) out[2] = (double)reorth;
+    }
   }
   __syncthreads();
+  const bool write_w = MODE == 0 || (MODE == 2 && reorth);
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     // one FMA per basis vector on a single chain (no partial sums to add: FP64 issue is the bound);
@@ -1006,7 +1019,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restric
       for (int u = 0; u < 8; ++u) v = fma(-cs[j + u], t[u], v);
     }
     for (; j < nv; ++j) v = fma(-cs[j], V[(int64_t)j * ldv + i], v);
-    if (MODE == 0) {
+    if (write_w) {
       w[i] = v;
       acc = fma(v, v, acc);
     } else {
@@ -1621,11 +1634,67 @@ int gs_cgs2(fm_ctx* c, const double* V, int nv, double* w, double* vout, double*
   c->launches += 2;
   FM_CUDA(cudaGetLastError());
   // one read-back: h1, h2 and the three scalars
-  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, (3 * kGsMaxVec + 3) * sizeof(double), cudaMemcpyDeviceToHost,
+  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, kGsRead * sizeof(double), cudaMemcpyDeviceToHost,
                           c->stream));
   FM_CUDA(cudaStreamSynchronize(c->stream));
   const double* hh = c->red_host;
+  if (c->tc_active && reinterpret_cast<const int*>(hh + kGsFlag)[0] != 0) return FM_ERR_TIMEOUT;
   for (int i = 0; i < nv; ++i) h[i] = hh[i] + hh[kGsMaxVec + i];
+  const double vn2 = hh[3 * kGsMaxVec + 1], nu = hh[3 * kGsMaxVec + 2];
+  if (!(nu > 0.0) || !(vn2 > 0.0)) {
+    *hn = std::isfinite(nu) && std::isfinite(vn2) ? 0.0 : nu + vn2;
+    return prof_harvest(c);
+  }
+  const double vn = std::sqrt(vn2);
+  *hn = nu * vn;
+  if (std::fabs(vn - 1.0) > 1e-12)  // Pythagoras lost digits: rescale to unit norm
+    if ((rc = scale_copy(c, vout, 1.0 / vn, vout))) return rc;
+  return prof_harvest(c);
+}
+
+// Single-pass classical Gram-Schmidt in float64 with the DGKS re-orthogonalisation test: one multi-dot (with
+// |w|^2 from the same pass), one update that normalises directly when |w - V h| >= |w| / sqrt(2); otherwise
+// it keeps w - V h and a second float64 pass (multi-dot, closing update) follows.  One host synchronisation
+// when no re-orthogonalisation is needed, two otherwise.  Same results as gs_cgs2 to rounding.
+int gs_cgs1(fm_ctx* c, const double* V, int nv, double* w, double* vout, double* h, double* hn) {
+  if (nv < 1 || nv + 1 > kGsMaxVec) return FM_ERR_ARG;
+  const int64_t N = c->N;
+  double* h1 = c->gsd;                  // [nv] V^T w, [nv] |w|^2
+  double* h2 = c->gsd + kGsMaxVec;
+  double* sc = c->gsd + 3 * kGsMaxVec;  // [1] |out|^2, [2] nu, [3] re-orthogonalise
+  const int nb2 = 4 * c->red_blocks;
+  int rc;
+  if ((rc = dot_many_dev(c, V, N, nv, w, w, h1))) return rc;
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+    k_gs_axpy<2><<<nb2, kRedThreads, 0, c->stream>>>(V, N, nv, h1, nullptr, nullptr, w, vout, N, c->red, c->gs_cnt,
+                                                     sc + 1, h1 + nv);
+    prof_end(c, tk_, (2.0 * nv + 2.0) * (double)N, (nv + 2.0) * 8.0 * (double)N);
+  }
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, kGsRead * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  const double* hh = c->red_host;
+  if (c->tc_active && reinterpret_cast<const int*>(hh + kGsFlag)[0] != 0) return FM_ERR_TIMEOUT;
+  for (int i = 0; i < nv; ++i) h[i] = hh[i];
+  if (hh[3 * kGsMaxVec + 3] != 0.0) {  // cancellation: second float64 pass on w - V h
+    if ((rc = dot_many_dev(c, V, N, nv, w, nullptr, h2))) return rc;
+    {
+      const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+      k_gs_axpy<1><<<nb2, kRedThreads, 0, c->stream>>>(V, N, nv, h2, nullptr, nullptr, w, vout, N, c->red, c->gs_cnt,
+                                                       sc + 1, sc + 1);
+      prof_end(c, tk_, (2.0 * nv + 2.0) * (double)N, (nv + 2.0) * 8.0 * (double)N);
+    }
+    c->launches++;
+    FM_CUDA(cudaGetLastError());
+    FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, kGsRead * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+    FM_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->tc_active && reinterpret_cast<const int*>(hh + kGsFlag)[0] != 0) return FM_ERR_TIMEOUT;
+    for (int i = 0; i < nv; ++i) h[i] += hh[kGsMaxVec + i];
+  }
   const double vn2 = hh[3 * kGsMaxVec + 1], nu = hh[3 * kGsMaxVec + 2];
   if (!(nu > 0.0) || !(vn2 > 0.0)) {
     *hn = std::isfinite(nu) && std::isfinite(vn2) ? 0.0 : nu + vn2;
@@ -1674,10 +1743,11 @@ int gs_cgs2_32(fm_ctx* c, const float* V, int nv, float* w, float* vout, double*
   }
   c->launches += 4;
   FM_CUDA(cudaGetLastError());
-  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, (3 * kGsMaxVec + 3) * sizeof(double), cudaMemcpyDeviceToHost,
+  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, kGsRead * sizeof(double), cudaMemcpyDeviceToHost,
                           c->stream));
   FM_CUDA(cudaStreamSynchronize(c->stream));
   const double* hh = c->red_host;
+  if (c->tc_active && reinterpret_cast<const int*>(hh + kGsFlag)[0] != 0) return FM_ERR_TIMEOUT;
   for (int i = 0; i < nv; ++i) h[i] = hh[i] + hh[kGsMaxVec + i];
   const double vn2 = hh[3 * kGsMaxVec + 1], nu = hh[3 * kGsMaxVec + 2];
   if (!(nu > 0.0) || !(vn2 > 0.0)) {
@@ -1883,6 +1953,8 @@ int axpby32(fm_ctx* c, float a, const float* x, float b, float* y) {
   FM_CUDA(cudaGetLastError());
   return FM_OK;
 }
+
+int* tc_flag_slot(fm_ctx* c) { return reinterpret_cast<int*>(c->gsd + kGsFlag); }
 
 int kernels_init(fm_ctx* c) {
   (void)c;

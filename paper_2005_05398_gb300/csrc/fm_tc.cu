@@ -572,15 +572,16 @@ __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMa
       const bool ok = i < a.nx && j < a.ny;
       const int64_t src = IN_JI ? a.off + ((int64_t)iM * a.nz * a.ny + j) * a.nx + i
                                 : a.off + ((int64_t)iM * a.nz * a.nx + i) * a.ny + j;
-      for (int k0 = 0; k0 < kpad; k0 += 8) {
-        float v[8];
+      // 32 loads in flight per thread (two round trips to memory for n_z <= 64)
+      for (int k0 = 0; k0 < kpad; k0 += 32) {
+        float v[32];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 32; ++u) {
           const int k = k0 + u;
           v[u] = (ok && k < a.nz) ? load_as_float<TI>(in + src + (int64_t)k * nxy) : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 32; ++u) {
           const int k = k0 + u;
           if (k < kpad) {
             const int kb = k / Op::kRow, byte = (k % Op::kRow) * (int)sizeof(TB);
@@ -1023,10 +1024,9 @@ int tc_setup(fm_ctx* c) {
   for (auto& cp : c->comps) all = all && (want_bf16 ? bf16_component_ok(cp) : tc_component_ok(cp));
   if (!all) return (c->opts.mma == FM_MMA_TF32 || want_bf16) ? FM_ERR_ARG : FM_OK;
   if (!encode_fn()) return c->opts.mma == FM_MMA_AUTO ? FM_OK : FM_ERR_CUDA;
-  if (!c->tc_err) {
-    int rc = dev_alloc(c, (void**)&c->tc_err, 256);
-    if (rc) return rc;
-    FM_CUDA(cudaMemsetAsync(c->tc_err, 0, 256, c->stream));
+  if (!c->tc_err) {  // read back with every Gram-Schmidt result, so a Krylov step sees an expired wait
+    c->tc_err = tc_flag_slot(c);
+    FM_CUDA(cudaMemsetAsync(c->tc_err, 0, sizeof(double), c->stream));
   }
   const CUtensorMapDataType dt = want_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const int es = want_bf16 ? 2 : 4, E = 128 / es;
@@ -1044,7 +1044,7 @@ int tc_setup(fm_ctx* c) {
     }
     if (!ok) return FM_ERR_CUDA;
     // z stages on the tensor cores (W_z with padded rows)
-    cp.tcz = cp.Wz_tc && cp.Wzb_tc && cp.nz <= 128;
+    cp.tcz = c->opts.tc_chain == 0 && cp.Wz_tc && cp.Wzb_tc && cp.nz <= 128;
     if (cp.tcz) {
       ok = encode3t(&cp.tmz[0], cp.Wzb_tc, dt, es, cp.ldz, cp.nz, c->nM, E, 128) &&
            encode3t(&cp.tmz[1], cp.Wz_tc, dt, es, cp.ldz, cp.nz, c->nM, E, 128);
