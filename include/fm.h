@@ -92,10 +92,10 @@ typedef struct {
 } fm_splitting;
 
 /* Precision modes.  FP64: float64 everywhere.  FP32: float32 preconditioner, float64 operator,
- * FGMRES and Gram-Schmidt.  MIXED: float64 iterative refinement on the true float64 residual
- * around float32 FGMRES corrections (float32 operator, preconditioner and Gram-Schmidt), each
- * solved to the relative residual fm_opts.inner_tol32 (default 3e-5); the result meets the same
- * float64 tolerance. */
+ * FGMRES and Gram-Schmidt.  MIXED: float32 FGMRES solves (float32 operator, preconditioner and
+ * Gram-Schmidt) inside a float64 iteration on the true float64 residual, chosen by
+ * fm_opts.mixed_scheme: a flexible float64 FGMRES whose preconditioner is the float32 solve
+ * (default), or iterative refinement; the result meets the same float64 tolerance. */
 enum { FM_PREC_FP64 = 0, FM_PREC_FP32 = 1, FM_PREC_MIXED = 2 };
 
 /* Mode products of the float32 preconditioner (FP32 and MIXED precision).  AUTO: TF32 tensor-core
@@ -134,14 +134,20 @@ typedef struct {
                         enriches the directions of the levels nearest the shift); 0..16, default 8 */
   int refine;        /* fm_eigs: most inverse-iteration steps c <- (H - shift S)^{-1} S c / |.| (float64 solves
                         to tol) given to a returned pair whose backward error is above eig_tol; 0..8, default 2 */
-  double inner_tol32; /* FM_PREC_MIXED: relative residual of each float32 inner solve, in [1e-7, 0.5]
-                        (default 3e-5; smaller means fewer refinement steps, more float32 iterations each) */
+  double inner_tol32; /* FM_PREC_MIXED: relative residual of each float32 inner solve, in [1e-7, 0.5], or 0 for
+                        the scheme's default (1e-2 flexible, 3e-5 refinement); smaller means fewer float64
+                        steps and more float32 iterations in each */
   int tc_chain;      /* tensor-core preconditioner chain: 0 = z stages on the tensor cores and, for n_M = 1, the
                         x / y stages of a slab in one fused kernel; 1 = z stages on CUDA cores and one
                         tensor-core launch per x / y stage (TF32) */
   int gram_schmidt;  /* float64 FGMRES orthogonalisation: 0 = two classical Gram-Schmidt passes, the first on
                         the FP32 pipe from the leading bits; 1 = one float64 pass, repeated only when it
                         cancelled more than half of the vector's norm (DGKS test) */
+  int mixed_scheme;  /* FM_PREC_MIXED: 0 = flexible inner-outer iteration (float64 FGMRES on the float64 operator,
+                        each of its preconditioner steps a float32 FGMRES solve of the normalised basis
+                        vector, so the float64 Krylov space is kept across the float32 solves; default);
+                        1 = iterative refinement x += float32 solve of the normalised float64 residual,
+                        each refinement step starting a new float32 Krylov space */
   int device;        /* CUDA device ordinal */
   void* stream;      /* cudaStream_t, NULL = legacy default stream */
 } fm_opts;
@@ -154,8 +160,10 @@ enum {
 };
 
 typedef struct {
-  int iters;          /* FGMRES iterations (fm_solve) or total inner iterations (fm_eigs, refinement included) */
-  int restarts;       /* FGMRES restarts (refinement steps in FM_PREC_MIXED) or Arnoldi restarts */
+  int iters;          /* FGMRES iterations (fm_solve; float32 iterations in FM_PREC_MIXED) or total inner
+                         iterations (fm_eigs, refinement included) */
+  int restarts;       /* FGMRES restarts (FM_PREC_MIXED: float64 outer iterations of the flexible scheme or
+                         refinement steps) or Arnoldi restarts */
   int op_applies;     /* shift-invert operator applications (fm_eigs, refinement included) */
   int converged;      /* 1 when every requested quantity met its tolerance */
   double resid;       /* fm_solve: final relative residual |b - (H - E S) x| / |b|;

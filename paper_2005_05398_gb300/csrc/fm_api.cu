@@ -14,9 +14,12 @@
 
 namespace fmi {
 
+// Context memory is stream-ordered on the context's stream where the device has memory pools: its release
+// (cudaFreeAsync) then waits for that stream only, so a context destroyed beside others running on their own
+// streams (the request loop) does not stall them as a device-wide cudaFree would.
 int dev_alloc(fm_ctx* c, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = c->pool_alloc ? cudaMallocAsync(p, bytes, c->stream) : cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -78,8 +81,30 @@ static int set_tuning(fm_ctx* c, double E, const double* U, int k) {
 }
 
 // Right-preconditioned restarted FGMRES for (H - E S) x = b (x: initial guess in, solution out).
+static int fgmres32(fm_ctx* c, double E, const float* b, float* d, double tol, int max_iters, int* iters_out);
+
+// Relative residual of each float32 inner solve in FM_PREC_MIXED (0 selects the scheme's default).
+static double inner_tol32(const fm_ctx* c) {
+  if (c->opts.inner_tol32 > 0.0) return c->opts.inner_tol32;
+  return c->opts.mixed_scheme == 0 ? 1e-2 : 3e-5;
+}
+
+// Preconditioner step of the flexible scheme: z <- float32 FGMRES solution of (H - E S) z = v for a unit
+// float64 vector v (float32 operator, preconditioner and basis), widened to float64.
+static int precond_flex32(fm_ctx* c, double E, const double* v, double* z, int max_iters, int* iters) {
+  int rc;
+  if ((rc = to32(c, v, 1.0, c->d32))) return rc;
+  if ((rc = fgmres32(c, E, c->d32, c->e32, inner_tol32(c), max_iters, iters))) return rc;
+  FM_CUDA(cudaMemsetAsync(z, 0, c->N * sizeof(double), c->stream));
+  return add32(c, c->e32, 1.0, z);
+}
+
+// Right-preconditioned flexible GMRES (restart m) for (H - E S) x = b on the float64 operator.  The
+// preconditioner step is the tensor preconditioner (FP64 / FP32 modes, optionally tuned) or, with flex32, a
+// float32 FGMRES solve (FM_PREC_MIXED, flexible scheme); iters_out then counts the float32 iterations and
+// restarts_out the float64 outer iterations.
 static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, int max_iters, int* iters_out,
-                  int* restarts_out, double* resid_out) {
+                  int* restarts_out, double* resid_out, bool flex32 = false) {
   int rc;
   const int m = c->opts.restart_m;
   const int64_t N = c->N;
@@ -98,7 +123,7 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
   double beta;
   if ((rc = nrm2(c, r, &beta))) return rc;
   std::vector<double> R((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 1), y(m);
-  int total = 0;
+  int total = 0, inner32 = 0, outer = 0;
   bool converged = false;
   double beta_prev = HUGE_VAL;
   while (true) {
@@ -119,8 +144,16 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
     for (int j = 0; j < m && total < max_iters; ++j) {
       double* Vj = c->V + (int64_t)j * N;
       double* Zj = c->Z + (int64_t)j * N;
-      if ((rc = launch_precond(c, Vj, Zj))) return rc;
-      if ((rc = apply_tuning(c, Zj))) return rc;
+      if (flex32) {
+        int it = 0;
+        if ((rc = precond_flex32(c, E, Vj, Zj, std::max(1, max_iters - total), &it))) return rc;
+        inner32 += it;
+        total += std::max(it, 1) - 1;  // the float32 iterations count against max_iters (+1 below)
+        ++outer;
+      } else {
+        if ((rc = launch_precond(c, Vj, Zj))) return rc;
+        if ((rc = apply_tuning(c, Zj))) return rc;
+      }
       if ((rc = launch_apply(c, E, Zj, c->w, false))) return rc;
       double hn;  // Gram-Schmidt writes the next basis vector V[j+1] = (w - V h) / hn
       if (c->opts.gram_schmidt == 1) rc = gs_cgs1(c, c->V, j + 1, c->w, c->V + (int64_t)(j + 1) * N, h.data(), &hn);
@@ -155,7 +188,8 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
     if ((rc = axpby(c, 1.0, b, -1.0, r))) return rc;
     if ((rc = nrm2(c, r, &beta))) return rc;
   }
-  *iters_out = total;
+  *iters_out = flex32 ? inner32 : total;
+  if (flex32) *restarts_out = outer;
   *resid_out = beta / bnorm;
   return converged ? FM_OK : FM_ERR_NOT_CONVERGED;
 }
@@ -258,7 +292,7 @@ static int ir_solve(fm_ctx* c, double E, const double* b, double* x, double tol,
     beta_prev = beta;
     if ((rc = to32(c, r, 1.0 / beta, c->d32))) return rc;  // normalised residual as the float32 right-hand side
     int it = 0;
-    if ((rc = fgmres32(c, E, c->d32, c->e32, c->opts.inner_tol32, max_iters - total, &it))) return rc;
+    if ((rc = fgmres32(c, E, c->d32, c->e32, inner_tol32(c), max_iters - total, &it))) return rc;
     total += it;
     ++*outer_out;
     if ((rc = add32(c, c->e32, beta, x))) return rc;  // x += beta * correction
@@ -275,7 +309,10 @@ static int ir_solve(fm_ctx* c, double E, const double* b, double* x, double tol,
 // iterative refinement around float32 FGMRES (mode 2).
 static int solve_any(fm_ctx* c, double E, const double* b, double* x, double tol, int max_iters, int* iters_out,
                      int* restarts_out, double* resid_out) {
-  if (c->opts.precision == FM_PREC_MIXED) return ir_solve(c, E, b, x, tol, max_iters, iters_out, restarts_out, resid_out);
+  if (c->opts.precision == FM_PREC_MIXED) {
+    if (c->opts.mixed_scheme == 1) return ir_solve(c, E, b, x, tol, max_iters, iters_out, restarts_out, resid_out);
+    return fgmres(c, E, b, x, tol, max_iters, iters_out, restarts_out, resid_out, true);
+  }
   return fgmres(c, E, b, x, tol, max_iters, iters_out, restarts_out, resid_out);
 }
 
@@ -378,9 +415,10 @@ void fm_default_opts(fm_opts* o) {
   o->mma = FM_MMA_AUTO;
   o->start_filter = 8;
   o->refine = 2;
-  o->inner_tol32 = 3e-5;
+  o->inner_tol32 = 0.0;
   o->tc_chain = 0;
   o->gram_schmidt = 0;
+  o->mixed_scheme = 0;
   o->device = 0;
   o->stream = nullptr;
 }
@@ -412,7 +450,12 @@ void fm_destroy(fm_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (auto e : c->ev_free) cudaEventDestroy(e);
-  for (void* p : c->allocs) cudaFree(p);
+  if (c->pool_alloc) {
+    for (void* p : c->allocs) cudaFreeAsync(p, c->stream);
+    cudaStreamSynchronize(c->stream);  // the memory is back in the pool when fm_destroy returns
+  } else {
+    for (void* p : c->allocs) cudaFree(p);
+  }
   if (c->red_host) cudaFreeHost(c->red_host);
   delete c;
 }
@@ -438,7 +481,8 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
   if (o.restart_m < 1 || o.restart_m > 256 || o.max_iters < 1 || !(o.tol > 0) || o.ncv < 3 || o.ncv > 64 ||
       o.max_restarts < 0 || !(o.eig_tol > 0) || o.precision < 0 || o.precision > 2 || o.y_solver < 0 ||
       o.y_solver > 2 || o.mma < 0 || o.mma > 3 || o.start_filter < 0 || o.start_filter > 16 || o.refine < 0 || o.refine > 8 ||
-      !(o.inner_tol32 >= 1e-7 && o.inner_tol32 <= 0.5) || o.gram_schmidt < 0 || o.gram_schmidt > 1 ||
+      !(o.inner_tol32 == 0.0 || (o.inner_tol32 >= 1e-7 && o.inner_tol32 <= 0.5)) || o.gram_schmidt < 0 ||
+      o.gram_schmidt > 1 || o.mixed_scheme < 0 || o.mixed_scheme > 1 ||
       o.tc_chain < 0 || o.tc_chain > 1 || (o.tc_chain == 1 && o.mma == FM_MMA_BF16))
     return FM_ERR_ARG;
   fm_ctx* c = new fm_ctx();
@@ -464,6 +508,11 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
     tph = now;
   };
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(FM_ERR_CUDA);
+  {
+    int pools = 0;
+    if (cudaDeviceGetAttribute(&pools, cudaDevAttrMemoryPoolsSupported, c->device) != cudaSuccess) return fail(FM_ERR_CUDA);
+    c->pool_alloc = pools != 0;
+  }
   if ((rc = kernels_init(c))) return fail(rc);
   phase("kernel attributes");
   if ((rc = setup_host(c, grids, n_grids))) return fail(rc);

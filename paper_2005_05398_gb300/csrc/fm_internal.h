@@ -136,6 +136,7 @@ struct fm_ctx {
   fm_opts opts{};
   int device = 0;
   cudaStream_t stream = nullptr;
+  bool pool_alloc = false;  // allocations stream-ordered on `stream` (cudaMallocAsync / cudaFreeAsync)
   int M0 = 0, nM = 0;
   std::vector<int> Mps;
   std::vector<fmi::Comp> comps;

@@ -105,9 +105,14 @@ struct fm_server {
       const int64_t n = c->N;
       res->n = n;
       const int nvec = (r.kind == FM_REQ_SOLVE) ? 1 : r.k;
-      if (cudaMalloc((void**)&b, n * 8) != cudaSuccess ||
-          cudaMalloc((void**)&x, (size_t)n * 8 * ((r.kind == FM_REQ_EIGS && !r.out_host) ? 1 : nvec)) != cudaSuccess)
+      // stream-ordered on the slot's stream: allocating and releasing them does not synchronise the device,
+      // so the other slots' kernels keep running
+      if (cudaMallocAsync((void**)&b, n * 8, stream) != cudaSuccess ||
+          cudaMallocAsync((void**)&x, (size_t)n * 8 * ((r.kind == FM_REQ_EIGS && !r.out_host) ? 1 : nvec), stream) !=
+              cudaSuccess) {
+        cudaGetLastError();
         rc = FM_ERR_OOM;
+      }
       if (rc == FM_OK) rc = fmi::fill_normal(c, b, r.seed);
       fm_info info{};
       if (rc == FM_OK && r.kind == FM_REQ_SOLVE) {
@@ -131,9 +136,9 @@ struct fm_server {
           rc = FM_ERR_CUDA;
       }
     }
-    if (b) cudaFree(b);
-    if (x) cudaFree(x);
-    if (c) fm_destroy(c);
+    if (b) cudaFreeAsync(b, stream);
+    if (x) cudaFreeAsync(x, stream);
+    if (c) fm_destroy(c);  // synchronises the slot's stream, after which b and x are back in the pool
     res->status = rc;
   }
 

@@ -269,17 +269,45 @@ static float2 split2(double v) {
   return make_float2(hi, (float)(v - (double)hi));
 }
 
-static double lfact(int n) { return std::lgamma(n + 1.0); }
+// log n! and binomial coefficients from tables (the arguments here are small integers: J <= 11)
+constexpr int kFactTab = 64;
+struct FactTables {
+  double lf[kFactTab];
+  double bin[kFactTab][kFactTab];
+  FactTables() {
+    for (int n = 0; n < kFactTab; ++n) lf[n] = std::lgamma(n + 1.0);
+    for (int n = 0; n < kFactTab; ++n)
+      for (int k = 0; k < kFactTab; ++k) bin[n][k] = (k == 0 || k == n) ? 1.0 : (k > n ? 0.0 : bin[n - 1][k - 1] + bin[n - 1][k]);
+  }
+};
+static const FactTables& fact_tables() {
+  static const FactTables t;
+  return t;
+}
+
+static double lfact(int n) { return (n >= 0 && n < kFactTab) ? fact_tables().lf[n] : std::lgamma(n + 1.0); }
 
 static double binom(int n, int k) {
   if (k < 0 || k > n) return 0.0;
+  if (n < kFactTab) return fact_tables().bin[n][k];
   return std::exp(lfact(n) - lfact(k) - lfact(n - k));
 }
 
+// x^e for a non-negative integer e by repeated squaring
+static double ipow(double x, int e) {
+  double r = 1.0;
+  while (e > 0) {
+    if (e & 1) r *= x;
+    x *= x;
+    e >>= 1;
+  }
+  return r;
+}
+
 static double jacobi_poly(int n, int al, int be, double x) {
+  const double xm = (x - 1.0) / 2.0, xp = (x + 1.0) / 2.0;
   double s = 0.0;
-  for (int k = 0; k <= n; ++k)
-    s += binom(n + al, n - k) * binom(n + be, k) * std::pow((x - 1.0) / 2.0, k) * std::pow((x + 1.0) / 2.0, n - k);
+  for (int k = 0; k <= n; ++k) s += binom(n + al, n - k) * binom(n + be, k) * ipow(xm, k) * ipow(xp, n - k);
   return s;
 }
 
@@ -302,8 +330,8 @@ static double wigner_d_sin(int J, int M, int Mp, double w, int k) {
   }
   const double pref = std::exp(0.5 * (lfact(J + mp) + lfact(J - mp) - lfact(J + m) - lfact(J - m)));
   const double sh = std::sin(0.5 * w), ch = std::cos(0.5 * w);
-  const double val = pref * std::pow(sh, mp - m - k) * std::pow(ch, mp + m - k) * jacobi_poly(J - mp, mp - m, mp + m, std::cos(w));
-  return sign * val / std::pow(2.0, k);
+  const double val = pref * ipow(sh, mp - m - k) * ipow(ch, mp + m - k) * jacobi_poly(J - mp, mp - m, mp + m, std::cos(w));
+  return sign * std::ldexp(val, -k);
 }
 
 // (-1)^{M''-M'} 2/sqrt(2+2 d_{M''0}) F^{J tau}_{M'' M'}(0, w, 0), divided by sin(w)^k
@@ -601,12 +629,12 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
               const int Mp = c->Mps[iM], Mpp = c->Mps[jM];
               double ang;
               if (Mpp >= Mp) {
-                ang = std::pow(sin_t, Mpp - Mp) * coupling_K(J, S.tau, Mp, Mpp, w, 0);
+                ang = ipow(sin_t, Mpp - Mp) * coupling_K(J, S.tau, Mp, Mpp, w, 0);
               } else {
                 const int kk = Mp - Mpp;
-                ang = std::pow(std::fabs(ss) * x / yb, kk) * std::pow(sgnw, kk) * coupling_K(J, S.tau, Mp, Mpp, w, kk);
+                ang = ipow(std::fabs(ss) * x / yb, kk) * ipow(sgnw, kk) * coupling_K(J, S.tau, Mp, Mpp, w, kk);
               }
-              double wv = vs * rho * std::pow(rho, Mpp) * ang;
+              double wv = vs * rho * ipow(rho, Mpp) * ang;
               if (src.sym) wv *= S.exch_p * ((Mpp % 2 == 0) ? 1.0 : -1.0);
               if (!std::isfinite(wv)) bad_w = 1;
               wt[(((size_t)s * nM * nM) + (size_t)iM * nM + jM) * na + p] = wv;

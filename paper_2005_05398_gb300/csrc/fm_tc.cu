@@ -461,6 +461,24 @@ template <typename T>
 __device__ __forceinline__ void store_from_float(T* p, float v) { *p = (T)v; }
 template <>
 __device__ __forceinline__ void store_from_float<uint16_t>(uint16_t* p, float v) { *p = OpBF16::from(v); }
+// four consecutive elements in one or two vector stores (p aligned to four elements)
+template <typename T>
+__device__ __forceinline__ void store4_from_float(T* p, const float* v);
+template <>
+__device__ __forceinline__ void store4_from_float<float>(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store4_from_float<double>(double* p, const float* v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store4_from_float<uint16_t>(uint16_t* p, const float* v) {
+  const uint32_t lo = (uint32_t)OpBF16::from(v[0]) | ((uint32_t)OpBF16::from(v[1]) << 16);
+  const uint32_t hi = (uint32_t)OpBF16::from(v[2]) | ((uint32_t)OpBF16::from(v[3]) << 16);
+  *reinterpret_cast<uint2*>(p) = make_uint2(lo, hi);
+}
 
 // Byte offset of (row, byte within the 128-byte row) in a 128-byte-swizzled K-major tile whose base is
 // 1024-byte aligned: 8-row atoms of 1024 bytes, the 16-byte chunks of row r permuted by XOR with r mod 8.
@@ -511,6 +529,7 @@ struct TcZArgs {
   int tiles_i, tiles_j;
   int kblocks;         // 128-byte K blocks of A and B
   int ksteps;          // MMA instructions per tile
+  int vec_out;         // output runs start on four-element boundaries (host-checked): vector stores
   int* err;
 };
 
@@ -626,9 +645,15 @@ __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMa
         const int j = j0 + c0 / 32;
         if (j < a.ny) {
           TO* o = out + a.off + (plane * a.ny + j) * a.nx + i0;
+          if (a.vec_out) {  // n_x is a multiple of 4: each group of four is wholly inside or outside
 #pragma unroll
-          for (int e = 0; e < 32; ++e)
-            if (i0 + e < a.nx) store_from_float<TO>(o + e, v[e]);
+            for (int e = 0; e < 32; e += 4)
+              if (i0 + e < a.nx) store4_from_float<TO>(o + e, v + e);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+              if (i0 + e < a.nx) store_from_float<TO>(o + e, v[e]);
+          }
         }
       } else {  // two runs of 16 consecutive j at i = i0 + c0 / 16, + 1
 #pragma unroll
@@ -636,9 +661,15 @@ __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMa
           const int i = i0 + c0 / 16 + h;
           if (i >= a.nx) continue;
           TO* o = out + a.off + (plane * a.nx + i) * a.ny + j0;
+          if (a.vec_out) {  // n_y is a multiple of 4
 #pragma unroll
-          for (int e = 0; e < 16; ++e)
-            if (j0 + e < a.ny) store_from_float<TO>(o + e, v[16 * h + e]);
+            for (int e = 0; e < 16; e += 4)
+              if (j0 + e < a.ny) store4_from_float<TO>(o + e, v + 16 * h + e);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              if (j0 + e < a.ny) store_from_float<TO>(o + e, v[16 * h + e]);
+          }
         }
       }
     }
@@ -1172,6 +1203,10 @@ static int tcz_launch(fm_ctx* c, const Comp& cp, const CUtensorMap& tm, const vo
   a.tiles_j = (cp.ny + TJ_ - 1) / TJ_;
   a.kblocks = (cp.nz + Op::kRow - 1) / Op::kRow;
   a.ksteps = (cp.nz + Op::kStep - 1) / Op::kStep;
+  // a run of four output elements starts at a multiple of 4 of the component's elements when the run
+  // dimension (n_x forward, n_y inverse), the component offset and the base address allow it
+  a.vec_out = ((OUT_JI ? cp.nx : cp.ny) % 4 == 0) && (cp.off % 4 == 0) &&
+              ((uintptr_t)out % (4 * sizeof(TO)) == 0 || ((uintptr_t)out % 16 == 0 && sizeof(TO) == 8));
   a.err = c->tc_err;
   const size_t smem = tcz_smem(a.kblocks);
   const int per_sm = std::max(1, std::min(4, (int)(232448 / (smem + 1024))));

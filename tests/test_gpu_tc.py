@@ -31,6 +31,9 @@ BF16_CASES = {
     "he_l0_rows136y": dict(nint=(36, 68, 3), R=(20.0, 17.0)),     # fused chain, 2 row tiles in y
     "he_l0_wide": dict(nint=(128, 128, 2), R=(20.0, 17.0)),       # n = 256: fused in BF16
     "he_l1_banded": dict(J=1, nint=(12, 8, 4), R=(20.0, 17.0)),   # n_M = 2: banded y, TF32 x stages
+    # n_x = 24, n_y = 16: the fused BF16 chain on a grid whose sparse LU (the oracle's eigen-solve)
+    # takes seconds; the two-row-tile grids above have 1.6e5 unknowns and 2e7 nonzeros
+    "he_l0_small": dict(nint=(12, 8, 3), R=(20.0, 17.0)),
 }
 
 
@@ -64,13 +67,15 @@ def test_tc_eligibility(pkg):
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("y_solver", [0, 1])
-def test_tc_precond_close_to_fp64(pkg, name, y_solver):
+@pytest.mark.parametrize("tc_chain", [0, 1])
+def test_tc_precond_close_to_fp64(pkg, name, y_solver, tc_chain):
     """TF32 tensor-core chain (z stages, fused or unfused x / y stages, banded y solves) against the float64
-    chain, which is itself equal to the paper's literal form (test_gpu_parity)."""
+    chain, which is itself equal to the paper's literal form (test_gpu_parity); tc_chain 0 is the chain with
+    tensor-core z stages and the fused per-slab x / y stages, 1 the chain with SIMT z stages."""
     wl = _wl(name)
     E = wl["shift"] + 0.011
     ref_ctx = pkg.Context(wl, precision=0, y_solver=y_solver)
-    tc = pkg.Context(wl, precision=1, mma=2, y_solver=y_solver)
+    tc = pkg.Context(wl, precision=1, mma=2, y_solver=y_solver, tc_chain=tc_chain)
     simt = pkg.Context(wl, precision=1, mma=1, y_solver=y_solver)
     v = _dev(rand_vec(ref_ctx.n, 21))
     out = {}
@@ -114,8 +119,10 @@ def test_tc_computed_z_inverts_fmfin(pkg):
     assert err < 5e-2
 
 
-@pytest.mark.parametrize("precision", [1, 2])
-def test_tc_solve_matches_sparse_lu(pkg, precision):
+@pytest.mark.parametrize("precision,tc_chain,gram_schmidt", [(1, 0, 0), (2, 0, 0), (1, 1, 0), (1, 0, 1), (2, 1, 1)])
+def test_tc_solve_matches_sparse_lu(pkg, precision, tc_chain, gram_schmidt):
+    """FGMRES with the TF32 preconditioner (either tensor-core chain; CGS2 or single-pass DGKS
+    orthogonalisation) reaches the sparse-LU solution of Eq. FM-lin."""
     from oracle.system import FMSystem
     from oracle import solvers
     wl = workload("he_l0_24x24x8", nint=(10, 12, 4), R=(20.0, 17.0))
@@ -124,12 +131,31 @@ def test_tc_solve_matches_sparse_lu(pkg, precision):
     E = -2.5
     b = rand_vec(s.N, 23)
     ref = solvers.solve(H, S, E, b)
-    ctx = pkg.Context(wl, precision=precision, mma=2, restart_m=40)
+    ctx = pkg.Context(wl, precision=precision, mma=2, restart_m=40, tc_chain=tc_chain, gram_schmidt=gram_schmidt)
     x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
     info = ctx.fm_solve(E, _dev(b), x)
     got = x.cpu().numpy()
     assert info["converged"] == 1 and info["resid"] <= 1e-12
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8
+
+
+@pytest.mark.parametrize("mixed_scheme", [0, 1])
+def test_mixed_schemes_match_sparse_lu(pkg, mixed_scheme):
+    """FM_PREC_MIXED, flexible inner-outer scheme (float64 FGMRES over float32 FGMRES preconditioner steps)
+    and iterative refinement: both reach the float64 tolerance and the sparse-LU solution of Eq. FM-lin."""
+    from oracle.system import FMSystem
+    from oracle import solvers
+    wl = workload("he_l0_24x24x8", nint=(10, 12, 4), R=(20.0, 17.0))
+    s = FMSystem(wl)
+    E = -2.5
+    b = rand_vec(s.N, 29)
+    ref = solvers.solve(s.H(), s.S(), E, b)
+    ctx = pkg.Context(wl, precision=2, mma=2, restart_m=40, mixed_scheme=mixed_scheme)
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    info = ctx.fm_solve(E, _dev(b), x)
+    print("mixed scheme", mixed_scheme, info)
+    assert info["converged"] == 1 and info["resid"] <= 1e-12
+    assert np.linalg.norm(x.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-8
 
 
 @pytest.mark.parametrize("name,k,precision", [("he_l1_banded", 2, 1), ("psm_l2", 2, 2), ("he_l1_banded", 2, 2)])
@@ -199,7 +225,7 @@ def test_bf16_solve_matches_sparse_lu(pkg, precision):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8
 
 
-@pytest.mark.parametrize("name,k,precision", [("he_l0_rows136", 2, 1), ("he_l1_banded", 2, 2)])
+@pytest.mark.parametrize("name,k,precision", [("he_l0_small", 2, 1), ("he_l0_small", 2, 2), ("he_l1_banded", 2, 2)])
 def test_bf16_eigs_match_oracle(pkg, name, k, precision):
     from oracle.system import FMSystem
     from oracle import solvers
