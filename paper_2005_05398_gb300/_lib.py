@@ -36,7 +36,7 @@ class fm_opts(ctypes.Structure):
                 ("ncv", c_int), ("max_restarts", c_int), ("eig_tol", c_double), ("z_eigs", c_int),
                 ("y_solver", c_int), ("tune", c_int), ("mma", c_int), ("start_filter", c_int),
                 ("refine", c_int), ("inner_tol32", c_double), ("tc_chain", c_int), ("gram_schmidt", c_int),
-                ("mixed_scheme", c_int), ("device", c_int), ("stream", c_void_p)]
+                ("mixed_scheme", c_int), ("z_tile", c_int), ("device", c_int), ("stream", c_void_p)]
 
 
 class fm_info(ctypes.Structure):

@@ -28,7 +28,9 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "fm_internal.h"
@@ -512,14 +514,16 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 // z mode products on the tensor cores (Eq. prec-2, the W-bar_z and W_z stages):
 //   out[M'][l][p] = sum_k W[M'][l][k] in[M'][k][p]
 // for every point p = (i, j) of a component.  A = W (rows l, K = k; n_z <= 128, TMA-loaded,
-// zero-filled to 128 rows and to the K padding), B = a tile of 128 points (rows) with their n_z values
-// (K), converted from the input type while it is written into shared memory, D in tensor memory
-// (128 lanes l x 128 columns p).  Persistent CTAs walk the (M', point tile) list.
-//   OUT_JI (forward):  in x[M'][k][i][j] -> out t[slab][j][i]; tiles of 32 i x 4 j, B row = jj * 32 + ii
-//   !OUT_JI (inverse): in u[slab][j][i] (IN_JI) or t[slab][i][j] -> out y[M'][k][i][j]; tiles of 8 i x 16 j,
-//                      B row = ii * 16 + jj
-// (slab = M' * n_z + l).  Each thread of the epilogue owns one output plane l and writes runs of 32
-// (forward) or 16 (inverse) consecutive elements of it.
+// zero-filled to 128 rows and to the K padding), B = a tile of NP points (rows; NP = 128, 64 or 32) with
+// their n_z values (K), converted from the input type while it is written into shared memory, D in tensor
+// memory (128 lanes l x NP columns p).  Persistent CTAs walk the (M', point tile) list.
+//   OUT_JI (forward):  in x[M'][k][i][j] -> out t[slab][j][i]; tiles of NP/4 i x 4 j, B row = jj * TI + ii
+//   !OUT_JI (inverse): in u[slab][j][i] (IN_JI) or t[slab][i][j] -> out y[M'][k][i][j]; tiles of 8 i x NP/8 j,
+//                      B row = ii * TJ + jj
+// (slab = M' * n_z + l).  Loads run along the input's contiguous index (runs of 4 j forward, 8 i inverse),
+// stores along the output's (runs of TI i forward, TJ j inverse).  Smaller tiles give more CTAs per SM,
+// hence more loads in flight per SM; the tile width is chosen per shape by the set-up's autotuner.  Each
+// thread of the epilogue owns one output plane l.
 // ---------------------------------------------------------------------------
 struct TcZArgs {
   const void* in;
@@ -533,18 +537,27 @@ struct TcZArgs {
   int* err;
 };
 
-template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI>
+template <bool OUT_JI, int NP>
+struct ZTile {
+  static constexpr int TI = OUT_JI ? NP / 4 : 8;   // i extent of a tile
+  static constexpr int TJ = OUT_JI ? 4 : NP / 8;   // j extent
+};
+
+template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI, int NP>
 __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMap tmW, const TcZArgs a) {
   static_assert(!(OUT_JI && IN_JI), "the forward stage reads x[M'][k][i][j]");
+  static_assert(NP == 128 || NP == 64 || NP == 32, "tile of 128, 64 or 32 points");
   using TB = typename Op::T;
-  constexpr int TI_ = OUT_JI ? 32 : 8, TJ_ = OUT_JI ? 4 : 16;
-  constexpr int kTile = 128 * 128;  // bytes of one K block (128 rows x 128 bytes)
+  constexpr int TI_ = ZTile<OUT_JI, NP>::TI, TJ_ = ZTile<OUT_JI, NP>::TJ;
+  constexpr int kTileA = 128 * 128;  // bytes of one K block of A (128 rows x 128 bytes)
+  constexpr int kTileB = NP * 128;   // of B (NP rows)
+  constexpr int kTpp = 128 / NP;     // threads per point of the tile (each loads every kTpp-th k)
   extern __shared__ unsigned char tz_smem[];
   const uint32_t raw = smem_u32(tz_smem);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = tz_smem + (base - raw);
-  const uint32_t sA = base, sB = base + (uint32_t)a.kblocks * kTile;
-  const uint32_t bars = sB + (uint32_t)a.kblocks * kTile;
+  const uint32_t sA = base, sB = base + (uint32_t)a.kblocks * kTileA;
+  const uint32_t bars = sB + (uint32_t)a.kblocks * kTileB;
   const uint32_t abar = bars, mdone = bars + 8, slot = bars + 16;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bars - base) + 24);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
@@ -555,7 +568,7 @@ __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMa
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(128) : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(NP) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
@@ -569,42 +582,44 @@ __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMa
   TO* out = static_cast<TO*>(a.out);
   int cur_iM = -1, a_loads = 0;
   uint32_t a_phase = 0, m_phase = 0;
-  // thread -> point of the tile for coalesced loads (the contiguous index runs across lanes)
-  const int ii = IN_JI ? tid % TI_ : tid / TJ_;
-  const int jj = IN_JI ? tid / TI_ : tid % TJ_;
+  // thread -> (point of the tile, k residue): consecutive threads take consecutive points along the
+  // input's contiguous index, so that a warp's loads are coalesced runs
+  const int pt = tid % NP, ksub = tid / NP;
+  const int ii = IN_JI ? pt % TI_ : pt / TJ_;
+  const int jj = IN_JI ? pt / TI_ : pt % TJ_;
   const int prow = OUT_JI ? jj * TI_ + ii : ii * TJ_ + jj;
   for (int q = blockIdx.x; q < ntiles * a.nM; q += gridDim.x) {
     const int iM = q / ntiles, t = q - iM * ntiles;
     const int i0 = (t / a.tiles_j) * TI_, j0 = (t % a.tiles_j) * TJ_;
     const bool reload = iM != cur_iM;
     if (reload && tid == 0) {  // W of this M' (every thread of the previous tile has passed the MMA wait)
-      mbar_expect_tx(abar, (uint32_t)a.kblocks * kTile);
-      for (int kb = 0; kb < a.kblocks; ++kb) tma_load_3d(sA + kb * kTile, &tmW, kb * Op::kRow, 0, iM, abar);
+      mbar_expect_tx(abar, (uint32_t)a.kblocks * kTileA);
+      for (int kb = 0; kb < a.kblocks; ++kb) tma_load_3d(sA + kb * kTileA, &tmW, kb * Op::kRow, 0, iM, abar);
     }
     if (reload) {
       cur_iM = iM;
       ++a_loads;
     }
-    // B tile: row prow, K = k
+    // B tile: row prow, K = k (this thread: k = ksub, ksub + kTpp, ...)
     {
       const int i = i0 + ii, j = j0 + jj;
       const bool ok = i < a.nx && j < a.ny;
       const int64_t src = IN_JI ? a.off + ((int64_t)iM * a.nz * a.ny + j) * a.nx + i
                                 : a.off + ((int64_t)iM * a.nz * a.nx + i) * a.ny + j;
-      // 32 loads in flight per thread (two round trips to memory for n_z <= 64)
-      for (int k0 = 0; k0 < kpad; k0 += 32) {
+      // 32 loads in flight per thread
+      for (int k0 = ksub; k0 < kpad; k0 += 32 * kTpp) {
         float v[32];
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
-          const int k = k0 + u;
+          const int k = k0 + u * kTpp;
           v[u] = (ok && k < a.nz) ? load_as_float<TI>(in + src + (int64_t)k * nxy) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
-          const int k = k0 + u;
+          const int k = k0 + u * kTpp;
           if (k < kpad) {
             const int kb = k / Op::kRow, byte = (k % Op::kRow) * (int)sizeof(TB);
-            st_elem<Op>(sB + kb * kTile + sw128(prow, byte), v[u]);
+            st_elem<Op>(sB + kb * kTileB + sw128(prow, byte), v[u]);
           }
         }
       }
@@ -619,11 +634,12 @@ __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMa
       }
       if (ok) {
         tc_fence_after();
-        const uint32_t id = Op::idesc(128);
+        const uint32_t id = Op::idesc(NP);
         for (int ks = 0; ks < a.ksteps; ++ks) {
           const int kb = (ks * Op::kStep) / Op::kRow, kin = (ks * Op::kStep) % Op::kRow;
-          const uint32_t off = (uint32_t)(kb * kTile) + (uint32_t)(kin * (int)sizeof(TB));
-          Op::mma(tmem, sw128_desc(sA + off), sw128_desc(sB + off), id, ks ? 1u : 0u);
+          const uint32_t kbyte = (uint32_t)(kin * (int)sizeof(TB));
+          Op::mma(tmem, sw128_desc(sA + (uint32_t)(kb * kTileA) + kbyte), sw128_desc(sB + (uint32_t)(kb * kTileB) + kbyte),
+                  id, ks ? 1u : 0u);
         }
       }
       mma_commit(mdone);  // arrives when the MMAs above (if any) have completed
@@ -636,39 +652,44 @@ __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMa
     if (__syncthreads_or(*abort_flag)) break;
     // epilogue: thread = output plane l (its TMEM lane), 32 columns (points) per load
     const int l = warp * 32 + lane;
-    for (int c0 = 0; c0 < 128; c0 += 32) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < NP; c0 += 32) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
       if (l >= a.nz) continue;
       const int64_t plane = (int64_t)iM * a.nz + l;
-      if (OUT_JI) {  // 32 consecutive i at j = j0 + c0 / 32
-        const int j = j0 + c0 / 32;
-        if (j < a.ny) {
+      if (OUT_JI) {  // 32 / TI runs of TI consecutive i, at j = j0 + (c0 + r * TI) / TI
+#pragma unroll
+        for (int r = 0; r < 32 / TI_; ++r) {
+          const int j = j0 + (c0 + r * TI_) / TI_;
+          if (j >= a.ny) continue;
           TO* o = out + a.off + (plane * a.ny + j) * a.nx + i0;
+          const float* w = v + r * TI_;
           if (a.vec_out) {  // n_x is a multiple of 4: each group of four is wholly inside or outside
 #pragma unroll
-            for (int e = 0; e < 32; e += 4)
-              if (i0 + e < a.nx) store4_from_float<TO>(o + e, v + e);
+            for (int e = 0; e < TI_; e += 4)
+              if (i0 + e < a.nx) store4_from_float<TO>(o + e, w + e);
           } else {
 #pragma unroll
-            for (int e = 0; e < 32; ++e)
-              if (i0 + e < a.nx) store_from_float<TO>(o + e, v[e]);
+            for (int e = 0; e < TI_; ++e)
+              if (i0 + e < a.nx) store_from_float<TO>(o + e, w[e]);
           }
         }
-      } else {  // two runs of 16 consecutive j at i = i0 + c0 / 16, + 1
+      } else {  // 32 / TJ runs of TJ consecutive j, at i = i0 + (c0 + r * TJ) / TJ
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int i = i0 + c0 / 16 + h;
+        for (int r = 0; r < 32 / TJ_; ++r) {
+          const int i = i0 + (c0 + r * TJ_) / TJ_;
           if (i >= a.nx) continue;
           TO* o = out + a.off + (plane * a.nx + i) * a.ny + j0;
+          const float* w = v + r * TJ_;
           if (a.vec_out) {  // n_y is a multiple of 4
 #pragma unroll
-            for (int e = 0; e < 16; e += 4)
-              if (j0 + e < a.ny) store4_from_float<TO>(o + e, v + 16 * h + e);
+            for (int e = 0; e < TJ_; e += 4)
+              if (j0 + e < a.ny) store4_from_float<TO>(o + e, w + e);
           } else {
 #pragma unroll
-            for (int e = 0; e < 16; ++e)
-              if (j0 + e < a.ny) store_from_float<TO>(o + e, v[16 * h + e]);
+            for (int e = 0; e < TJ_; ++e)
+              if (j0 + e < a.ny) store_from_float<TO>(o + e, w[e]);
           }
         }
       }
@@ -681,7 +702,7 @@ __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMa
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NP) : "memory");
   }
   if (tid == 0 && *abort_flag) atomicExch(a.err, 1);
 }
@@ -1019,7 +1040,7 @@ int fused_stages(int nx, int ny, int row_elems) {
   return 0;
 }
 
-size_t tcz_smem(int kblocks) { return 1024 + (size_t)2 * kblocks * 16384 + 64; }
+size_t tcz_smem(int kblocks, int np) { return 1024 + (size_t)kblocks * 16384 + (size_t)kblocks * np * 128 + 64; }
 
 int tmem_cols(int nb) {
   int c = 32;
@@ -1045,6 +1066,8 @@ bool tc_component_ok(const Comp& cp) {
 static bool bf16_component_ok(const Comp& cp) {
   return tc_component_ok(cp) && cp.nx % 8 == 0 && cp.ny % 8 == 0 && cp.nz <= 128;
 }
+
+static int tcz_autotune(fm_ctx* c);
 
 int tc_setup(fm_ctx* c) {
   c->tc_active = false;
@@ -1098,12 +1121,18 @@ int tc_setup(fm_ctx* c) {
   }
   c->bf16 = want_bf16;
   c->tc_active = true;
-  return FM_OK;
+  return tcz_autotune(c);
 }
 
 template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI>
 static cudaError_t tcz_attr() {
-  return cudaFuncSetAttribute(k_tc_z<TI, Op, TO, OUT_JI, IN_JI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_z<TI, Op, TO, OUT_JI, IN_JI, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_z<TI, Op, TO, OUT_JI, IN_JI, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_z<TI, Op, TO, OUT_JI, IN_JI, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return e;
 }
 
 int tc_kernels_init() {
@@ -1188,8 +1217,8 @@ int zstage(fm_ctx* c, const Comp& cp, const float* W, const TI* in, TO* out) {
 
 // z stages on the tensor cores.  Forward: x -> t[slab][j][i] (BF16 storage when 'to_bf16', ahead of the fused
 // BF16 chain).  Inverse: u[slab][j][i] (fused chain, 'in_ji') or t[slab][i][j] (unfused) -> y.
-template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI>
-static int tcz_launch(fm_ctx* c, const Comp& cp, const CUtensorMap& tm, const void* in, void* out) {
+template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI, int NP>
+static int tcz_launch_np(fm_ctx* c, const Comp& cp, const CUtensorMap& tm, const void* in, void* out) {
   TcZArgs a;
   a.in = in;
   a.out = out;
@@ -1198,7 +1227,7 @@ static int tcz_launch(fm_ctx* c, const Comp& cp, const CUtensorMap& tm, const vo
   a.ny = cp.ny;
   a.nM = c->nM;
   a.off = cp.off;
-  const int TI_ = OUT_JI ? 32 : 8, TJ_ = OUT_JI ? 4 : 16;
+  const int TI_ = ZTile<OUT_JI, NP>::TI, TJ_ = ZTile<OUT_JI, NP>::TJ;
   a.tiles_i = (cp.nx + TI_ - 1) / TI_;
   a.tiles_j = (cp.ny + TJ_ - 1) / TJ_;
   a.kblocks = (cp.nz + Op::kRow - 1) / Op::kRow;
@@ -1208,17 +1237,28 @@ static int tcz_launch(fm_ctx* c, const Comp& cp, const CUtensorMap& tm, const vo
   a.vec_out = ((OUT_JI ? cp.nx : cp.ny) % 4 == 0) && (cp.off % 4 == 0) &&
               ((uintptr_t)out % (4 * sizeof(TO)) == 0 || ((uintptr_t)out % 16 == 0 && sizeof(TO) == 8));
   a.err = c->tc_err;
-  const size_t smem = tcz_smem(a.kblocks);
-  const int per_sm = std::max(1, std::min(4, (int)(232448 / (smem + 1024))));
+  const size_t smem = tcz_smem(a.kblocks, NP);
+  // CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA), tensor memory (512 columns), at most 8
+  const int per_sm = std::max(1, std::min({8, 512 / NP, (int)(233472 / (smem + 1024))}));
   const int tiles = a.tiles_i * a.tiles_j * c->nM;
   const int grid = std::max(1, std::min(tiles, 152 * per_sm));
   const double nun = (double)cp.nx * cp.ny * cp.nz * c->nM;
   const int tk_ = prof_begin(c, FM_KERNEL_ZMIX);
-  k_tc_z<TI, Op, TO, OUT_JI, IN_JI><<<grid, 128, smem, c->stream>>>(tm, a);
+  k_tc_z<TI, Op, TO, OUT_JI, IN_JI, NP><<<grid, 128, smem, c->stream>>>(tm, a);
   prof_end(c, tk_, 2.0 * cp.nz * nun, nun * (double)(sizeof(TI) + sizeof(TO)));
   c->launches++;
   FM_CUDA(cudaGetLastError());
   return FM_OK;
+}
+
+// the component's z-stage tile width for this direction (set by the autotuner, or by fm_opts.z_tile)
+template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI>
+static int tcz_launch(fm_ctx* c, const Comp& cp, const CUtensorMap& tm, const void* in, void* out) {
+  switch (cp.tcz_np[OUT_JI ? 0 : 1]) {
+    case 32: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 32>(c, cp, tm, in, out);
+    case 64: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 64>(c, cp, tm, in, out);
+    default: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 128>(c, cp, tm, in, out);
+  }
 }
 
 bool tc_uses_ydiag(const fm_ctx* c, const Comp& cp) {
@@ -1335,6 +1375,108 @@ int precond_tc_back(fm_ctx* c, TIO* y) {
     if (rc) return rc;
   }
   return FM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the z-stage tile width (128, 64 or 32 points per tensor-core tile).  For each component and
+// direction it times every width on the context's own buffers (CUDA events on the context's stream, one
+// untimed launch, then the mean of three) and keeps the fastest.  Results are cached per shape (n_x, n_y,
+// n_z, n_M, operand type, input / output type, fused or not), so contexts of the same shape -- the request
+// loop's, a test's -- reuse them.  fm_opts.z_tile fixes the width instead.
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+  int nx, ny, nz, nM, bf16, fused, tio, dir;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(nx, ny, nz, nM, bf16, fused, tio, dir) < std::tie(o.nx, o.ny, o.nz, o.nM, o.bf16, o.fused, o.tio, o.dir);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+template <typename TIO>
+int tcz_run(fm_ctx* c, Comp& cp, int dir, const TIO* x, TIO* y) {
+  const bool fz = tc_uses_ydiag(c, cp) && cp.fused;
+  if (dir == 0) return zfwd<TIO>(c, cp, x, fz && c->bf16);
+  if (fz)
+    return !c->bf16 ? tcz_launch<float, OpTF32, TIO, false, true>(c, cp, cp.tmz[1], c->u32, y)
+                    : tcz_launch<uint16_t, OpBF16, TIO, false, true>(c, cp, cp.tmz[1], c->u32, y);
+  return !c->bf16 ? tcz_launch<float, OpTF32, TIO, false, false>(c, cp, cp.tmz[1], c->t32, y)
+                  : tcz_launch<float, OpBF16, TIO, false, false>(c, cp, cp.tmz[1], c->t32, y);
+}
+
+template <typename TIO>
+int tcz_tune_comp(fm_ctx* c, Comp& cp, const TIO* x, TIO* y) {
+  cudaEvent_t e0, e1;
+  FM_CUDA(cudaEventCreate(&e0));
+  FM_CUDA(cudaEventCreate(&e1));
+  int rc = FM_OK;
+  for (int dir = 0; dir < 2 && rc == FM_OK; ++dir) {
+    const TuneKey key{cp.nx, cp.ny, cp.nz, c->nM, c->bf16 ? 1 : 0, (tc_uses_ydiag(c, cp) && cp.fused) ? 1 : 0,
+                      (int)sizeof(TIO), dir};
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) {
+        cp.tcz_np[dir] = it->second;
+        continue;
+      }
+    }
+    float best = 1e30f;
+    int best_np = 128;
+    for (int np : {128, 64, 32}) {
+      cp.tcz_np[dir] = np;
+      if ((rc = tcz_run<TIO>(c, cp, dir, x, y))) break;
+      if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = FM_ERR_CUDA; break; }
+      for (int r = 0; r < 3 && rc == FM_OK; ++r) rc = tcz_run<TIO>(c, cp, dir, x, y);
+      if (rc) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = FM_ERR_CUDA;
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        best_np = np;
+      }
+    }
+    cp.tcz_np[dir] = best_np;
+    if (rc == FM_OK) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = best_np;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+}  // namespace
+
+static int tcz_autotune(fm_ctx* c) {
+  const int fixed = c->opts.z_tile;
+  bool any = false;
+  for (auto& cp : c->comps) {
+    cp.tcz_np[0] = cp.tcz_np[1] = fixed ? fixed : 128;
+    any = any || cp.tcz;
+  }
+  if (fixed || !any) return FM_OK;
+  // scratch: x and y in the float64 vector u64 (the float32 form in its first half), inputs zeroed
+  FM_CUDA(cudaMemsetAsync(c->u64, 0, (size_t)c->N * sizeof(double), c->stream));
+  FM_CUDA(cudaMemsetAsync(c->u32, 0, (size_t)c->N * sizeof(float), c->stream));
+  FM_CUDA(cudaMemsetAsync(c->t32, 0, (size_t)c->N * sizeof(float), c->stream));
+  int rc = FM_OK;
+  for (auto& cp : c->comps) {
+    if (!cp.tcz) continue;
+    if (c->opts.precision == FM_PREC_MIXED) {
+      float* v = reinterpret_cast<float*>(c->u64);
+      rc = tcz_tune_comp<float>(c, cp, v, v);
+    } else {
+      rc = tcz_tune_comp<double>(c, cp, c->u64, c->u64);
+    }
+    if (rc) return rc;
+  }
+  return tc_check(c);
 }
 
 template int precond_tc_front<double>(fm_ctx*, const double*, std::vector<Comp*>*);

@@ -93,6 +93,28 @@ def test_tc_precond_close_to_fp64(pkg, name, y_solver, tc_chain):
     assert e_tc < TF32_REL, name
 
 
+@pytest.mark.parametrize("name,mma", [("he_l0_rows132", 2), ("he_l1_banded", 2), ("psm_l2", 2), ("he_l0_rows136", 3)])
+def test_z_tile_widths_agree_bitwise(pkg, name, mma):
+    """The z-stage tile width (points per tensor-core tile: 128, 64, 32, or the autotuner's choice) changes
+    only which points share an MMA, not the K accumulation of any output element: every width gives the
+    same preconditioner output bit for bit (an index or layout error in a narrow tile does not)."""
+    wl = workload("he_l0_24x24x8", **(BF16_CASES[name] if mma == 3 else CASES[name]))
+    E = wl["shift"] + 0.011
+    out = {}
+    for zt in (128, 64, 32, 0):
+        c = pkg.Context(wl, precision=1, mma=mma, z_tile=zt)
+        c.fm_set_shift(E)
+        v = _dev(rand_vec(c.n, 31))
+        y = torch.empty_like(v)
+        c.fm_precond_apply(v, y)
+        torch.cuda.synchronize()
+        out[zt] = y
+        c.close()
+    assert torch.isfinite(out[128]).all()
+    for zt in (64, 32, 0):
+        assert torch.equal(out[zt], out[128]), (name, zt, (out[zt] - out[128]).abs().max().item())
+
+
 def test_tc_computed_z_inverts_fmfin(pkg):
     """n_M = 1, computed z eigenvalues: the preconditioner is the exact inverse of Eq. FM-fin's left
     operator, so P^{-1} L v returns v to TF32 accuracy through the tensor-core chain."""
