@@ -86,7 +86,7 @@ static int fgmres32(fm_ctx* c, double E, const float* b, float* d, double tol, i
 // Relative residual of each float32 inner solve in FM_PREC_MIXED (0 selects the scheme's default).
 static double inner_tol32(const fm_ctx* c) {
   if (c->opts.inner_tol32 > 0.0) return c->opts.inner_tol32;
-  return c->opts.mixed_scheme == 0 ? 1e-2 : 3e-5;
+  return c->opts.mixed_scheme == 0 ? 1e-3 : 3e-5;
 }
 
 // Preconditioner step of the flexible scheme: z <- float32 FGMRES solution of (H - E S) z = v for a unit

@@ -483,8 +483,17 @@ int decompose_pairs(int n, const double* A1, const double* A2, int top, double* 
       ++c;
     } else {
       if (c + 1 >= n) return -1;
-      // phase so that the value at z = 1 (coefficient 'top') is real and positive
-      const cplx f(Vr[(size_t)top * n + e], Vi[(size_t)top * n + e]);
+      // phase so that coefficient 'top' (the value at z = 1 for the z axis; the largest coefficient when
+      // top < 0) is real and positive
+      int tp = top;
+      if (tp < 0) {
+        tp = 0;
+        for (int i = 1; i < n; ++i)
+          if (std::hypot(Vr[(size_t)i * n + e], Vi[(size_t)i * n + e]) >
+              std::hypot(Vr[(size_t)tp * n + e], Vi[(size_t)tp * n + e]))
+            tp = i;
+      }
+      const cplx f(Vr[(size_t)tp * n + e], Vi[(size_t)tp * n + e]);
       if (std::abs(f) == 0.0) return -1;
       const cplx ph = std::conj(f) / std::abs(f);
       for (int i = 0; i < n; ++i) {

@@ -38,7 +38,8 @@ int decompose(int n, const double* A1, const double* A2, bool descending,
 // Like decompose(), descending, for pencils that may have complex-conjugate eigenvalue pairs:
 // a pair contributes two real columns, the real and imaginary parts of the eigenvector of the
 // member with positive imaginary part, phased so that its coefficient 'top' is real positive
-// (kind = 1 and 2; real eigenvalues kind = 0; lam = real parts).  W-bar = (A2 W)^{-1}, so
+// (kind = 1 and 2; real eigenvalues kind = 0; lam = real parts; top < 0: the largest coefficient
+// is made real positive).  W-bar = (A2 W)^{-1}, so
 // W-bar A2 W = I and W-bar A1 W is block diagonal with 2x2 blocks for the pairs.
 int decompose_pairs(int n, const double* A1, const double* A2, int top, double* Wbar, double* W, double* lam,
                     int* kind);

@@ -126,6 +126,7 @@ struct Comp {
   CUtensorMap tmf[5];            // fused chain: slab t[slab][j][i], W-bar_x, W-bar_y, W_y, W_x
   bool tcz = false;              // z stages on the tensor cores
   int tcz_np[2] = {128, 128};    // their tile widths (points per tile), forward / inverse
+  int x_pair_ls = 0;             // x pencils (values of l) with complex-conjugate pairs, kept in a real basis
   bool fused = false;            // n_M = 1: x / y stages in one kernel per slab (with the y diagonalisation)
 };
 

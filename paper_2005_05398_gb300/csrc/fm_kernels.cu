@@ -505,17 +505,60 @@ __device__ __forceinline__ void copy_segments(int nseg, int valid, int pb, SrcF 
   for (int sg = t / pps; sg < nseg; sg += spr) cp_async_pb(dst(sg) + k * ep, src(sg) + k * ep, pb);
 }
 
+// w[p] for 0 <= p < N through a binary tree of selects (depth log2 N instead of a chain of N)
+template <typename T, int N>
+__device__ __forceinline__ T pick_window(const T* w, int p) {
+  T s[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) s[i] = w[i];
+  int n = N;
+#pragma unroll
+  for (int b = 0; (1 << b) < N; ++b) {
+    const bool hi = (p >> b) & 1;
+#pragma unroll
+    for (int i = 0; i < (N + 1) / 2; ++i)
+      if (i < (n + 1) / 2) s[i] = (hi && 2 * i + 1 < n) ? s[2 * i + 1] : s[2 * i];
+    n = (n + 1) / 2;
+  }
+  return s[0];
+}
+
+// Row walker of a line: row r = j * n_c + c lives at P0 + c * DC + j * nx (DC the distance between the
+// chain's neighbouring M' components), stepped without divisions.
+template <typename T>
+struct RowPtr {
+  T* p;
+  int c, nc;
+  int64_t dc, nx;
+  __device__ __forceinline__ void next() {
+    p += dc;
+    if (++c == nc) {
+      c = 0;
+      p += nx - (int64_t)nc * dc;
+    }
+  }
+  __device__ __forceinline__ void prev() {
+    p -= dc;
+    if (--c < 0) {
+      c = nc - 1;
+      p -= nx - (int64_t)nc * dc;
+    }
+  }
+};
+
 // One line through the banded LU factors, in place on the line's entries in global memory: seg(r) is the
-// entry of row r of the CTA's first line, and this thread's line is tid entries further.  Every row of both sweeps streams through a shared-memory
-// ring filled a chunk ahead by cooperative cp.async: a ring row holds the row's factor slots and, in its
-// last slot, one line value -- the right-hand side entry x[r + KL + 1] that enters the forward window at
-// row r, or the forward result z[r] the backward sweep starts from.  The forward sweep keeps x[r .. r+KL]
-// in a register window (the pivot swap is a select over the window) and writes z[r] back; the backward
-// sweep keeps the KL+KU solved values x[r+1 ..] in registers, adds the newest one last and writes x[r].
+// entry of row r of the CTA's first line, and this thread's line is tid entries further.  Every row of both
+// sweeps streams through a shared-memory ring filled a chunk ahead by cooperative cp.async: a ring row holds
+// the row's factor slots and, in its last slot, one line value -- the right-hand side entry x[r + KL + 1]
+// that enters the forward window at row r, or the forward result z[r] the backward sweep starts from.  The
+// forward sweep keeps x[r .. r+KL] in a register window (the pivot row is picked from it by a select tree,
+// its index read one row ahead) and writes z[r] back; the backward sweep keeps the KL+KU solved values
+// x[r+1 ..] in registers (four independent FMA chains), adds the newest one last and writes x[r].  The
+// rows' addresses are walked (RowPtr) rather than recomputed.
 template <typename T, int LPB, int KL, typename SegF>
 __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* __restrict__ Ub, int64_t nx, int n,
-                                            int R, SegF seg, T* ring, int Wring, int tid, bool live, int valid,
-                                            int pb) {
+                                            int R, SegF seg, RowPtr<T> rp0, T* ring, int Wring, int tid, bool live,
+                                            int valid, int pb) {
   constexpr int W = 2 * KL + 1;
   const int nch = (n + R - 1) / R;
   const int RS = Wring + 1;  // slots per ring row (factor slots + the line value)
@@ -536,6 +579,7 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
   T w[KL + 1];
 #pragma unroll
   for (int i = 0; i <= KL; ++i) w[i] = (live && i < n) ? seg(i)[tid] : (T)0;
+  RowPtr<T> rp = rp0;  // row 0
   issue_f(0);
   for (int ch = 0; ch < nch; ++ch) {
     if (ch + 1 < nch) {
@@ -548,22 +592,23 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
     if (live) {
       const T* buf = ring + (ch & 1) * half;
       const int r0 = ch * R, rows = min(R, n - r0);
+      int p = (int)buf[tid];
       for (int q = 0; q < rows; ++q) {
         const int r = r0 + q;
         const T* f = buf + (size_t)q * RS * LPB + tid;
-        const int p = (int)f[0];
-        T xr = w[0];
-#pragma unroll
-        for (int i = 1; i <= KL; ++i) xr = (p == i) ? w[i] : xr;
+        const int pn = (q + 1 < rows) ? (int)f[RS * LPB] : 0;  // next row's pivot offset, ahead of use
+        const T xr = pick_window<T, KL + 1>(w, p);
 #pragma unroll
         for (int i = 1; i <= KL; ++i)
           if (p == i) w[i] = w[0];
 #pragma unroll
         for (int d = 1; d <= KL; ++d) w[d] -= f[d * LPB] * xr;
-        seg(r)[tid] = xr;
+        rp.p[tid] = xr;
+        rp.next();
 #pragma unroll
         for (int i = 0; i < KL; ++i) w[i] = w[i + 1];
         w[KL] = (r + KL + 1 < n) ? f[Wring * LPB] : (T)0;
+        p = pn;
       }
     }
     __syncthreads();
@@ -586,6 +631,7 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
   T v[W - 1];
 #pragma unroll
   for (int i = 0; i < W - 1; ++i) v[i] = (T)0;
+  rp.prev();  // row n - 1
   issue_b(0);
   for (int ch = 0; ch < nch; ++ch) {
     if (ch + 1 < nch) {
@@ -599,15 +645,19 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
       const T* buf = ring + (ch & 1) * half;
       const int rows = min(R, n - ch * R);
       for (int q = 0; q < rows; ++q) {
-        const int r = n - 1 - (ch * R + q);
         const T* f = buf + (size_t)q * RS * LPB + tid;
-        T s0 = f[Wring * LPB], s1 = 0;
+        T s0 = f[Wring * LPB], s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
-        for (int d = 2; d < W; d += 2) s0 -= f[d * LPB] * v[d - 1];
+        for (int d = 2; d < W; d += 4) s0 -= f[d * LPB] * v[d - 1];
 #pragma unroll
-        for (int d = 3; d < W; d += 2) s1 -= f[d * LPB] * v[d - 1];
-        const T x = ((s0 + s1) - f[LPB] * v[0]) * f[0];
-        seg(r)[tid] = x;
+        for (int d = 3; d < W; d += 4) s1 -= f[d * LPB] * v[d - 1];
+#pragma unroll
+        for (int d = 4; d < W; d += 4) s2 -= f[d * LPB] * v[d - 1];
+#pragma unroll
+        for (int d = 5; d < W; d += 4) s3 -= f[d * LPB] * v[d - 1];
+        const T x = (((s0 + s1) + (s2 + s3)) - f[LPB] * v[0]) * f[0];
+        rp.p[tid] = x;
+        rp.prev();
 #pragma unroll
         for (int i = W - 2; i > 0; --i) v[i] = v[i - 1];
         v[0] = x;
@@ -653,9 +703,15 @@ __global__ void __launch_bounds__(LPB) k_ysolve(const YBatch<T> yb, int R, int W
   (void)maxn;
   const T* Lb = L + a.lmul_off[il] + ix0;
   const T* Ub = U + a.band_off[il] + ix0;
+  RowPtr<T> rp0;
+  rp0.p = seg(0);
+  rp0.c = 0;
+  rp0.nc = nc;
+  rp0.dc = (int64_t)(a.nz - 1) * a.ny * a.nx;  // (iM + 1, k - 1) from (iM, k): row r + 1 within one j
+  rp0.nx = a.nx;
   // band half-width of this chain (band_kl on the host; at most kMaxBandKL there)
   const int KLc = (nc == 1) ? a.kq : a.kq * nc + 1;
-#define FM_YS(KLV) ysolve_line<T, LPB, KLV>(Lb, Ub, a.nx, n, R, seg, ring, Wring, tid, live, valid, pb)
+#define FM_YS(KLV) ysolve_line<T, LPB, KLV>(Lb, Ub, a.nx, n, R, seg, rp0, ring, Wring, tid, live, valid, pb)
   switch (KLc) {
     case 2: FM_YS(2); break;
     case 4: FM_YS(4); break;

@@ -491,7 +491,7 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
   // z eigenvalues replace l(l+1): then they follow the z decompositions below)
   struct XD {
     std::vector<double> Wx, Wxb;
-    std::vector<int> err;
+    std::vector<int> err, pairs;
   };
   std::vector<XD> xd(c->comps.size());
   auto x_task = [&](const Comp& cp, int il, XD& d) {
@@ -509,6 +509,17 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
     Comp& cw = const_cast<Comp&>(cp);
     d.err[il] = fmh::decompose(nx, A1.data(), Sxd.data(), false, &d.Wxb[(size_t)il * nx * nx],
                                &d.Wx[(size_t)il * nx * nx], &cw.Lx[(size_t)il * nx]);
+    if (d.err[il] == -1) {
+      // complex-conjugate pairs (quintic collocation pencils, Section 4): each pair in a real basis (real and
+      // imaginary parts of its eigenvector), its real part as the diagonal value of both columns.  The
+      // preconditioner then leaves out the pair's 2 x 2 rotation (relative size |Im| / |Re + lambda_y +
+      // lambda_z - E|), an approximation of the tensor-trick inverse that FGMRES absorbs; the operator, and
+      // so every result, is unchanged.
+      std::vector<int> kind(nx);
+      d.err[il] = fmh::decompose_pairs(nx, A1.data(), Sxd.data(), -1, &d.Wxb[(size_t)il * nx * nx],
+                                       &d.Wx[(size_t)il * nx * nx], &cw.Lx[(size_t)il * nx], kind.data());
+      if (d.err[il] == 0) d.pairs[il] = 1;
+    }
   };
   const bool x_first = c->opts.z_eigs != 1;
   if (x_first) {
@@ -519,6 +530,7 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       xd[q].Wx.resize((size_t)cp.nl * cp.nx * cp.nx);
       xd[q].Wxb.resize((size_t)cp.nl * cp.nx * cp.nx);
       xd[q].err.assign(cp.nl, 0);
+      xd[q].pairs.assign(cp.nl, 0);
       cp.Lx.assign((size_t)cp.nl * cp.nx, 0.0);
       for (int il = 0; il < cp.nl; ++il) tasks.push_back({(int)q, il});
     }
@@ -730,6 +742,7 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       d.Wx.resize((size_t)nl * nx * nx);
       d.Wxb.resize((size_t)nl * nx * nx);
       d.err.assign(nl, 0);
+      d.pairs.assign(nl, 0);
       cp.Lx.assign((size_t)nl * nx, 0.0);
       parallel_for(nl, [&](int il) { x_task(cp, il, d); });
     }
@@ -737,6 +750,11 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       if (e == -1) return FM_ERR_COMPLEX_SPECTRUM;
       if (e != 0) return FM_ERR_NUMERIC;
     }
+    cp.x_pair_ls = 0;
+    for (int p : d.pairs) cp.x_pair_ls += p;
+    if (cp.x_pair_ls && getenv("FM_VERBOSE"))
+      fprintf(stderr, "[fm_setup] component %d: %d x pencils with complex-conjugate pairs (real basis)\n", cp.label,
+              cp.x_pair_ls);
     const std::vector<double>& Wx = d.Wx;
     const std::vector<double>& Wxb = d.Wxb;
     tm.mark("z decompositions");
