@@ -16,6 +16,20 @@ namespace fmh {
 
 static inline double& at(double* A, int n, int i, int j) { return A[(size_t)i * n + j]; }
 
+// sum_j a[j] b[j] in four independent partial sums (instruction-level parallelism; vectorisable)
+static inline double dot4(const double* a, const double* b, int m) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int j = 0;
+  for (; j + 4 <= m; j += 4) {
+    s0 += a[j] * b[j];
+    s1 += a[j + 1] * b[j + 1];
+    s2 += a[j + 2] * b[j + 2];
+    s3 += a[j + 3] * b[j + 3];
+  }
+  for (; j < m; ++j) s0 += a[j] * b[j];
+  return (s0 + s1) + (s2 + s3);
+}
+
 bool lu_factor(int n, double* A, int* piv) {
   for (int k = 0; k < n; ++k) {
     int p = k;
@@ -51,17 +65,42 @@ void lu_solve(int n, const double* LU, const int* piv, double* b) {
   }
 }
 
+// X = A^{-1} B for n x n row-major B (m columns = n) from the LU factors, by whole-row operations (the
+// rows are contiguous: forward and back substitution as row AXPYs instead of strided column walks)
+static void lu_solve_rows(int n, const double* LU, const int* piv, double* B) {
+  // forward: the swaps interleaved with the elimination steps, as lu_factor made them (its multipliers
+  // of step k are not permuted by the later swaps)
+  for (int k = 0; k < n; ++k) {
+    double* bk = B + (size_t)k * n;
+    if (piv[k] != k)
+      for (int j = 0; j < n; ++j) std::swap(bk[j], B[(size_t)piv[k] * n + j]);
+    for (int i = k + 1; i < n; ++i) {
+      const double l = LU[(size_t)i * n + k];
+      if (l == 0.0) continue;
+      double* bi = B + (size_t)i * n;
+      for (int j = 0; j < n; ++j) bi[j] -= l * bk[j];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double* bi = B + (size_t)i * n;
+    for (int k = i + 1; k < n; ++k) {
+      const double u = LU[(size_t)i * n + k];
+      if (u == 0.0) continue;
+      const double* bk = B + (size_t)k * n;
+      for (int j = 0; j < n; ++j) bi[j] -= u * bk[j];
+    }
+    const double inv = 1.0 / LU[(size_t)i * n + i];
+    for (int j = 0; j < n; ++j) bi[j] *= inv;
+  }
+}
+
 bool invert(int n, const double* A, double* Ainv) {
   std::vector<double> LU(A, A + (size_t)n * n);
   std::vector<int> piv(n);
   if (!lu_factor(n, LU.data(), piv.data())) return false;
-  std::vector<double> col(n);
-  for (int j = 0; j < n; ++j) {
-    std::fill(col.begin(), col.end(), 0.0);
-    col[j] = 1.0;
-    lu_solve(n, LU.data(), piv.data(), col.data());
-    for (int i = 0; i < n; ++i) Ainv[(size_t)i * n + j] = col[i];
-  }
+  std::fill(Ainv, Ainv + (size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Ainv[(size_t)i * n + i] = 1.0;
+  lu_solve_rows(n, LU.data(), piv.data(), Ainv);
   return true;
 }
 
@@ -100,7 +139,7 @@ static void hessenberg(int n, double* A, double* Q) {
     std::fill(Q, Q + (size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i) at(Q, n, i, i) = 1.0;
   }
-  std::vector<double> v(n);
+  std::vector<double> v(n), srow(n);
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;  // length of the reflector, rows k+1..n-1
     double nrm = 0.0;
@@ -115,24 +154,30 @@ static void hessenberg(int n, double* A, double* Q) {
     for (int i = 0; i < m; ++i) vn += v[i] * v[i];
     if (vn == 0.0) continue;
     const double beta = 2.0 / vn;
-    for (int j = k; j < n; ++j) {  // left: rows k+1..n-1
-      double s = 0.0;
-      for (int i = 0; i < m; ++i) s += v[i] * at(A, n, k + 1 + i, j);
-      s *= beta;
-      for (int i = 0; i < m; ++i) at(A, n, k + 1 + i, j) -= s * v[i];
+    {  // left: rows k+1..n-1, s = beta v^T A[k+1.., k..] accumulated row by row (contiguous)
+      std::fill(srow.begin() + k, srow.end(), 0.0);
+      for (int i = 0; i < m; ++i) {
+        const double vi = v[i];
+        const double* ar = A + (size_t)(k + 1 + i) * n;
+        for (int j = k; j < n; ++j) srow[j] += vi * ar[j];
+      }
+      for (int j = k; j < n; ++j) srow[j] *= beta;
+      for (int i = 0; i < m; ++i) {
+        const double vi = v[i];
+        double* ar = A + (size_t)(k + 1 + i) * n;
+        for (int j = k; j < n; ++j) ar[j] -= srow[j] * vi;
+      }
     }
     for (int i = 0; i < n; ++i) {  // right: columns k+1..n-1
-      double s = 0.0;
-      for (int j = 0; j < m; ++j) s += at(A, n, i, k + 1 + j) * v[j];
-      s *= beta;
-      for (int j = 0; j < m; ++j) at(A, n, i, k + 1 + j) -= s * v[j];
+      double* ar = A + (size_t)i * n + k + 1;
+      const double s = beta * dot4(ar, v.data(), m);
+      for (int j = 0; j < m; ++j) ar[j] -= s * v[j];
     }
     if (Q)
       for (int i = 0; i < n; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < m; ++j) s += at(Q, n, i, k + 1 + j) * v[j];
-        s *= beta;
-        for (int j = 0; j < m; ++j) at(Q, n, i, k + 1 + j) -= s * v[j];
+        double* qr = Q + (size_t)i * n + k + 1;
+        const double s = beta * dot4(qr, v.data(), m);
+        for (int j = 0; j < m; ++j) qr[j] -= s * v[j];
       }
     at(A, n, k + 1, k) = alpha;
     for (int i = k + 2; i < n; ++i) at(A, n, i, k) = 0.0;
@@ -302,9 +347,7 @@ static void hess_shifted_lu_solve(int n, const double* M, const double* l, const
   }
   for (int i = n - 1; i >= 0; --i) {
     const double* ri = M + (size_t)i * n;
-    double s = b[i];
-    for (int j = i + 1; j < n; ++j) s -= ri[j] * b[j];
-    b[i] = s / ri[i];
+    b[i] = (b[i] - dot4(ri + i + 1, b + i + 1, n - i - 1)) / ri[i];
   }
 }
 
@@ -352,6 +395,8 @@ int eig_general2(int n, const double* Ain, double* re, double* im, double* Vr, d
   std::vector<double> work((size_t)n * n), y(n), lmul(n);
   std::vector<char> swp(n);
   std::vector<cplx> cwork((size_t)n * n), cy(n);
+  std::vector<double> Yh((size_t)n * n, 0.0);  // Hessenberg-basis eigenvectors of the real eigenvalues
+  std::vector<int> real_cols;
   const double tiny = 1e-15 * (hn > 0 ? hn : 1.0);
   for (int e = 0; e < n; ++e) {
     const bool cx = std::fabs(im[e]) > 1e-10 * maxabs;
@@ -367,18 +412,10 @@ int eig_general2(int n, const double* Ain, double* re, double* im, double* Vr, d
         if (!(nr > 0.0) || !std::isfinite(nr)) return -1;
         for (int i = 0; i < n; ++i) y[i] /= nr;
       }
-      double nr = 0.0;
-      for (int i = 0; i < n; ++i) {
-        double sacc = 0.0;
-        for (int j = 0; j < n; ++j) sacc += Q[(size_t)i * n + j] * y[j];
-        Vr[(size_t)i * n + e] = D[i] * sacc;
-        nr += Vr[(size_t)i * n + e] * Vr[(size_t)i * n + e];
-      }
-      nr = std::sqrt(nr);
-      for (int i = 0; i < n; ++i) {
-        Vr[(size_t)i * n + e] /= nr;
-        Vi[(size_t)i * n + e] = 0.0;
-      }
+      // Hessenberg-basis eigenvector, column e of Y; all real ones are back-transformed together below
+      for (int i = 0; i < n; ++i) Yh[(size_t)i * n + e] = y[i];
+      real_cols.push_back(e);
+      for (int i = 0; i < n; ++i) Vi[(size_t)i * n + e] = 0.0;
       continue;
     }
     status = 1;
@@ -406,6 +443,28 @@ int eig_general2(int n, const double* Ain, double* re, double* im, double* Vr, d
       Vi[(size_t)i * n + e] = v[i].imag() / nr;
     }
   }
+  if (!real_cols.empty()) {
+    // V = D Q Y for the real eigenvectors at once, by rows (row i of Q times the rows of Y: contiguous AXPYs)
+    std::vector<double> Vt((size_t)n * n, 0.0), nrm2(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      double* vt = Vt.data() + (size_t)i * n;
+      const double* qi = Q.data() + (size_t)i * n;
+      for (int j = 0; j < n; ++j) {
+        const double q = qi[j];
+        if (q == 0.0) continue;
+        const double* yj = Yh.data() + (size_t)j * n;
+        for (int e = 0; e < n; ++e) vt[e] += q * yj[e];
+      }
+      for (int e = 0; e < n; ++e) {
+        vt[e] *= D[i];
+        nrm2[e] += vt[e] * vt[e];
+      }
+    }
+    for (int e : real_cols) {
+      const double inv = 1.0 / std::sqrt(nrm2[e]);
+      for (int i = 0; i < n; ++i) Vr[(size_t)i * n + e] = Vt[(size_t)i * n + e] * inv;
+    }
+  }
   return status;
 }
 
@@ -427,15 +486,10 @@ int eig_real(int n, const double* Ain, double* lam, double* V) {
 
 int decompose(int n, const double* A1, const double* A2, bool descending, double* Wbar, double* W, double* lam) {
   // C = A2^{-1} A1
-  std::vector<double> LU(A2, A2 + (size_t)n * n), C((size_t)n * n);
+  std::vector<double> LU(A2, A2 + (size_t)n * n), C(A1, A1 + (size_t)n * n);
   std::vector<int> piv(n);
   if (!lu_factor(n, LU.data(), piv.data())) return -2;
-  std::vector<double> col(n);
-  for (int j = 0; j < n; ++j) {
-    for (int i = 0; i < n; ++i) col[i] = A1[(size_t)i * n + j];
-    lu_solve(n, LU.data(), piv.data(), col.data());
-    for (int i = 0; i < n; ++i) C[(size_t)i * n + j] = col[i];
-  }
+  lu_solve_rows(n, LU.data(), piv.data(), C.data());
   std::vector<double> l(n), V((size_t)n * n);
   if (eig_real(n, C.data(), l.data(), V.data()) != 0) return -1;
   std::vector<int> order(n);
@@ -459,15 +513,10 @@ int decompose(int n, const double* A1, const double* A2, bool descending, double
 
 int decompose_pairs(int n, const double* A1, const double* A2, int top, double* Wbar, double* W, double* lam,
                     int* kind) {
-  std::vector<double> LU(A2, A2 + (size_t)n * n), C((size_t)n * n);
+  std::vector<double> LU(A2, A2 + (size_t)n * n), C(A1, A1 + (size_t)n * n);
   std::vector<int> piv(n);
   if (!lu_factor(n, LU.data(), piv.data())) return -2;
-  std::vector<double> col(n);
-  for (int j = 0; j < n; ++j) {
-    for (int i = 0; i < n; ++i) col[i] = A1[(size_t)i * n + j];
-    lu_solve(n, LU.data(), piv.data(), col.data());
-    for (int i = 0; i < n; ++i) C[(size_t)i * n + j] = col[i];
-  }
+  lu_solve_rows(n, LU.data(), piv.data(), C.data());
   std::vector<double> re(n), im(n), Vr((size_t)n * n), Vi((size_t)n * n);
   if (eig_general2(n, C.data(), re.data(), im.data(), Vr.data(), Vi.data()) < 0) return -1;
   std::vector<int> order;
