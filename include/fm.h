@@ -148,9 +148,10 @@ typedef struct {
                         vector, so the float64 Krylov space is kept across the float32 solves; default);
                         1 = iterative refinement x += float32 solve of the normalised float64 residual,
                         each refinement step starting a new float32 Krylov space */
-  int z_tile;        /* points per tensor-core tile of the z stages: 0 = chosen per shape by fm_create's autotuner
-                        (each of 128, 64 and 32 timed on the context's buffers, results cached per shape for
-                        the process), or 128, 64, 32 fixed */
+  int z_tile;        /* tensor-core tile of the z stages: 0 = chosen per shape by fm_create's autotuner (widths 128,
+                        64 and 32 points in two shapes each, timed on the context's buffers, results cached per
+                        shape for the process); or fixed: 128, 64, 32 (runs along the output's contiguous
+                        index), + 256 for the shape with runs of 8 on the input side too */
   int device;        /* CUDA device ordinal */
   void* stream;      /* cudaStream_t, NULL = legacy default stream */
 } fm_opts;

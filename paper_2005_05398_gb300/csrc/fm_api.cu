@@ -484,7 +484,8 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
       o.y_solver > 2 || o.mma < 0 || o.mma > 3 || o.start_filter < 0 || o.start_filter > 16 || o.refine < 0 || o.refine > 8 ||
       !(o.inner_tol32 == 0.0 || (o.inner_tol32 >= 1e-7 && o.inner_tol32 <= 0.5)) || o.gram_schmidt < 0 ||
       o.gram_schmidt > 1 || o.mixed_scheme < 0 || o.mixed_scheme > 1 ||
-      !(o.z_tile == 0 || o.z_tile == 32 || o.z_tile == 64 || o.z_tile == 128) ||
+      !(o.z_tile == 0 || (((o.z_tile & ~256) == 32 || (o.z_tile & ~256) == 64 || (o.z_tile & ~256) == 128) &&
+        (o.z_tile & ~(256 | 255)) == 0)) ||
       o.tc_chain < 0 || o.tc_chain > 1 || (o.tc_chain == 1 && o.mma == FM_MMA_BF16))
     return FM_ERR_ARG;
   fm_ctx* c = new fm_ctx();

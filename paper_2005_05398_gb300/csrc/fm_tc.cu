@@ -27,6 +27,8 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -537,18 +539,21 @@ struct TcZArgs {
   int* err;
 };
 
-template <bool OUT_JI, int NP>
+// Tile shapes (SH): 0 = long runs on the output side (forward NP/4 i x 4 j, inverse 8 i x NP/8 j), 1 = runs
+// of 8 elements on the input side too (NP/8 i x 8 j both ways), for longer DRAM bursts on the strided loads.
+template <bool OUT_JI, int NP, int SH>
 struct ZTile {
-  static constexpr int TI = OUT_JI ? NP / 4 : 8;   // i extent of a tile
-  static constexpr int TJ = OUT_JI ? 4 : NP / 8;   // j extent
+  static constexpr int TI = SH == 1 ? NP / 8 : (OUT_JI ? NP / 4 : 8);  // i extent of a tile
+  static constexpr int TJ = SH == 1 ? 8 : (OUT_JI ? 4 : NP / 8);       // j extent
 };
 
-template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI, int NP>
+template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI, int NP, int SH>
 __global__ void __launch_bounds__(128) k_tc_z(const __grid_constant__ CUtensorMap tmW, const TcZArgs a) {
   static_assert(!(OUT_JI && IN_JI), "the forward stage reads x[M'][k][i][j]");
   static_assert(NP == 128 || NP == 64 || NP == 32, "tile of 128, 64 or 32 points");
   using TB = typename Op::T;
-  constexpr int TI_ = ZTile<OUT_JI, NP>::TI, TJ_ = ZTile<OUT_JI, NP>::TJ;
+  constexpr int TI_ = ZTile<OUT_JI, NP, SH>::TI, TJ_ = ZTile<OUT_JI, NP, SH>::TJ;
+  static_assert(TI_ * TJ_ == NP && 32 % TI_ == 0 && 32 % TJ_ == 0, "a 32-column load spans whole runs");
   constexpr int kTileA = 128 * 128;  // bytes of one K block of A (128 rows x 128 bytes)
   constexpr int kTileB = NP * 128;   // of B (NP rows)
   constexpr int kTpp = 128 / NP;     // threads per point of the tile (each loads every kTpp-th k)
@@ -1124,15 +1129,22 @@ int tc_setup(fm_ctx* c) {
   return tcz_autotune(c);
 }
 
+template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI, int SH>
+static cudaError_t tcz_attr_sh() {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_z<TI, Op, TO, OUT_JI, IN_JI, 128, SH>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_z<TI, Op, TO, OUT_JI, IN_JI, 64, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_z<TI, Op, TO, OUT_JI, IN_JI, 32, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+  return e;
+}
 template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI>
 static cudaError_t tcz_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_z<TI, Op, TO, OUT_JI, IN_JI, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_tc_z<TI, Op, TO, OUT_JI, IN_JI, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_tc_z<TI, Op, TO, OUT_JI, IN_JI, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  return e;
+  cudaError_t e = tcz_attr_sh<TI, Op, TO, OUT_JI, IN_JI, 0>();
+  return e == cudaSuccess ? tcz_attr_sh<TI, Op, TO, OUT_JI, IN_JI, 1>() : e;
 }
 
 int tc_kernels_init() {
@@ -1217,7 +1229,7 @@ int zstage(fm_ctx* c, const Comp& cp, const float* W, const TI* in, TO* out) {
 
 // z stages on the tensor cores.  Forward: x -> t[slab][j][i] (BF16 storage when 'to_bf16', ahead of the fused
 // BF16 chain).  Inverse: u[slab][j][i] (fused chain, 'in_ji') or t[slab][i][j] (unfused) -> y.
-template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI, int NP>
+template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI, int NP, int SH>
 static int tcz_launch_np(fm_ctx* c, const Comp& cp, const CUtensorMap& tm, const void* in, void* out) {
   TcZArgs a;
   a.in = in;
@@ -1227,7 +1239,7 @@ static int tcz_launch_np(fm_ctx* c, const Comp& cp, const CUtensorMap& tm, const
   a.ny = cp.ny;
   a.nM = c->nM;
   a.off = cp.off;
-  const int TI_ = ZTile<OUT_JI, NP>::TI, TJ_ = ZTile<OUT_JI, NP>::TJ;
+  const int TI_ = ZTile<OUT_JI, NP, SH>::TI, TJ_ = ZTile<OUT_JI, NP, SH>::TJ;
   a.tiles_i = (cp.nx + TI_ - 1) / TI_;
   a.tiles_j = (cp.ny + TJ_ - 1) / TJ_;
   a.kblocks = (cp.nz + Op::kRow - 1) / Op::kRow;
@@ -1244,20 +1256,24 @@ static int tcz_launch_np(fm_ctx* c, const Comp& cp, const CUtensorMap& tm, const
   const int grid = std::max(1, std::min(tiles, 152 * per_sm));
   const double nun = (double)cp.nx * cp.ny * cp.nz * c->nM;
   const int tk_ = prof_begin(c, FM_KERNEL_ZMIX);
-  k_tc_z<TI, Op, TO, OUT_JI, IN_JI, NP><<<grid, 128, smem, c->stream>>>(tm, a);
+  k_tc_z<TI, Op, TO, OUT_JI, IN_JI, NP, SH><<<grid, 128, smem, c->stream>>>(tm, a);
   prof_end(c, tk_, 2.0 * cp.nz * nun, nun * (double)(sizeof(TI) + sizeof(TO)));
   c->launches++;
   FM_CUDA(cudaGetLastError());
   return FM_OK;
 }
 
-// the component's z-stage tile width for this direction (set by the autotuner, or by fm_opts.z_tile)
+// the component's z-stage tile for this direction: width (points) + 256 * shape, set by the autotuner (or
+// the width by fm_opts.z_tile, shape 0)
 template <typename TI, typename Op, typename TO, bool OUT_JI, bool IN_JI>
 static int tcz_launch(fm_ctx* c, const Comp& cp, const CUtensorMap& tm, const void* in, void* out) {
   switch (cp.tcz_np[OUT_JI ? 0 : 1]) {
-    case 32: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 32>(c, cp, tm, in, out);
-    case 64: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 64>(c, cp, tm, in, out);
-    default: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 128>(c, cp, tm, in, out);
+    case 32: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 32, 0>(c, cp, tm, in, out);
+    case 64: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 64, 0>(c, cp, tm, in, out);
+    case 256 + 32: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 32, 1>(c, cp, tm, in, out);
+    case 256 + 64: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 64, 1>(c, cp, tm, in, out);
+    case 256 + 128: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 128, 1>(c, cp, tm, in, out);
+    default: return tcz_launch_np<TI, Op, TO, OUT_JI, IN_JI, 128, 0>(c, cp, tm, in, out);
   }
 }
 
@@ -1424,7 +1440,7 @@ int tcz_tune_comp(fm_ctx* c, Comp& cp, const TIO* x, TIO* y) {
     }
     float best = 1e30f;
     int best_np = 128;
-    for (int np : {128, 64, 32}) {
+    for (int np : {128, 64, 32, 256 + 128, 256 + 64, 256 + 32}) {
       cp.tcz_np[dir] = np;
       if ((rc = tcz_run<TIO>(c, cp, dir, x, y))) break;
       if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = FM_ERR_CUDA; break; }
@@ -1440,6 +1456,9 @@ int tcz_tune_comp(fm_ctx* c, Comp& cp, const TIO* x, TIO* y) {
         best = ms;
         best_np = np;
       }
+      if (getenv("FM_VERBOSE"))
+        fprintf(stderr, "[fm_tune] component %d z %s, %3d-point tiles, shape %d: %.1f us\n", cp.label,
+                dir ? "inverse" : "forward", np & 255, np >> 8, 1e3 * ms / 3);
     }
     cp.tcz_np[dir] = best_np;
     if (rc == FM_OK) {

@@ -101,7 +101,7 @@ def test_z_tile_widths_agree_bitwise(pkg, name, mma):
     wl = workload("he_l0_24x24x8", **(BF16_CASES[name] if mma == 3 else CASES[name]))
     E = wl["shift"] + 0.011
     out = {}
-    for zt in (128, 64, 32, 0):
+    for zt in (128, 64, 32, 256 + 128, 256 + 64, 256 + 32, 0):
         c = pkg.Context(wl, precision=1, mma=mma, z_tile=zt)
         c.fm_set_shift(E)
         v = _dev(rand_vec(c.n, 31))
@@ -111,7 +111,7 @@ def test_z_tile_widths_agree_bitwise(pkg, name, mma):
         out[zt] = y
         c.close()
     assert torch.isfinite(out[128]).all()
-    for zt in (64, 32, 0):
+    for zt in (64, 32, 256 + 128, 256 + 64, 256 + 32, 0):
         assert torch.equal(out[zt], out[128]), (name, zt, (out[zt] - out[128]).abs().max().item())
 
 
