@@ -505,39 +505,6 @@ __device__ __forceinline__ void copy_segments(int nseg, int valid, int pb, SrcF 
   for (int sg = t / pps; sg < nseg; sg += spr) cp_async_pb(dst(sg) + k * ep, src(sg) + k * ep, pb);
 }
 
-// Copy the S factor slots of 'rows' consecutive ring rows: global slot (row, slot) at src0 + (row * sdir * S +
-// slot) * nx (sdir = +1: rows ascending in memory, -1: descending), shared at dst0 + (row * RS + slot) * LPB;
-// each slot segment holds the CTA's LPB lines.  Same piece split as copy_segments, addresses stepped
-// (no division per piece).
-template <typename T, int LPB, int S>
-__device__ __forceinline__ void copy_factor_rows(int rows, int valid, int pb, const T* src0, int64_t nx, int sdir,
-                                                 T* dst0, int RS) {
-  const int ep = pb / (int)sizeof(T);
-  const int pps = (valid + ep - 1) / ep;
-  const int spr = LPB / pps;
-  const int t = threadIdx.x;
-  if (t >= spr * pps) return;
-  const int k = t % pps;
-  int seg = t / pps;
-  int row = seg / S, slot = seg - row * S;
-  const int nseg = rows * S;
-  // spr <= LPB <= 32 < 2 S is not guaranteed: wrap with a loop
-  const T* src = src0 + ((int64_t)row * sdir * S + slot) * nx + k * ep;
-  T* dst = dst0 + ((size_t)row * RS + slot) * LPB + k * ep;
-  for (; seg < nseg; seg += spr) {
-    cp_async_pb(dst, src, pb);
-    slot += spr;
-    src += (int64_t)spr * nx;
-    dst += (size_t)spr * LPB;
-    while (slot >= S) {
-      slot -= S;
-      ++row;
-      src += (int64_t)(sdir * S - S) * nx;  // next row: + sdir S slots, minus the S slots just passed
-      dst += (size_t)(RS - S) * LPB;
-    }
-  }
-}
-
 // w[p] for 0 <= p < N through a binary tree of selects (depth log2 N instead of a chain of N)
 template <typename T, int N>
 __device__ __forceinline__ T pick_window(const T* w, int p) {
@@ -577,45 +544,7 @@ struct RowPtr {
       p -= nx - (int64_t)nc * dc;
     }
   }
-  __device__ __forceinline__ void advance(int k) {  // k >= 0 rows on
-    int cc = c + k;
-    const int dj = cc / nc;
-    cc -= dj * nc;
-    p += (int64_t)(cc - c) * dc + (int64_t)dj * nx;
-    c = cc;
-  }
-  __device__ __forceinline__ void retreat(int k) {  // k >= 0 rows back
-    int cc = c - k, dj = 0;
-    if (cc < 0) {
-      dj = (nc - 1 - cc) / nc;
-      cc += dj * nc;
-    }
-    p += (int64_t)(cc - c) * dc - (int64_t)dj * nx;
-    c = cc;
-  }
 };
-
-// Copy one line value per ring row for 'cnt' consecutive rows of the line, starting at row walker w0
-// (ascending rows when up, descending otherwise) into ring slot 'slot' of rows 0 .. cnt-1.
-template <typename T, int LPB>
-__device__ __forceinline__ void copy_line_rows(int cnt, int valid, int pb, RowPtr<T> w0, bool up, T* dst0, int RS,
-                                               int slot) {
-  const int ep = pb / (int)sizeof(T);
-  const int pps = (valid + ep - 1) / ep;
-  const int spr = LPB / pps;
-  const int t = threadIdx.x;
-  if (t >= spr * pps) return;
-  const int k = t % pps;
-  int sg = t / pps;
-  RowPtr<T> w = w0;
-  if (up) w.advance(sg);
-  else w.retreat(sg);
-  for (; sg < cnt; sg += spr) {
-    cp_async_pb(dst0 + ((size_t)sg * RS + slot) * LPB + k * ep, w.p + k * ep, pb);
-    if (up) w.advance(spr);
-    else w.retreat(spr);
-  }
-}
 
 // One line through the banded LU factors, in place on the line's entries in global memory: seg(r) is the
 // entry of row r of the CTA's first line, and this thread's line is tid entries further.  Every row of both
@@ -635,17 +564,16 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
   const int RS = Wring + 1;  // slots per ring row (factor slots + the line value)
   const size_t half = (size_t)R * RS * LPB;
   // forward: L z = P b, row r uses L[r][0] (pivot offset) and L[r][1..KL]
-  // line walkers for the ring refills: the forward refill of chunk ch starts at row ch R + KL + 1, the
-  // backward one at row n - 1 - ch R; both advance R rows per chunk
-  RowPtr<T> wf = rp0, wb = rp0;
-  wf.advance(KL + 1);
   auto issue_f = [&](int ch) {
     T* buf = ring + (ch & 1) * half;
     const int r0 = ch * R, rows = min(R, n - r0);
-    copy_factor_rows<T, LPB, KL + 1>(rows, valid, pb, Lb + (int64_t)r0 * (KL + 1) * nx, nx, 1, buf, RS);
+    copy_segments<T, LPB>(
+        rows * (KL + 1), valid, pb,
+        [&](int sg) { return Lb + ((int64_t)(r0 + sg / (KL + 1)) * (KL + 1) + sg % (KL + 1)) * nx; },
+        [&](int sg) { return buf + ((size_t)(sg / (KL + 1)) * RS + sg % (KL + 1)) * LPB; });
     const int lo = r0 + KL + 1, cnt = max(0, min(rows, n - lo));  // window refills of rows r0 .. r0 + cnt - 1
-    copy_line_rows<T, LPB>(cnt, valid, pb, wf, true, buf, RS, Wring);
-    wf.advance(R);
+    copy_segments<T, LPB>(cnt, valid, pb, [&](int sg) { return (const T*)seg(lo + sg); },
+                          [&](int sg) { return buf + ((size_t)sg * RS + Wring) * LPB; });
     cp_commit();
   };
   T w[KL + 1];
@@ -669,15 +597,10 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
         const int r = r0 + q;
         const T* f = buf + (size_t)q * RS * LPB + tid;
         const int pn = (q + 1 < rows) ? (int)f[RS * LPB] : 0;  // next row's pivot offset, ahead of use
-        T xr = w[0];
-        // rows whose pivot stays on the diagonal in every line of the warp skip the pick and the swap
-        // (the branch is warp-uniform; live lanes are a prefix of the warp, so the mask covers them)
-        if (__any_sync(__activemask(), p != 0)) {
-          xr = pick_window<T, KL + 1>(w, p);
+        const T xr = pick_window<T, KL + 1>(w, p);
 #pragma unroll
-          for (int i = 1; i <= KL; ++i)
-            if (p == i) w[i] = w[0];
-        }
+        for (int i = 1; i <= KL; ++i)
+          if (p == i) w[i] = w[0];
 #pragma unroll
         for (int d = 1; d <= KL; ++d) w[d] -= f[d * LPB] * xr;
         rp.p[tid] = xr;
@@ -695,13 +618,14 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
   __syncthreads();
   // backward: U x = z, rows descending, U[r][0] the reciprocal of the pivot, U[r][d] the coefficient
   // of x[r + d]; v[i] = x[r + 1 + i] (0 beyond the line, where the band entries are 0)
-  wb.advance(n - 1);  // row n - 1
   auto issue_b = [&](int ch) {
     T* buf = ring + (ch & 1) * half;
     const int rtop = n - 1 - ch * R, rows = min(R, rtop + 1);
-    copy_factor_rows<T, LPB, W>(rows, valid, pb, Ub + (int64_t)rtop * W * nx, nx, -1, buf, RS);
-    copy_line_rows<T, LPB>(rows, valid, pb, wb, false, buf, RS, Wring);
-    wb.retreat(R);
+    copy_segments<T, LPB>(
+        rows * W, valid, pb, [&](int sg) { return Ub + ((int64_t)(rtop - sg / W) * W + sg % W) * nx; },
+        [&](int sg) { return buf + ((size_t)(sg / W) * RS + sg % W) * LPB; });
+    copy_segments<T, LPB>(rows, valid, pb, [&](int sg) { return (const T*)seg(rtop - sg); },
+                          [&](int sg) { return buf + ((size_t)sg * RS + Wring) * LPB; });
     cp_commit();
   };
   T v[W - 1];
