@@ -135,7 +135,7 @@ typedef struct {
   int refine;        /* fm_eigs: most inverse-iteration steps c <- (H - shift S)^{-1} S c / |.| (float64 solves
                         to tol) given to a returned pair whose backward error is above eig_tol; 0..8, default 2 */
   double inner_tol32; /* FM_PREC_MIXED: relative residual of each float32 inner solve, in [1e-7, 0.5], or 0 for
-                        the scheme's default (1e-3 flexible, 3e-5 refinement); smaller means fewer float64
+                        the scheme's default (1e-3 flexible, 3e-5 refinement, 1e-6 double-float); smaller means fewer float64
                         steps and more float32 iterations in each */
   int tc_chain;      /* tensor-core preconditioner chain: 0 = z stages on the tensor cores and, for n_M = 1, the
                         x / y stages of a slab in one fused kernel; 1 = z stages on CUDA cores and one
@@ -147,7 +147,9 @@ typedef struct {
                         each of its preconditioner steps a float32 FGMRES solve of the normalised basis
                         vector, so the float64 Krylov space is kept across the float32 solves; default);
                         1 = iterative refinement x += float32 solve of the normalised float64 residual,
-                        each refinement step starting a new float32 Krylov space */
+                        each refinement step starting a new float32 Krylov space; 2 = the flexible iteration
+                        with double-float inner solves (operator, basis and Gram-Schmidt as pairs of floats,
+                        about 48 significand bits, on the FP32 pipe; the float32 tensor preconditioner) */
   int z_tile;        /* tensor-core tile of the z stages: 0 = chosen per shape by fm_create's autotuner (widths 128,
                         64 and 32 points in two shapes each, timed on the context's buffers, results cached per
                         shape for the process); or fixed: 128, 64, 32 (runs along the output's contiguous

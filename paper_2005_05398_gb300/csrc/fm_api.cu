@@ -86,7 +86,7 @@ static int fgmres32(fm_ctx* c, double E, const float* b, float* d, double tol, i
 // Relative residual of each float32 inner solve in FM_PREC_MIXED (0 selects the scheme's default).
 static double inner_tol32(const fm_ctx* c) {
   if (c->opts.inner_tol32 > 0.0) return c->opts.inner_tol32;
-  return c->opts.mixed_scheme == 0 ? 1e-3 : 3e-5;
+  return c->opts.mixed_scheme == 0 ? 1e-3 : (c->opts.mixed_scheme == 2 ? 1e-6 : 3e-5);
 }
 
 // Preconditioner step of the flexible scheme: z <- float32 FGMRES solution of (H - E S) z = v for a unit
@@ -97,6 +97,83 @@ static int precond_flex32(fm_ctx* c, double E, const double* v, double* z, int m
   if ((rc = fgmres32(c, E, c->d32, c->e32, inner_tol32(c), max_iters, iters))) return rc;
   FM_CUDA(cudaMemsetAsync(z, 0, c->N * sizeof(double), c->stream));
   return add32(c, c->e32, 1.0, z);
+}
+
+// double-float right-preconditioned FGMRES for (H - E S) d = b (double-float operator and basis, the
+// float32 tensor preconditioner on the leading parts; Givens and the small least-squares problem in float64).
+// d starts at zero.  Mirrors fgmres32.
+static int fgmres_dd(fm_ctx* c, double E, const fmi::dd* b, fmi::dd* d, double tol, int max_iters, int* iters_out) {
+  using fmi::dd;
+  int rc;
+  const int m = c->opts.restart_m;
+  const int64_t N = c->N;
+  double b2;
+  if ((rc = dot_many_dd(c, b, N, 1, b, &b2))) return rc;
+  const double bnorm = std::sqrt(std::max(b2, 0.0));
+  *iters_out = 0;
+  FM_CUDA(cudaMemsetAsync(d, 0, N * sizeof(dd), c->stream));
+  if (!(bnorm > 0.0)) return FM_OK;
+  dd* r = c->rdd;
+  FM_CUDA(cudaMemcpyAsync(r, b, N * sizeof(dd), cudaMemcpyDeviceToDevice, c->stream));
+  double beta = bnorm, beta_prev = HUGE_VAL;
+  std::vector<double> R((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 1), y(m);
+  int total = 0;
+  while (beta > tol * bnorm && total < max_iters && beta <= 0.5 * beta_prev) {
+    beta_prev = beta;
+    if ((rc = axpby_dd(c, 1.0 / beta, r, 0.0, c->Vdd))) return rc;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m && total < max_iters; ++j) {
+      dd* Vj = c->Vdd + (int64_t)j * N;
+      dd* Zj = c->Zdd + (int64_t)j * N;
+      if ((rc = launch_precond_dd(c, Vj, Zj))) return rc;
+      if ((rc = launch_apply_dd(c, E, Zj, c->wdd, false))) return rc;
+      double hn;  // CGS2 writes the next basis vector Vdd[j+1] = (w - V h) / hn
+      if ((rc = gs_cgs2_dd(c, c->Vdd, j + 1, c->wdd, c->Vdd + (int64_t)(j + 1) * N, h.data(), &hn))) return rc;
+      if (!std::isfinite(hn)) return FM_ERR_BREAKDOWN;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+      }
+      const double rr = std::hypot(h[j], hn);
+      cs[j] = (rr == 0.0) ? 1.0 : h[j] / rr;
+      sn[j] = (rr == 0.0) ? 0.0 : hn / rr;
+      h[j] = rr;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) R[(size_t)i * m + j] = h[i];
+      ++total;
+      jdone = j + 1;
+      if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0) break;
+    }
+    for (int i = jdone - 1; i >= 0; --i) {
+      double sacc = g[i];
+      for (int k = i + 1; k < jdone; ++k) sacc -= R[(size_t)i * m + k] * y[k];
+      if (R[(size_t)i * m + i] == 0.0) return FM_ERR_BREAKDOWN;
+      y[i] = sacc / R[(size_t)i * m + i];
+    }
+    if ((rc = axpy_many_dd(c, c->Zdd, N, jdone, y.data(), d))) return rc;
+    if ((rc = launch_apply_dd(c, E, d, c->wdd, false))) return rc;  // double-float residual r = b - A d
+    if ((rc = axpby_dd(c, 1.0, b, 0.0, r))) return rc;
+    if ((rc = axpby_dd(c, -1.0, c->wdd, 1.0, r))) return rc;
+    double r2;
+    if ((rc = dot_many_dd(c, r, N, 1, r, &r2))) return rc;
+    beta = std::sqrt(std::max(r2, 0.0));
+    if (!std::isfinite(beta)) return FM_ERR_BREAKDOWN;
+  }
+  *iters_out = total;
+  return FM_OK;
+}
+
+// Preconditioner step of the flexible scheme with double-float inner solves (mixed_scheme 2).
+static int precond_flexdd(fm_ctx* c, double E, const double* v, double* z, int max_iters, int* iters) {
+  int rc;
+  if ((rc = to_dd(c, v, 1.0, c->bdd))) return rc;
+  if ((rc = fgmres_dd(c, E, c->bdd, c->xdd, inner_tol32(c), max_iters, iters))) return rc;
+  FM_CUDA(cudaMemsetAsync(z, 0, c->N * sizeof(double), c->stream));
+  return add_dd(c, c->xdd, 1.0, z);
 }
 
 // Right-preconditioned flexible GMRES (restart m) for (H - E S) x = b on the float64 operator.  The
@@ -146,7 +223,9 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
       double* Zj = c->Z + (int64_t)j * N;
       if (flex32) {
         int it = 0;
-        if ((rc = precond_flex32(c, E, Vj, Zj, std::max(1, max_iters - total), &it))) return rc;
+        if (c->use_dd) rc = precond_flexdd(c, E, Vj, Zj, std::max(1, max_iters - total), &it);
+        else rc = precond_flex32(c, E, Vj, Zj, std::max(1, max_iters - total), &it);
+        if (rc) return rc;
         inner32 += it;
         total += std::max(it, 1) - 1;  // the float32 iterations count against max_iters (+1 below)
         ++outer;
@@ -483,7 +562,7 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
       o.max_restarts < 0 || !(o.eig_tol > 0) || o.precision < 0 || o.precision > 2 || o.y_solver < 0 ||
       o.y_solver > 2 || o.mma < 0 || o.mma > 3 || o.start_filter < 0 || o.start_filter > 16 || o.refine < 0 || o.refine > 8 ||
       !(o.inner_tol32 == 0.0 || (o.inner_tol32 >= 1e-7 && o.inner_tol32 <= 0.5)) || o.gram_schmidt < 0 ||
-      o.gram_schmidt > 1 || o.mixed_scheme < 0 || o.mixed_scheme > 1 ||
+      o.gram_schmidt > 1 || o.mixed_scheme < 0 || o.mixed_scheme > 2 ||
       !(o.z_tile == 0 || (((o.z_tile & ~256) == 32 || (o.z_tile & ~256) == 64 || (o.z_tile & ~256) == 128) &&
         (o.z_tile & ~(256 | 255)) == 0)) ||
       o.tc_chain < 0 || o.tc_chain > 1 || (o.tc_chain == 1 && o.mma == FM_MMA_BF16))
@@ -518,6 +597,7 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
   }
   if ((rc = kernels_init(c))) return fail(rc);
   phase("kernel attributes");
+  c->use_dd = o.precision == FM_PREC_MIXED && o.mixed_scheme == 2;
   if ((rc = setup_host(c, grids, n_grids))) return fail(rc);
   phase("tables and decompositions");
   const int64_t N = c->N;
@@ -538,7 +618,13 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
     return fail(rc);
   if (cudaMemset(c->gs_cnt, 0, 256) != cudaSuccess) return fail(FM_ERR_CUDA);
   if (cudaMallocHost((void**)&c->red_host, 8192 * 8) != cudaSuccess) return fail(FM_ERR_OOM);
-  if (o.precision == FM_PREC_MIXED) {  // float32 Krylov workspace of the mixed-precision solves
+  if (c->use_dd) {  // double-float Krylov workspace; float32 buffers of the preconditioner's input and output
+    if ((rc = dev_alloc(c, (void**)&c->Vdd, (size_t)(m + 1) * N * 8)) || (rc = dev_alloc(c, (void**)&c->Zdd, (size_t)m * N * 8)) ||
+        (rc = dev_alloc(c, (void**)&c->wdd, N * 8)) || (rc = dev_alloc(c, (void**)&c->rdd, N * 8)) ||
+        (rc = dev_alloc(c, (void**)&c->bdd, N * 8)) || (rc = dev_alloc(c, (void**)&c->xdd, N * 8)) ||
+        (rc = dev_alloc(c, (void**)&c->d32, N * 4)) || (rc = dev_alloc(c, (void**)&c->e32, N * 4)))
+      return fail(rc);
+  } else if (o.precision == FM_PREC_MIXED) {  // float32 Krylov workspace of the mixed-precision solves
     if ((rc = dev_alloc(c, (void**)&c->V32, (size_t)(m + 1) * N * 4)) || (rc = dev_alloc(c, (void**)&c->Z32, (size_t)m * N * 4)) ||
         (rc = dev_alloc(c, (void**)&c->w32, N * 4)) || (rc = dev_alloc(c, (void**)&c->r32, N * 4)) ||
         (rc = dev_alloc(c, (void**)&c->d32, N * 4)) || (rc = dev_alloc(c, (void**)&c->e32, N * 4)) ||

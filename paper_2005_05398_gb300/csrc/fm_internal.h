@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/fm.h"
+#include "fm_dd.h"
 
 namespace fmi {
 
@@ -63,11 +64,18 @@ struct Tabs32 {
   float *zp = nullptr, *W = nullptr, *A = nullptr, *B = nullptr, *iy2 = nullptr, *cval = nullptr, *cw = nullptr;
 };
 
+// double-float copies of the operator tables (mixed_scheme 2: double-float inner solves)
+struct TabsDD {
+  dd *Sx = nullptr, *D2x = nullptr, *Sy = nullptr, *D2y = nullptr, *Sz = nullptr, *D1z = nullptr, *D2z = nullptr;
+  dd *zp = nullptr, *W = nullptr, *A = nullptr, *B = nullptr, *iy2 = nullptr, *cval = nullptr, *cw = nullptr;
+};
+
 struct Comp {
   int label = 0;                 // particle label alpha
   int r = 4;                     // taps per point of the component's basis (4 cubic, 6 quintic)
   int64_t ystage_off = 0;        // offset of the component in fm_ctx::ystage32 ([nM][nz][nx][nint_y][r])
   Tabs32 f32;
+  TabsDD tdd;
   Axis ax, ay, az;
   int nx = 0, ny = 0, nz = 0;
   int64_t npts = 0, off = 0;     // points per M' block, offset in the vector
@@ -164,6 +172,13 @@ struct fm_ctx {
   float* d32 = nullptr;          // [N]
   float* e32 = nullptr;          // [N]
   float* ystage32 = nullptr;     // float32 sources of the coupling regrouped by y interval (MIXED precision)
+  bool use_dd = false;           // MIXED precision, mixed_scheme 2: double-float inner solves
+  fmi::dd* Vdd = nullptr;             // their FGMRES basis [(m+1)][N]
+  fmi::dd* Zdd = nullptr;             // [m][N]
+  fmi::dd* wdd = nullptr;             // [N]
+  fmi::dd* rdd = nullptr;             // [N]
+  fmi::dd* bdd = nullptr;             // [N] right-hand side
+  fmi::dd* xdd = nullptr;             // [N] solution
   double* V = nullptr;           // FGMRES basis [(m+1)][N]
   double* Z = nullptr;           // FGMRES preconditioned directions [m][N]
   double* w = nullptr;           // [N]
@@ -233,6 +248,15 @@ int dot_many_dev(fm_ctx* c, const double* V, int64_t ldv, int nv, const double* 
 int gs_cgs2(fm_ctx* c, const double* V, int nv, double* w, double* vout, double* h, double* hn);
 int gs_cgs1(fm_ctx* c, const double* V, int nv, double* w, double* vout, double* h, double* hn);
 int gs_cgs2_32(fm_ctx* c, const float* V, int nv, float* w, float* vout, double* h, double* hn);
+// double-float inner solves (mixed_scheme 2)
+int launch_apply_dd(fm_ctx* c, double E, const dd* x, dd* y, bool only_S);
+int launch_precond_dd(fm_ctx* c, const dd* x, dd* y);  // the float32 tensor preconditioner on the leading parts
+int to_dd(fm_ctx* c, const double* x, double a, dd* y);    // y = a x
+int add_dd(fm_ctx* c, const dd* y, double a, double* x);   // x += a y
+int axpby_dd(fm_ctx* c, double a, const dd* x, double b, dd* y);  // y = a x + b y
+int dot_many_dd(fm_ctx* c, const dd* V, int64_t ldv, int nv, const dd* w, double* h_host);
+int axpy_many_dd(fm_ctx* c, const dd* V, int64_t ldv, int nv, const double* h_host, dd* w);  // w += sum h_j V_j
+int gs_cgs2_dd(fm_ctx* c, const dd* V, int nv, dd* w, dd* vout, double* h, double* hn);
 int tuning_correct(fm_ctx* c, const double* U, const double* WmU, const double* Gdev, int k, double* z);
 int scale_copy(fm_ctx* c, const double* x, double a, double* y);   // y = a x
 int axpby(fm_ctx* c, double a, const double* x, double b, double* y);  // y = a x + b y

@@ -1286,6 +1286,115 @@ __global__ void __launch_bounds__(256) k_absmax(const double* __restrict__ x, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float Krylov kernels (mixed_scheme 2 inner solves): vectors of dd, reductions summed in dd per
+// thread and in float64 across threads (fixed order, deterministic).
+// ---------------------------------------------------------------------------
+using fmi::dd;
+
+__device__ __forceinline__ double dd_d(dd v) { return (double)v.hi + (double)v.lo; }
+
+// y = dd(a x)
+__global__ void k_to_dd(const double* __restrict__ x, double a, dd* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = dd(a * x[i]);
+}
+// x += a y
+__global__ void k_add_dd(const dd* __restrict__ y, double a, double* __restrict__ x, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = fma(a, dd_d(y[i]), x[i]);
+}
+// leading parts as float32 (the tensor preconditioner's input), and back (its output, lo = 0)
+__global__ void k_dd_hi(const dd* __restrict__ x, float* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i].hi;
+}
+__global__ void k_f_to_dd(const float* __restrict__ x, dd* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = dd(x[i], 0.f);
+}
+// y = a x + b y (y is not read when b = 0)
+__global__ void k_axpby_dd(dd a, const dd* x, dd b, bool b_zero, dd* y, int64_t n) {  // x may be y
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = b_zero ? a * x[i] : fma(a, x[i], b * y[i]);
+}
+
+// out[j] = V_j . w for j < nv (eight vectors per pass)
+__global__ void __launch_bounds__(kRedThreads) k_dot_many_dd(const dd* __restrict__ V, int64_t ldv, int nv,
+                                                            const dd* __restrict__ w, int64_t n,
+                                                            double* __restrict__ partial, unsigned* counter,
+                                                            double* __restrict__ out) {
+  constexpr int JT = 8;
+  __shared__ double sh[JT][kRedThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j0 = 0; j0 < nv; j0 += JT) {
+    const int nj = min(JT, nv - j0);
+    dd acc[JT];
+#pragma unroll
+    for (int u = 0; u < JT; ++u) acc[u] = dd(0.f, 0.f);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      const dd wi = w[i];
+#pragma unroll
+      for (int u = 0; u < JT; ++u)
+        if (u < nj) acc[u] = fma(V[(int64_t)(j0 + u) * ldv + i], wi, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < JT; ++u) {
+      double v = dd_d(acc[u]);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[u][wid] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nj) {
+      double r = 0.0;
+      for (int q = 0; q < kRedThreads / 32; ++q) r += sh[threadIdx.x][q];
+      partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = r;
+    }
+    __syncthreads();
+  }
+  last_block_reduce(partial, nv, counter, out);
+}
+
+// w' = w - sum_j h_j V_j in dd (h from the device); MODE 0: w <- w', out[0] = ||w'||^2; MODE 1:
+// vout = w' / nu with nu^2 = nrm2_prev - |h|^2, out[0] = ||vout||^2, out[1] = nu.  MODE 2: w <- w + sum_j
+// h_j V_j (sign +, no norm).
+template <int MODE>
+__global__ void __launch_bounds__(kRedThreads) k_gs_axpy_dd(const dd* __restrict__ V, int64_t ldv, int nv,
+                                                           const double* __restrict__ h, dd* w, dd* vout, int64_t n,
+                                                           double* __restrict__ partial, unsigned* counter,
+                                                           double* __restrict__ out,
+                                                           const double* __restrict__ nrm2_prev) {
+  __shared__ dd cs[kGsMaxVec];
+  __shared__ double sh[32];
+  __shared__ dd inv_nu;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = MODE == 2 ? dd(h[j]) : dd(-h[j]);
+  if (MODE == 1 && threadIdx.x == 0) {
+    double c2 = 0.0;
+    for (int j = 0; j < nv; ++j) c2 = fma(h[j], h[j], c2);
+    const double nu2 = *nrm2_prev - c2;
+    const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
+    inv_nu = nu > 0.0 ? dd(1.0 / nu) : dd(0.f, 0.f);
+    if (blockIdx.x == 0) out[1] = nu;
+  }
+  __syncthreads();
+  dd acc(0.f, 0.f);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    dd v = w[i];
+    for (int j = 0; j < nv; ++j) v = fma(cs[j], V[(int64_t)j * ldv + i], v);
+    if (MODE == 1) {
+      v = v * inv_nu;
+      vout[i] = v;
+    } else {
+      w[i] = v;
+    }
+    if (MODE != 2) acc = fma(v, v, acc);
+  }
+  if (MODE == 2) return;
+  const double a = block_sum(dd_d(acc), sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = a;
+  last_block_reduce(partial, 1, counter, out);
+}
+
 inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
   int64_t g = (n + threads - 1) / threads;
   if (g > cap) g = cap;
@@ -1315,6 +1424,12 @@ template <>
 ApplyTabs<float> tabs_of<float>(const Comp& cp) {
   return {cp.f32.Sx, cp.f32.D2x, cp.f32.Sy, cp.f32.D2y, cp.f32.Sz, cp.f32.D1z, cp.f32.D2z, cp.f32.zp, cp.f32.W,
           cp.f32.A, cp.f32.B, cp.f32.iy2, cp.f32.cval, cp.f32.cw};
+}
+
+template <>
+ApplyTabs<dd> tabs_of<dd>(const Comp& cp) {
+  return {cp.tdd.Sx, cp.tdd.D2x, cp.tdd.Sy, cp.tdd.D2y, cp.tdd.Sz, cp.tdd.D1z, cp.tdd.D2z, cp.tdd.zp, cp.tdd.W,
+          cp.tdd.A, cp.tdd.B, cp.tdd.iy2, cp.tdd.cval, cp.tdd.cw};
 }
 
 // y = (H - E S) x (only_S: y = S x) with scratch planes P, Q, R, in the element type T.
@@ -2010,6 +2125,140 @@ int axpby32(fm_ctx* c, float a, const float* x, float b, float* y) {
   return FM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// double-float inner solves (mixed_scheme 2)
+// ---------------------------------------------------------------------------
+int launch_apply_dd(fm_ctx* c, double E, const dd* x, dd* y, bool only_S) {
+  // the float64 scratch planes, read as dd (the same 8 bytes per element; the float64 and dd applies never
+  // overlap)
+  return apply_t<dd>(c, E, x, y, only_S, reinterpret_cast<dd*>(c->P), reinterpret_cast<dd*>(c->Q),
+                     reinterpret_cast<dd*>(c->R), true);
+}
+
+int launch_precond_dd(fm_ctx* c, const dd* x, dd* y) {
+  int rc;
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+    k_dd_hi<<<grid_for(c->N, 256), 256, 0, c->stream>>>(x, c->d32, c->N);
+    prof_end(c, tk_, 0.0, 12.0 * (double)c->N);
+  }
+  if ((rc = launch_precond32(c, c->d32, c->e32))) return rc;
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+    k_f_to_dd<<<grid_for(c->N, 256), 256, 0, c->stream>>>(c->e32, y, c->N);
+    prof_end(c, tk_, 0.0, 12.0 * (double)c->N);
+  }
+  c->launches += 2;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+int to_dd(fm_ctx* c, const double* x, double a, dd* y) {
+  const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+  k_to_dd<<<grid_for(c->N, 256), 256, 0, c->stream>>>(x, a, y, c->N);
+  prof_end(c, tk_, 0.0, 16.0 * (double)c->N);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+int add_dd(fm_ctx* c, const dd* y, double a, double* x) {
+  const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+  k_add_dd<<<grid_for(c->N, 256), 256, 0, c->stream>>>(y, a, x, c->N);
+  prof_end(c, tk_, 0.0, 24.0 * (double)c->N);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+int axpby_dd(fm_ctx* c, double a, const dd* x, double b, dd* y) {
+  const int tk_ = prof_begin(c, FM_KERNEL_OTHER);
+  k_axpby_dd<<<grid_for(c->N, 256), 256, 0, c->stream>>>(dd(a), x, dd(b), b == 0.0, y, c->N);
+  prof_end(c, tk_, 0.0, 24.0 * (double)c->N);
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;
+}
+
+int dot_many_dd(fm_ctx* c, const dd* V, int64_t ldv, int nv, const dd* w, double* h_host) {
+  if (nv < 1 || nv > kGsMaxVec) return FM_ERR_ARG;
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+    k_dot_many_dd<<<c->red_blocks, kRedThreads, 0, c->stream>>>(V, ldv, nv, w, c->N, c->red, c->gs_cnt, c->gsd);
+    prof_end(c, tk_, 2.0 * nv * (double)c->N, (nv + 1.0) * 8.0 * (double)c->N);
+  }
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  std::memcpy(h_host, c->red_host, nv * sizeof(double));
+  return prof_harvest(c);
+}
+
+int axpy_many_dd(fm_ctx* c, const dd* V, int64_t ldv, int nv, const double* h_host, dd* w) {
+  if (nv < 1 || nv > kGsMaxVec) return FM_ERR_ARG;
+  double* hd = c->red + (int64_t)c->red_blocks * 256 + 512;
+  FM_CUDA(cudaMemcpyAsync(hd, h_host, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+    k_gs_axpy_dd<2><<<4 * c->red_blocks, kRedThreads, 0, c->stream>>>(V, ldv, nv, hd, w, nullptr, c->N, nullptr,
+                                                                      nullptr, nullptr, nullptr);
+    prof_end(c, tk_, 2.0 * nv * (double)c->N, (nv + 2.0) * 8.0 * (double)c->N);
+  }
+  c->launches++;
+  FM_CUDA(cudaGetLastError());
+  return FM_OK;  // the next copy into hd is ordered after this kernel on the stream
+}
+
+// Two classical Gram-Schmidt passes in dd (dot products and updates accumulated in dd): w <- w - V h,
+// vout = w / hn, as gs_cgs2_32 does in float32.
+int gs_cgs2_dd(fm_ctx* c, const dd* V, int nv, dd* w, dd* vout, double* h, double* hn) {
+  if (nv < 1 || nv > kGsMaxVec) return FM_ERR_ARG;
+  const int64_t N = c->N;
+  double* h1 = c->gsd;
+  double* h2 = c->gsd + kGsMaxVec;
+  double* sc = c->gsd + 3 * kGsMaxVec;
+  const int nb = c->red_blocks, nb2 = 4 * c->red_blocks;
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+    k_dot_many_dd<<<nb, kRedThreads, 0, c->stream>>>(V, N, nv, w, N, c->red, c->gs_cnt, h1);
+    prof_end(c, tk_, 2.0 * nv * (double)N, (nv + 1.0) * 8.0 * (double)N);
+  }
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+    k_gs_axpy_dd<0><<<nb2, kRedThreads, 0, c->stream>>>(V, N, nv, h1, w, nullptr, N, c->red, c->gs_cnt, sc, nullptr);
+    prof_end(c, tk_, (2.0 * nv + 2.0) * (double)N, (nv + 2.0) * 8.0 * (double)N);
+  }
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_DOT);
+    k_dot_many_dd<<<nb, kRedThreads, 0, c->stream>>>(V, N, nv, w, N, c->red, c->gs_cnt, h2);
+    prof_end(c, tk_, 2.0 * nv * (double)N, (nv + 1.0) * 8.0 * (double)N);
+  }
+  {
+    const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
+    k_gs_axpy_dd<1><<<nb2, kRedThreads, 0, c->stream>>>(V, N, nv, h2, w, vout, N, c->red, c->gs_cnt, sc + 1, sc);
+    prof_end(c, tk_, (2.0 * nv + 2.0) * (double)N, (nv + 2.0) * 8.0 * (double)N);
+  }
+  c->launches += 4;
+  FM_CUDA(cudaGetLastError());
+  FM_CUDA(cudaMemcpyAsync(c->red_host, c->gsd, kGsRead * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FM_CUDA(cudaStreamSynchronize(c->stream));
+  const double* hh = c->red_host;
+  if (c->tc_active && reinterpret_cast<const int*>(hh + kGsFlag)[0] != 0) return FM_ERR_TIMEOUT;
+  for (int i = 0; i < nv; ++i) h[i] = hh[i] + hh[kGsMaxVec + i];
+  const double vn2 = hh[3 * kGsMaxVec + 1], nu = hh[3 * kGsMaxVec + 2];
+  if (!(nu > 0.0) || !(vn2 > 0.0)) {
+    *hn = std::isfinite(nu) && std::isfinite(vn2) ? 0.0 : nu + vn2;
+    return prof_harvest(c);
+  }
+  const double vn = std::sqrt(vn2);
+  *hn = nu * vn;
+  int rc;
+  if (std::fabs(vn - 1.0) > 1e-12)  // renormalise when Pythagoras lost digits
+    if ((rc = axpby_dd(c, 1.0 / vn, vout, 0.0, vout))) return rc;
+  return prof_harvest(c);
+}
+
 int* tc_flag_slot(fm_ctx* c) { return reinterpret_cast<int*>(c->gsd + kGsFlag); }
 
 int kernels_init(fm_ctx* c) {
@@ -2018,6 +2267,8 @@ int kernels_init(fm_ctx* c) {
   FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, 4, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, 6, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, 6, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, 4, dd>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  FM_CUDA(cudaFuncSetAttribute(k_apply_xy<8, 6, dd>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<double, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   FM_CUDA(cudaFuncSetAttribute(k_zmix<float, double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));

@@ -591,6 +591,17 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
           (rc = up32(&cp.f32.A, Atab)) || (rc = up32(&cp.f32.B, Btab)) || (rc = up32(&cp.f32.iy2, iy2)))
         return rc;
     }
+    if (c->use_dd) {  // double-float copies for the double-float inner solves
+      auto updd = [&](dd** dst, const std::vector<double>& v) {
+        std::vector<dd> f(v.begin(), v.end());
+        return upload(c, (void**)dst, f.data(), f.size() * sizeof(dd));
+      };
+      if ((rc = updd(&cp.tdd.Sx, cp.ax.S)) || (rc = updd(&cp.tdd.D2x, cp.ax.D2)) || (rc = updd(&cp.tdd.Sy, cp.ay.S)) ||
+          (rc = updd(&cp.tdd.D2y, cp.ay.D2)) || (rc = updd(&cp.tdd.Sz, cp.az.S)) || (rc = updd(&cp.tdd.D1z, cp.az.D1)) ||
+          (rc = updd(&cp.tdd.D2z, cp.az.D2)) || (rc = updd(&cp.tdd.zp, cp.az.pts)) || (rc = updd(&cp.tdd.W, W)) ||
+          (rc = updd(&cp.tdd.A, Atab)) || (rc = updd(&cp.tdd.B, Btab)) || (rc = updd(&cp.tdd.iy2, iy2)))
+        return rc;
+    }
 
     // coupling geometry (Eqs. r-form, s-rot): active points and, per source, taps and weights
     if (!cp.sources.empty()) {
@@ -663,6 +674,11 @@ int setup_host(fm_ctx* c, const fm_grid* grids, int n_grids) {
       std::vector<float> val32(val.begin(), val.end()), wt32(wt.begin(), wt.end());
       if ((rc = upload(c, (void**)&cp.f32.cval, val32.data(), val32.size() * sizeof(float)))) return rc;
       if ((rc = upload(c, (void**)&cp.f32.cw, wt32.data(), wt32.size() * sizeof(float)))) return rc;
+      if (c->use_dd) {
+        std::vector<dd> vdd(val.begin(), val.end()), wdd(wt.begin(), wt.end());
+        if ((rc = upload(c, (void**)&cp.tdd.cval, vdd.data(), vdd.size() * sizeof(dd)))) return rc;
+        if ((rc = upload(c, (void**)&cp.tdd.cw, wdd.data(), wdd.size() * sizeof(dd)))) return rc;
+      }
     }
 
     tm.mark("coupling upload");
@@ -846,7 +862,7 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
   else if (S->identical_pair == 12) labels = {1, 3};
   else labels = {1, 2, 3};
   if (n_grids != 1 && n_grids != (int)labels.size()) return FM_ERR_ARG;
-  double bytes = 0.0;
+  double bytes = 0.0, dd_tables = 0.0;
   int64_t N = 0;
   for (size_t ic = 0; ic < labels.size(); ++ic) {
     const fm_grid& g = grids[n_grids == 1 ? 0 : ic];
@@ -861,6 +877,7 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
     N += (int64_t)(npts * nM);
     bytes += (nx + ny + nz) * (4 + 3 * R * 12 + 8) * 1.5;              // tap tables (float64 + float32)
     bytes += (2.0 * nM + 1.0) * npts * 12.0 + ny * 12.0;                 // W, B per M'; A; iy2 (+ float32)
+    dd_tables += (nx + ny + nz) * 3 * R * 8 + (2.0 * nM + 1.0) * npts * 8.0;
     if (split->mode != FM_SPLIT_SCHRODINGER) {                           // coupling geometry
       double act = 0.0;
       for (int i = 0; i < ax.n; ++i)
@@ -869,6 +886,7 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
       act *= nz;
       const double ns = 2.0;
       bytes += act * (4.0 + ns * (12.0 + 3.0 * R * 12.0 + nM * nM * 12.0));
+      dd_tables += act * ns * (3.0 * R + nM * nM) * 8.0;
     }
     const double nl = nM + nz - 1;
     bytes += 2.0 * nM * nz * nz * 12.0 + 2.0 * nl * nx * nx * 12.0;     // z and x decompositions
@@ -892,6 +910,8 @@ int estimate_bytes(const fm_system* S, const fm_grid* grids, int n_grids, const 
     }
   }
   const double m = o->restart_m, ncv = o->ncv, n = (double)N;
+  if (o->precision == FM_PREC_MIXED && o->mixed_scheme == 2)
+    bytes += dd_tables + n * 8.0 * ((m + 1) + m + 4);                  // double-float tables and Krylov vectors
   bytes += n * 8.0 * (5 + 2 + 3 + 16) + n * 4.0 * 2;                    // apply scratch, stage buffers, tuning
   bytes += n * 8.0 * ((m + 1) + std::max(m, ncv) + (ncv + 1));          // FGMRES and Arnoldi bases
   if (o->precision == FM_PREC_MIXED) bytes += n * 4.0 * ((m + 1) + m + 7 + 2.5);  // + y-interval sources

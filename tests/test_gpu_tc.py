@@ -161,10 +161,11 @@ def test_tc_solve_matches_sparse_lu(pkg, precision, tc_chain, gram_schmidt):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8
 
 
-@pytest.mark.parametrize("mixed_scheme", [0, 1])
+@pytest.mark.parametrize("mixed_scheme", [0, 1, 2])
 def test_mixed_schemes_match_sparse_lu(pkg, mixed_scheme):
-    """FM_PREC_MIXED, flexible inner-outer scheme (float64 FGMRES over float32 FGMRES preconditioner steps)
-    and iterative refinement: both reach the float64 tolerance and the sparse-LU solution of Eq. FM-lin."""
+    """FM_PREC_MIXED, flexible inner-outer scheme (float64 FGMRES over float32 FGMRES preconditioner steps),
+    iterative refinement, and the flexible scheme with double-float inner solves: each reaches the float64
+    tolerance and the sparse-LU solution of Eq. FM-lin."""
     from oracle.system import FMSystem
     from oracle import solvers
     wl = workload("he_l0_24x24x8", nint=(10, 12, 4), R=(20.0, 17.0))
@@ -178,6 +179,25 @@ def test_mixed_schemes_match_sparse_lu(pkg, mixed_scheme):
     print("mixed scheme", mixed_scheme, info)
     assert info["converged"] == 1 and info["resid"] <= 1e-12
     assert np.linalg.norm(x.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-8
+
+
+@pytest.mark.parametrize("name", ["he_l1_banded", "psm_l2", "he_l0_small"])
+def test_dd_inner_eigs_match_oracle(pkg, name):
+    """Double-float inner solves (mixed_scheme 2) inside the flexible float64 iteration: the certified
+    eigenvalues equal the oracle's to 1e-9 (n_M = 2 and 3 with banded y solves; n_M = 1 with the fused chain)."""
+    from oracle.system import FMSystem
+    from oracle import solvers
+    wl = workload("he_l0_24x24x8", **BF16_CASES[name]) if name == "he_l0_small" else _wl(name)
+    s = FMSystem(wl)
+    shift = wl["shift"] if name != "he_l1_banded" else -2.12
+    Eo, _ = solvers.eigs_near(s.H(), s.S(), shift, 6)
+    Eo = Eo[np.abs(Eo.imag) <= 1e-10 * np.abs(Eo)][:2].real
+    ctx = pkg.Context(wl, restart_m=40, precision=2, mixed_scheme=2)
+    ev, info = ctx.fm_eigs(shift, 2)
+    print(name, "double-float inner", info)
+    assert info["converged"] == 1 and info["resid"] <= 1e-9, info
+    for i in range(2):
+        assert abs(ev[i] - Eo[i]) <= 1e-9 * abs(Eo[i]), (ev, Eo)
 
 
 @pytest.mark.parametrize("name,k,precision", [("he_l1_banded", 2, 1), ("psm_l2", 2, 2), ("he_l1_banded", 2, 2)])
