@@ -337,12 +337,13 @@ def precision_modes(pkg, wl, args, copts, stream):
     certified eigenvalue and its deviation from the float64 mode.  fp64: float64 everywhere; fp32 /
     mixed: float32 preconditioner with TF32 tensor-core mode products (mixed also runs float32 inner
     solves as the preconditioner steps of a flexible float64 FGMRES; mixed_ir inside float64 iterative
-    refinement); *_bf16: the same with BF16 operands in the mode products."""
+    refinement; mixed_dd the flexible FGMRES with double-float inner solves on the FP32 pipe); *_bf16: the
+    same with BF16 operands in the mode products."""
     import torch
     n = None
     out = {}
     for name, code, mma, scheme in (("fp64", 0, 0, 0), ("fp32", 1, 0, 0), ("mixed", 2, 0, 0), ("mixed_ir", 2, 0, 1),
-                                    ("fp32_bf16", 1, 3, 0), ("mixed_bf16", 2, 3, 0)):
+                                    ("mixed_dd", 2, 0, 2), ("fp32_bf16", 1, 3, 0), ("mixed_bf16", 2, 3, 0)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c = pkg.Context(wl, precision=code, mma=mma, mixed_scheme=scheme, **copts)

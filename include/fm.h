@@ -135,7 +135,8 @@ typedef struct {
   int refine;        /* fm_eigs: most inverse-iteration steps c <- (H - shift S)^{-1} S c / |.| (float64 solves
                         to tol) given to a returned pair whose backward error is above eig_tol; 0..8, default 2 */
   double inner_tol32; /* FM_PREC_MIXED: relative residual of each float32 inner solve, in [1e-7, 0.5], or 0 for
-                        the scheme's default (1e-3 flexible, 3e-5 refinement, 1e-6 double-float); smaller means fewer float64
+                        the scheme's default (1e-3 flexible, 3e-5 refinement, half the outer tolerance but at least 3e-9 for
+                        double-float); smaller means fewer float64
                         steps and more float32 iterations in each */
   int tc_chain;      /* tensor-core preconditioner chain: 0 = z stages on the tensor cores and, for n_M = 1, the
                         x / y stages of a slab in one fused kernel; 1 = z stages on CUDA cores and one

@@ -168,10 +168,17 @@ static int fgmres_dd(fm_ctx* c, double E, const fmi::dd* b, fmi::dd* d, double t
 }
 
 // Preconditioner step of the flexible scheme with double-float inner solves (mixed_scheme 2).
-static int precond_flexdd(fm_ctx* c, double E, const double* v, double* z, int max_iters, int* iters) {
+// Its inner tolerance: fm_opts.inner_tol32 when set; by default half the outer tolerance, so that one
+// double-float Krylov space does the work (the float64 outer iteration then checks the true residual and
+// corrects what the double-float rounding left), but not below 3e-9, above the double-float rounding floor
+// of the operator (about 1e-14 relative per operation times its conditioning), where an inner solve
+// would only stagnate.
+static int precond_flexdd(fm_ctx* c, double E, const double* v, double* z, int max_iters, int* iters,
+                          double tol_outer) {
   int rc;
+  const double tin = c->opts.inner_tol32 > 0.0 ? c->opts.inner_tol32 : std::max(0.5 * tol_outer, 3e-9);
   if ((rc = to_dd(c, v, 1.0, c->bdd))) return rc;
-  if ((rc = fgmres_dd(c, E, c->bdd, c->xdd, inner_tol32(c), max_iters, iters))) return rc;
+  if ((rc = fgmres_dd(c, E, c->bdd, c->xdd, tin, max_iters, iters))) return rc;
   FM_CUDA(cudaMemsetAsync(z, 0, c->N * sizeof(double), c->stream));
   return add_dd(c, c->xdd, 1.0, z);
 }
@@ -223,7 +230,7 @@ static int fgmres(fm_ctx* c, double E, const double* b, double* x, double tol, i
       double* Zj = c->Z + (int64_t)j * N;
       if (flex32) {
         int it = 0;
-        if (c->use_dd) rc = precond_flexdd(c, E, Vj, Zj, std::max(1, max_iters - total), &it);
+        if (c->use_dd) rc = precond_flexdd(c, E, Vj, Zj, std::max(1, max_iters - total), &it, tol);
         else rc = precond_flex32(c, E, Vj, Zj, std::max(1, max_iters - total), &it);
         if (rc) return rc;
         inner32 += it;
