@@ -1438,28 +1438,43 @@ int tcz_tune_comp(fm_ctx* c, Comp& cp, const TIO* x, TIO* y) {
         continue;
       }
     }
-    float best = 1e30f;
-    int best_np = 128;
-    for (int np : {128, 64, 32, 256 + 128, 256 + 64, 256 + 32}) {
-      cp.tcz_np[dir] = np;
-      if ((rc = tcz_run<TIO>(c, cp, dir, x, y))) break;
-      if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = FM_ERR_CUDA; break; }
-      for (int r = 0; r < 3 && rc == FM_OK; ++r) rc = tcz_run<TIO>(c, cp, dir, x, y);
-      if (rc) break;
-      float ms = 0.f;
-      if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        rc = FM_ERR_CUDA;
-        break;
-      }
-      if (ms < best) {
-        best = ms;
-        best_np = np;
-      }
-      if (getenv("FM_VERBOSE"))
-        fprintf(stderr, "[fm_tune] component %d z %s, %3d-point tiles, shape %d: %.1f us\n", cp.label,
-                dir ? "inverse" : "forward", np & 255, np >> 8, 1e3 * ms / 3);
+    // three interleaved rounds of four timed launches per candidate (after one untimed launch each), the
+    // best round of each kept: the rounds share the device's state (clocks, L2) evenly among candidates
+    constexpr int kCands = 6, kRounds = 3, kReps = 4;
+    const int cand[kCands] = {128, 64, 32, 256 + 128, 256 + 64, 256 + 32};
+    float tbest[kCands];
+    for (int q = 0; q < kCands; ++q) tbest[q] = 1e30f;
+    for (int q = 0; q < kCands && rc == FM_OK; ++q) {
+      cp.tcz_np[dir] = cand[q];
+      rc = tcz_run<TIO>(c, cp, dir, x, y);
     }
+    for (int round = 0; round < kRounds && rc == FM_OK; ++round)
+      for (int q = 0; q < kCands && rc == FM_OK; ++q) {
+        cp.tcz_np[dir] = cand[q];
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = FM_ERR_CUDA; break; }
+        for (int r = 0; r < kReps && rc == FM_OK; ++r) rc = tcz_run<TIO>(c, cp, dir, x, y);
+        if (rc) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rc = FM_ERR_CUDA;
+          break;
+        }
+        tbest[q] = std::min(tbest[q], ms / kReps);
+      }
+    // the default (128 points, first shape) unless another tile is faster by more than 3 %
+    int best_np = cand[0];
+    float best = tbest[0];
+    for (int q = 1; q < kCands; ++q)
+      if (tbest[q] < 0.97f * best) {
+        best = tbest[q];
+        best_np = cand[q];
+      }
+    if (getenv("FM_VERBOSE"))
+      for (int q = 0; q < kCands; ++q)
+        fprintf(stderr, "[fm_tune] component %d z %s, %3d-point tiles, shape %d: %.1f us%s\n", cp.label,
+                dir ? "inverse" : "forward", cand[q] & 255, cand[q] >> 8, 1e3 * tbest[q],
+                cand[q] == best_np ? "  <- chosen" : "");
     cp.tcz_np[dir] = best_np;
     if (rc == FM_OK) {
       std::lock_guard<std::mutex> lk(g_tune_mu);
