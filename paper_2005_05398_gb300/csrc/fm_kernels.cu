@@ -598,15 +598,16 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
         const T* f = buf + (size_t)q * RS * LPB + tid;
         const int pn = (q + 1 < rows) ? (int)f[RS * LPB] : 0;  // next row's pivot offset, ahead of use
         const T xr = pick_window<T, KL + 1>(w, p);
+        const T w0 = w[0];
+        // swap (the pivot row's entry takes w[0]), elimination and window shift in one pass:
+        // new w[i] = (old w[i+1], or w[0] where it was the pivot row) - L[r][i+1] x_r
 #pragma unroll
-        for (int i = 1; i <= KL; ++i)
-          if (p == i) w[i] = w[0];
-#pragma unroll
-        for (int d = 1; d <= KL; ++d) w[d] -= f[d * LPB] * xr;
+        for (int i = 0; i < KL; ++i) {
+          const T src = (p == i + 1) ? w0 : w[i + 1];
+          w[i] = src - f[(i + 1) * LPB] * xr;
+        }
         rp.p[tid] = xr;
         rp.next();
-#pragma unroll
-        for (int i = 0; i < KL; ++i) w[i] = w[i + 1];
         w[KL] = (r + KL + 1 < n) ? f[Wring * LPB] : (T)0;
         p = pn;
       }
@@ -644,18 +645,41 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
     if (live) {
       const T* buf = ring + (ch & 1) * half;
       const int rows = min(R, n - ch * R);
-      for (int q = 0; q < rows; ++q) {
-        const T* f = buf + (size_t)q * RS * LPB + tid;
+      // one row: x = ((z - sum_{d >= 2} U[d] v[d-1]) - U[1] v[0]) U[0], from the solved values vv[0 ..]
+      auto row_x = [&](const T* f, const T* vv) -> T {
         T s0 = f[Wring * LPB], s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
-        for (int d = 2; d < W; d += 4) s0 -= f[d * LPB] * v[d - 1];
+        for (int d = 2; d < W; d += 4) s0 -= f[d * LPB] * vv[d - 1];
 #pragma unroll
-        for (int d = 3; d < W; d += 4) s1 -= f[d * LPB] * v[d - 1];
+        for (int d = 3; d < W; d += 4) s1 -= f[d * LPB] * vv[d - 1];
 #pragma unroll
-        for (int d = 4; d < W; d += 4) s2 -= f[d * LPB] * v[d - 1];
+        for (int d = 4; d < W; d += 4) s2 -= f[d * LPB] * vv[d - 1];
 #pragma unroll
-        for (int d = 5; d < W; d += 4) s3 -= f[d * LPB] * v[d - 1];
-        const T x = (((s0 + s1) + (s2 + s3)) - f[LPB] * v[0]) * f[0];
+        for (int d = 5; d < W; d += 4) s3 -= f[d * LPB] * vv[d - 1];
+        return (((s0 + s1) + (s2 + s3)) - f[LPB] * vv[0]) * f[0];
+      };
+      int q = 0;
+      // two rows per step: the second sees [x_a, v[0 .. W-3]], then the window moves by two
+      for (; q + 1 < rows; q += 2) {
+        const T* fa = buf + (size_t)q * RS * LPB + tid;
+        const T xa = row_x(fa, v);
+        T vb[W - 1];
+        vb[0] = xa;
+#pragma unroll
+        for (int i = 1; i < W - 1; ++i) vb[i] = v[i - 1];
+        const T xb = row_x(fa + RS * LPB, vb);
+        rp.p[tid] = xa;
+        rp.prev();
+        rp.p[tid] = xb;
+        rp.prev();
+#pragma unroll
+        for (int i = W - 2; i > 1; --i) v[i] = v[i - 2];
+        v[1] = xa;
+        v[0] = xb;
+      }
+      for (; q < rows; ++q) {
+        const T* f = buf + (size_t)q * RS * LPB + tid;
+        const T x = row_x(f, v);
         rp.p[tid] = x;
         rp.prev();
 #pragma unroll
