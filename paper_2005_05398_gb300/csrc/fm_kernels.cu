@@ -645,41 +645,18 @@ __device__ __forceinline__ void ysolve_line(const T* __restrict__ Lb, const T* _
     if (live) {
       const T* buf = ring + (ch & 1) * half;
       const int rows = min(R, n - ch * R);
-      // one row: x = ((z - sum_{d >= 2} U[d] v[d-1]) - U[1] v[0]) U[0], from the solved values vv[0 ..]
-      auto row_x = [&](const T* f, const T* vv) -> T {
+      for (int q = 0; q < rows; ++q) {
+        const T* f = buf + (size_t)q * RS * LPB + tid;
         T s0 = f[Wring * LPB], s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
-        for (int d = 2; d < W; d += 4) s0 -= f[d * LPB] * vv[d - 1];
+        for (int d = 2; d < W; d += 4) s0 -= f[d * LPB] * v[d - 1];
 #pragma unroll
-        for (int d = 3; d < W; d += 4) s1 -= f[d * LPB] * vv[d - 1];
+        for (int d = 3; d < W; d += 4) s1 -= f[d * LPB] * v[d - 1];
 #pragma unroll
-        for (int d = 4; d < W; d += 4) s2 -= f[d * LPB] * vv[d - 1];
+        for (int d = 4; d < W; d += 4) s2 -= f[d * LPB] * v[d - 1];
 #pragma unroll
-        for (int d = 5; d < W; d += 4) s3 -= f[d * LPB] * vv[d - 1];
-        return (((s0 + s1) + (s2 + s3)) - f[LPB] * vv[0]) * f[0];
-      };
-      int q = 0;
-      // two rows per step: the second sees [x_a, v[0 .. W-3]], then the window moves by two
-      for (; q + 1 < rows; q += 2) {
-        const T* fa = buf + (size_t)q * RS * LPB + tid;
-        const T xa = row_x(fa, v);
-        T vb[W - 1];
-        vb[0] = xa;
-#pragma unroll
-        for (int i = 1; i < W - 1; ++i) vb[i] = v[i - 1];
-        const T xb = row_x(fa + RS * LPB, vb);
-        rp.p[tid] = xa;
-        rp.prev();
-        rp.p[tid] = xb;
-        rp.prev();
-#pragma unroll
-        for (int i = W - 2; i > 1; --i) v[i] = v[i - 2];
-        v[1] = xa;
-        v[0] = xb;
-      }
-      for (; q < rows; ++q) {
-        const T* f = buf + (size_t)q * RS * LPB + tid;
-        const T x = row_x(f, v);
+        for (int d = 5; d < W; d += 4) s3 -= f[d * LPB] * v[d - 1];
+        const T x = (((s0 + s1) + (s2 + s3)) - f[LPB] * v[0]) * f[0];
         rp.p[tid] = x;
         rp.prev();
 #pragma unroll
