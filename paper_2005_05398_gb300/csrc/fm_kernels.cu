@@ -786,6 +786,17 @@ __device__ __forceinline__ float f64_lead_f32(double d) {
   return __uint_as_float((fe - 1u < 254u) ? (sign | (fe << 23) | ((hi & 0xFFFFFu) << 3)) : sign);
 }
 
+// a float64 value truncated to float32 by integer operations (1 + 23 significand bits; relative error < 2^-23),
+// without the FP64 pipe; values outside float32's normal range become signed zero
+__device__ __forceinline__ float f64_trunc_f32(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned fe = ((hi >> 20) & 0x7FFu) - 896u;  // float exponent (wraps below the float range)
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  return __uint_as_float((fe - 1u < 254u) ? (sign | (fe << 23) | mant) : sign);
+}
+
 // partial[j][block] = sum over this block's slice of V[j] . w  (j < nv), and for j = nv, when
 // 'extra' is given, extra . w; the last block reduces the partials into out[j].  The vectors are read
 // as 16-byte element pairs (n even, 16-byte aligned vectors), eight vectors and two pairs per thread
@@ -1037,6 +1048,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restric
   __shared__ double sh[32];
   __shared__ double inv_nu;
   __shared__ int reorth;
+  __shared__ int corr32;
   for (int j = threadIdx.x; j < nv; j += blockDim.x) {
     double cj;
     if (G) {
@@ -1055,6 +1067,9 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restric
     const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
     inv_nu = nu > 0.0 ? 1.0 / nu : 0.0;
     reorth = (MODE == 2 && !(nu2 >= 0.5 * *nrm2_prev)) ? 1 : 0;
+    // closing update on the FP32 pipe only while |h| <= 1e-6 |w'| (its float32 error, ~1e-7 |V h|, then stays
+    // below 1e-13 |w'|); with heavier cancellation the float64 path below
+    corr32 = (MODE == 1 && c2 <= 1e-12 * *nrm2_prev) ? 1 : 0;
     if (blockIdx.x == 0) {
       out[1] = nu;
       if (MODE == 2) out[2] = (double)reorth;
@@ -1063,6 +1078,36 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restric
   __syncthreads();
   const bool write_w = MODE == 0 || (MODE == 2 && reorth);
   double acc = 0.0;
+  if (MODE == 1 && corr32) {
+    // the closing update of CGS2: its coefficients are the second projection, of relative size ~5e-7 (the
+    // error of the first, FP32-pipe projection), so V h is summed on the FP32 pipe from 24-bit truncations
+    // (error ~1e-7 of a term ~5e-7 |w|: ~5e-14 |w|) and only w - corr, the scaling and the norm run in float64
+    __shared__ float csf[kGsMaxVec];
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) csf[j] = (float)cs[j];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      float c0 = 0.f, c1 = 0.f;
+      int j = 0;
+      for (; j + 7 < nv; j += 8) {
+        double t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = V[(int64_t)(j + u) * ldv + i];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          c0 = fmaf(csf[j + u], f64_trunc_f32(t[u]), c0);
+          c1 = fmaf(csf[j + u + 1], f64_trunc_f32(t[u + 1]), c1);
+        }
+      }
+      for (; j < nv; ++j) c0 = fmaf(csf[j], f64_trunc_f32(V[(int64_t)j * ldv + i]), c0);
+      const double o = (w[i] - (double)(c0 + c1)) * inv_nu;
+      vout[i] = o;
+      acc = fma(o, o, acc);
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+    last_block_reduce(partial, 1, counter, out);
+    return;
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     // one FMA per basis vector on a single chain (no partial sums to add: FP64 issue is the bound);
     // eight loads issued ahead of their FMAs
