@@ -1067,9 +1067,9 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restric
     const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
     inv_nu = nu > 0.0 ? 1.0 / nu : 0.0;
     reorth = (MODE == 2 && !(nu2 >= 0.5 * *nrm2_prev)) ? 1 : 0;
-    // closing update on the FP32 pipe only while |h| <= 1e-6 |w'| (its float32 error, ~1e-7 |V h|, then stays
-    // below 1e-13 |w'|); with heavier cancellation the float64 path below
-    corr32 = (MODE == 1 && c2 <= 1e-12 * *nrm2_prev) ? 1 : 0;
+    // closing update on the FP32 pipe only while |h| <= 1e-5 |w'| (its float32 error, ~1e-7 |V h|, then stays
+    // below 1e-12 |w'|); with heavier cancellation the float64 path below
+    corr32 = (MODE == 1 && c2 <= 1e-10 * *nrm2_prev) ? 1 : 0;
     if (blockIdx.x == 0) {
       out[1] = nu;
       if (MODE == 2) out[2] = (double)reorth;
@@ -1079,9 +1079,9 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_axpy(const double* __restric
   const bool write_w = MODE == 0 || (MODE == 2 && reorth);
   double acc = 0.0;
   if (MODE == 1 && corr32) {
-    // the closing update of CGS2: its coefficients are the second projection, of relative size ~5e-7 (the
+    // the closing update of CGS2: its coefficients are the second projection, of relative size ~1e-6 (the
     // error of the first, FP32-pipe projection), so V h is summed on the FP32 pipe from 24-bit truncations
-    // (error ~1e-7 of a term ~5e-7 |w|: ~5e-14 |w|) and only w - corr, the scaling and the norm run in float64
+    // (error ~1e-7 of a term <= 1e-5 |w'|) and only w - corr, the scaling and the norm run in float64
     __shared__ float csf[kGsMaxVec];
     for (int j = threadIdx.x; j < nv; j += blockDim.x) csf[j] = (float)cs[j];
     __syncthreads();
