@@ -797,112 +797,6 @@ __device__ __forceinline__ float f64_trunc_f32(double d) {
   return __uint_as_float((fe - 1u < 254u) ? (sign | (fe << 23) | mant) : sign);
 }
 
-// a float64 value as an unevaluated sum hi + lo of two floats, by integer operations (no FP64 pipe): hi = the
-// leading 24 significand bits, lo = the remaining 29 rounded to 24 (relative error < 2^-47); hi keeps
-// float32's normal range (other values give signed zero), lo is flushed to zero below 2^-74
-__device__ __forceinline__ void f64_split(double d, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
-  const unsigned e = (h >> 20) & 0x7FFu;
-  const unsigned fe = e - 896u;
-  const unsigned sign = h & 0x80000000u;
-  if (fe - 1u < 254u) {
-    hi = __uint_as_float(sign | (fe << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29));
-    const int se = (int)e - 948;  // biased float exponent of 2^(e - 1075), the weight of the low 29 bits
-    const float scale = (se > 0) ? __uint_as_float((unsigned)se << 23) : 0.f;
-    const float r = __fmul_rn(__uint2float_rn(l & 0x1FFFFFFFu), scale);
-    lo = sign ? -r : r;
-  } else {
-    hi = __uint_as_float(sign);
-    lo = 0.f;
-  }
-}
-
-// acc (an unnormalised double-float sum s + c) += (ah + al)(bh + bl), the product by TwoProd with the
-// cross terms, the sum by TwoSum; every step rounded to nearest, never contracted
-__device__ __forceinline__ void dd_dot_acc(float ah, float al, float bh, float bl, float& s, float& c) {
-  const float p = __fmul_rn(ah, bh);
-  float e = __fmaf_rn(ah, bh, -p);
-  e = __fmaf_rn(ah, bl, e);
-  e = __fmaf_rn(al, bh, e);
-  const float t = __fadd_rn(s, p);
-  const float bb = __fsub_rn(t, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
-  s = t;
-  c = __fadd_rn(c, __fadd_rn(err, e));
-}
-
-// The float64 multi-dot (16-byte pairs, eight vectors per pass) with its products and per-thread sums in
-// double-float arithmetic on the FP32 pipe, operands split by f64_split: about 2^-47 of sum |V_j w| per
-// coefficient, for the second projection of CGS2 (whose result is ~1e-6 of |w| and needs ~1e-14 |w|).
-__global__ void __launch_bounds__(kRedThreads) k_dot_many_split(const double* __restrict__ V, int64_t ldv, int nv,
-                                                               const double* __restrict__ w, int64_t n,
-                                                               double* __restrict__ partial, unsigned* counter,
-                                                               double* __restrict__ out) {
-  constexpr int JT = 8;
-  __shared__ double sh[JT][kRedThreads / 32];
-  const int64_t npair = n / 2;
-  const int64_t chunk = (npair + gridDim.x - 1) / gridDim.x;
-  const int64_t lo = (int64_t)blockIdx.x * chunk;
-  const int64_t hi = min(npair, lo + chunk);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const double2* w2 = reinterpret_cast<const double2*>(w);
-  for (int j0 = 0; j0 < nv; j0 += JT) {
-    const int nj = min(JT, nv - j0);
-    const double2* vp[JT];
-#pragma unroll
-    for (int u = 0; u < JT; ++u) vp[u] = reinterpret_cast<const double2*>(V + (int64_t)(j0 + min(u, nj - 1)) * ldv);
-    float as[JT], ac[JT];
-#pragma unroll
-    for (int u = 0; u < JT; ++u) as[u] = ac[u] = 0.f;
-    for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-      const double2 wv = w2[p];
-      double2 va[JT];
-#pragma unroll
-      for (int u = 0; u < JT; ++u)
-        if (u < nj) va[u] = vp[u][p];
-      float wxh, wxl, wyh, wyl;
-      f64_split(wv.x, wxh, wxl);
-      f64_split(wv.y, wyh, wyl);
-#pragma unroll
-      for (int u = 0; u < JT; ++u)
-        if (u < nj) {
-          float h0, l0, h1, l1;
-          f64_split(va[u].x, h0, l0);
-          f64_split(va[u].y, h1, l1);
-          dd_dot_acc(h0, l0, wxh, wxl, as[u], ac[u]);
-          dd_dot_acc(h1, l1, wyh, wyl, as[u], ac[u]);
-        }
-    }
-    if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {  // odd length: the last element
-      const int64_t e = n - 1;
-      float wh, wl;
-      f64_split(w[e], wh, wl);
-#pragma unroll
-      for (int u = 0; u < JT; ++u)
-        if (u < nj) {
-          float vh, vl;
-          f64_split(reinterpret_cast<const double*>(vp[u])[e], vh, vl);
-          dd_dot_acc(vh, vl, wh, wl, as[u], ac[u]);
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < JT; ++u) {
-      double v = (double)as[u] + (double)ac[u];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) sh[u][wid] = v;
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < nj) {
-      double r = 0.0;
-      for (int q = 0; q < kRedThreads / 32; ++q) r += sh[threadIdx.x][q];
-      partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = r;
-    }
-    __syncthreads();
-  }
-  last_block_reduce(partial, nv, counter, out);
-}
-
 // partial[j][block] = sum over this block's slice of V[j] . w  (j < nv), and for j = nv, when
 // 'extra' is given, extra . w; the last block reduces the partials into out[j].  The vectors are read
 // as 16-byte element pairs (n even, 16-byte aligned vectors), eight vectors and two pairs per thread
@@ -1947,19 +1841,7 @@ int gs_cgs2(fm_ctx* c, const double* V, int nv, double* w, double* vout, double*
                                                      sc, nullptr);
     prof_end(c, tk_, (2.0 * nv + 2.0) * (double)N, (nv + 2.0) * 8.0 * (double)N);
   }
-  {
-    // second projection: double-float products from split operands on the FP32 pipe (16-byte pairs), else
-    // the float64 multi-dot
-    const uintptr_t al = reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w) | (uintptr_t)(N * 8);
-    if ((al & 15u) == 0) {
-      const int tk_ = prof_begin(c, FM_KERNEL_DOT);
-      k_dot_many_split<<<c->red_blocks, kRedThreads, 0, c->stream>>>(V, N, nv, w, N, c->red, c->gs_cnt, h2);
-      prof_end(c, tk_, 2.0 * nv * (double)N, (nv + 1.0) * 8.0 * (double)N);
-      c->launches++;
-    } else if ((rc = dot_many_dev(c, V, N, nv, w, nullptr, h2))) {
-      return rc;
-    }
-  }
+  if ((rc = dot_many_dev(c, V, N, nv, w, nullptr, h2))) return rc;
   {
     const int tk_ = prof_begin(c, FM_KERNEL_AXPY);
     k_gs_axpy<1><<<nb2, kRedThreads, 0, c->stream>>>(V, N, nv, h2, nullptr, nullptr, w, vout, N, c->red, c->gs_cnt,
