@@ -142,8 +142,9 @@ typedef struct {
                         x / y stages of a slab in one fused kernel; 1 = z stages on CUDA cores and one
                         tensor-core launch per x / y stage (TF32) */
   int gram_schmidt;  /* float64 FGMRES orthogonalisation: 0 = two classical Gram-Schmidt passes, the first on
-                        the FP32 pipe from the leading bits; 1 = one float64 pass, repeated only when it
-                        cancelled more than half of the vector's norm (DGKS test) */
+                        the FP32 pipe from the leading bits, the closing update on the FP32 pipe too while the
+                        second projection is below 1e-5 of the vector (float64 otherwise); 1 = one float64
+                        pass, repeated only when it cancelled more than half of the vector's norm (DGKS test) */
   int mixed_scheme;  /* FM_PREC_MIXED: 0 = flexible inner-outer iteration (float64 FGMRES on the float64 operator,
                         each of its preconditioner steps a float32 FGMRES solve of the normalised basis
                         vector, so the float64 Krylov space is kept across the float32 solves; default);
