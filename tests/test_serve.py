@@ -119,3 +119,18 @@ def test_request_mix_is_seeded_and_in_range():
         else:
             lo, hi = MIX_EIG_SHIFT[wl["system"]]
             assert lo <= r["E"] <= hi
+
+
+def test_memory_estimate_counts_each_precision_mode(serve):
+    """fm_estimate_bytes (host only) sizes what fm_create allocates, so admission can trust it: the float32
+    Krylov workspace of MIXED precision and the double-float tables and basis of its mixed_scheme 2 each add
+    memory, and the vectors alone set a floor (N x 8 bytes x (2 m + ncv) for the float64 bases)."""
+    from paper_2005_05398_gb300._lib import fm_estimate_bytes
+    wl = workload("he_l0_24x24x8")
+    n = 2 * 48 * 48 * 18  # two components, 48 x 48 x 18 functions each
+    fp32 = fm_estimate_bytes(wl, restart_m=40, ncv=20, precision=1)
+    mixed = fm_estimate_bytes(wl, restart_m=40, ncv=20, precision=2, mixed_scheme=0)
+    mixed_dd = fm_estimate_bytes(wl, restart_m=40, ncv=20, precision=2, mixed_scheme=2)
+    assert fp32 >= n * 8 * (2 * 40 + 20)
+    assert mixed > fp32 + n * 4 * (2 * 40)          # float32 basis and directions
+    assert mixed_dd > mixed + n * 8 * (2 * 40 + 1)   # double-float basis and directions on top
