@@ -559,7 +559,8 @@ def main():
     ap.add_argument("--restart", type=int, default=40)
     ap.add_argument("--ncv", type=int, default=20)
     ap.add_argument("--tune", type=int, default=0, choices=[0, 1], help="tuned preconditioner in fm_eigs")
-    ap.add_argument("--start-filter", type=int, default=8, help="preconditioner passes on the Arnoldi start vector")
+    ap.add_argument("--start-filter", type=int, default=-1,
+                    help="preconditioner passes on the Arnoldi start vector (-1: the library's choice by k)")
     ap.add_argument("--k", type=int, default=None, help="eigenpairs per step (default: the workload's)")
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -131,7 +131,9 @@ typedef struct {
   int mma;           /* FM_MMA_AUTO, FM_MMA_SIMT, FM_MMA_TF32 or FM_MMA_BF16 */
   int start_filter;  /* fm_eigs: passes v <- P^{-1} S v / |.| applied to the start vector before the Arnoldi
                         process (the tensor preconditioner approximates (H - E* S)^{-1}, so each pass
-                        enriches the directions of the levels nearest the shift); 0..16, default 8 */
+                        enriches the directions of the levels nearest the shift); 0..16, or -1 (default):
+                        16 when one level is wanted, 6 when several are (more passes then filter the other
+                        wanted levels out) */
   int refine;        /* fm_eigs: most inverse-iteration steps c <- (H - shift S)^{-1} S c / |.| (float64 solves
                         to tol) given to a returned pair whose backward error is above eig_tol; 0..8, default 2 */
   double inner_tol32; /* FM_PREC_MIXED: relative residual of each float32 inner solve, in [1e-7, 0.5], or 0 for
@@ -191,7 +193,7 @@ typedef struct {
 typedef struct fm_ctx fm_ctx;
 
 /* Default options: tol 1e-12, restart 64, max_iters 2000, FP64, ncv 20, 50 restarts,
- * eig_tol 1e-9, replaced z eigenvalues, plain preconditioner, 8 start-vector filter passes, 2 refinement
+ * eig_tol 1e-9, replaced z eigenvalues, plain preconditioner, start-vector filter passes by k, 2 refinement
  * steps, device 0, default stream. */
 void fm_default_opts(fm_opts* opts);
 

@@ -499,7 +499,7 @@ void fm_default_opts(fm_opts* o) {
   o->tune = 0;
   o->y_solver = 0;
   o->mma = FM_MMA_AUTO;
-  o->start_filter = 8;
+  o->start_filter = -1;
   o->refine = 2;
   o->inner_tol32 = 0.0;
   o->tc_chain = 0;
@@ -567,7 +567,7 @@ int fm_create(const fm_system* sys, const fm_grid* grids, int n_grids, const fm_
   if (o.z_eigs == 1 && nM != 1) return FM_ERR_ARG;
   if (o.restart_m < 1 || o.restart_m > 256 || o.max_iters < 1 || !(o.tol > 0) || o.ncv < 3 || o.ncv > 64 ||
       o.max_restarts < 0 || !(o.eig_tol > 0) || o.precision < 0 || o.precision > 2 || o.y_solver < 0 ||
-      o.y_solver > 2 || o.mma < 0 || o.mma > 3 || o.start_filter < 0 || o.start_filter > 16 || o.refine < 0 || o.refine > 8 ||
+      o.y_solver > 2 || o.mma < 0 || o.mma > 3 || o.start_filter < -1 || o.start_filter > 16 || o.refine < 0 || o.refine > 8 ||
       !(o.inner_tol32 == 0.0 || (o.inner_tol32 >= 1e-7 && o.inner_tol32 <= 0.5)) || o.gram_schmidt < 0 ||
       o.gram_schmidt > 1 || o.mixed_scheme < 0 || o.mixed_scheme > 2 ||
       !(o.z_tile == 0 || (((o.z_tile & ~256) == 32 || (o.z_tile & ~256) == 64 || (o.z_tile & ~256) == 128) &&
@@ -814,7 +814,10 @@ static int eigs_impl(fm_ctx* c, double shift, int k, const double* v0, double* e
   if ((rc = nrm2(c, V, &nv))) return rc;
   if (!(nv > 0.0) || !std::isfinite(nv)) return FM_ERR_ARG;
   if ((rc = scale_copy(c, V, 1.0 / nv, V))) return rc;
-  for (int pass = 0; pass < c->opts.start_filter; ++pass) {  // v <- P^{-1} S v / ||P^{-1} S v||
+  // -1 (default): 16 passes for one wanted level, 6 for several (more passes filter the other wanted levels
+  // out of the start vector: measured on He L=0 with k = 1 and Ps- L=3 with k = 4)
+  const int n_filter = c->opts.start_filter >= 0 ? c->opts.start_filter : (k == 1 ? 16 : 6);
+  for (int pass = 0; pass < n_filter; ++pass) {  // v <- P^{-1} S v / ||P^{-1} S v||
     if ((rc = launch_apply(c, 0.0, V, c->tmpN, true))) return rc;
     if ((rc = launch_precond(c, c->tmpN, c->tmpN2))) return rc;
     if ((rc = nrm2(c, c->tmpN2, &nv))) return rc;
